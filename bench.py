@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark: one forward render + full gradient (Eq. Cost, score-function adjoint) of the
+64^3 cumulus scene (20 m voxels, cloud fraction 0.3, up to 80 1/km, albedo 0.999, g 0.85,
+sun zenith 45 deg) seen by 9 in-situ 128x128 cameras, 1e8 photons per step.
+
+Metric: photon path segments per second = forward-transport voxel crossings of one step
+(the same count for any implementation that traces the same photons) / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank traces its own 1e8 photons (distinct
+photon ids; weak scaling, no collective on the data path); the timed region is bracketed by
+a barrier and a device synchronize, and the max over ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "photon path segments/s (forward + full gradient, 64^3, 9 in-situ cams, 1e8 photons)"
+UNIT = "segments/s"
+WORKLOAD = "cumulus64: 64^3 x 20 m k^-5/3 cloud field (cf 0.3, max 80 1/km), albedo 0.999, g 0.85, " \
+           "sun zenith 45 deg, 9 in-situ 128x128 cams (2 inside the cloud base), 1e8 photons, full gradient"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--photons", type=float, default=1e8)
+    ap.add_argument("--grad", default="full", choices=["full", "surrogate"])
+    ap.add_argument("--grid-dtype", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--ref-photons", type=float, default=2e4, help="photons per oracle step (bounded sample)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            cols = [c.strip() for c in line.split(",")]
+            if len(cols) < 10 or (self.uuid and cols[1] != self.uuid):
+                continue
+            try:
+                sm.append(float(cols[2]))
+                mx.append(float(cols[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, cols[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel source
+    has not changed since the capture (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1512_02110_gb300", "csrc", "transport.cu"), "rb").read()
+        if d.get("transport_cu_sha1") != hashlib.sha1(src).hexdigest():
+            return None
+        rec = d.get("kernels", {}).get(kernel)
+        return None if rec is None else float(rec["dram_bytes_per_launch_full"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+
+
+def oracle_step(sc, p, meas, nthreads=0):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.full_grad(sc, p, meas, nthreads=nthreads)
+    return time.perf_counter() - t0, r["stats"]["segments"]
+
+
+def cpu_baseline(sc, p, meas, n_sample):
+    import oracle
+    oracle.build()
+    q = p.replace(n_photons=int(n_sample), n_photons_total=int(n_sample))
+    dt, segs = oracle_step(sc, q, meas)
+    cores = os.cpu_count()
+    return {"value": segs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"cumulus64 scene, {int(n_sample)} photons forward + full gradient incl. all deterministic "
+                      f"stages in full (LOS, images, back-projection, LOS adjoint), FP64, OpenMP over {cores} "
+                      f"threads; {dt:.2f} s",
+            "step_s": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    sc, p = synth.cfg_cumulus64()
+    sc = sc.with_beta(sc.beta.astype(np.float32).astype(np.float64))
+    n = int(args.ref_photons)
+    q = p.replace(n_photons=n, n_photons_total=n)
+    meas = np.zeros(sc.n_pix)
+    for _ in range(args.warmup):
+        oracle_step(sc, q.replace(n_photons=1000, n_photons_total=1000), meas)
+    times, segs = [], 0
+    for _ in range(args.steps):
+        dt, segs = oracle_step(sc, q, meas)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = segs / (ms * 1e-3)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("1e8 photons", f"{n} photons (bounded CPU sample)"),
+                       "photons_per_step": n, "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} photons per step, forward + full gradient, all deterministic stages "
+                                       f"in full; warm-up steps use 1000 photons"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import paper_1512_02110_gb300 as m
+    import synth
+
+    sc, p = synth.cfg_cumulus64(int(args.photons))
+    n = int(args.photons)
+    p = p.replace(photon_offset=rank * n, n_photons_total=n)
+    grid = m.Grid.from_scene(sc)
+    beta_np = sc.beta.astype(np.float32)
+    beta = torch.from_numpy(beta_np).cuda()
+    # measured images: a render of the same field with another seed (the end state of a
+    # reconstruction, where paths are longest)
+    meas = grid.render(beta, m.make_params(p, seed=4), images=True)["images"]
+    params = m.make_params(p, grad_mode=args.grad, grid_dtype=args.grid_dtype)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    for _ in range(args.warmup):
+        grid.render_grad(beta, params, meas, images=False)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    grid.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phase_acc = {}
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(uuid)
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))          # L2 flush between timed steps, outside the event pair
+        ev[i][0].record()
+        out = grid.render_grad(beta, params, meas, images=False)
+        ev[i][1].record()
+        for k, (ms, nl) in grid.phase_times().items():
+            a = phase_acc.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += nl
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st = grid.stats()
+    grid.set_profiling(False)
+
+    ms_step = sum(step_ms) / len(step_ms)
+    segs = st["segments"]
+    local_vals = torch.tensor([ms_step, segs], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        mx = local_vals.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = local_vals.clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        ms_job, segs_job = float(mx[0]), float(tot[1])
+    else:
+        ms_job, segs_job = ms_step, segs
+    value = segs_job / (ms_job * 1e-3)
+
+    # roofline of the dominant kernel (algorithmic bytes per launch / average launch time)
+    C = sc.n_cams
+    tr_ms, tr_n = phase_acc["transport"]
+    rp_ms, rp_n = phase_acc["replay"]
+    if rp_ms > tr_ms:
+        kern, kms, kn = "k_replay", rp_ms, rp_n
+        abytes = 4 * st["replay_segments"] + 4 * C * st["replay_events"] + 8 * st["replay_scatters"]
+        calls_per_step = rp_n / args.steps
+    else:
+        kern, kms, kn = "k_transport", tr_ms, tr_n
+        abytes = 4 * st["segments"] + 8 * C * st["events"]
+        calls_per_step = tr_n / args.steps
+    per_launch_bytes = abytes / calls_per_step
+    per_launch_s = (kms / kn) * 1e-3
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = traffic_record(kern)
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": kms / kn,
+                "launches_per_step": calls_per_step,
+                "phase_ms_per_step": {k: v[0] / args.steps for k, v in phase_acc.items()}}
+    launches = int(sum(v[1] for v in phase_acc.values()))
+
+    # end to end through the public API, host buffers in pinned memory
+    e2e = None
+    if not args.no_e2e:
+        beta_h = torch.from_numpy(beta_np).pin_memory()
+        meas_h = meas.cpu().pin_memory()
+        grad_h = torch.empty(sc.nvox, dtype=torch.float64).pin_memory()
+        loss_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        e_ms = []
+        for i in range(max(1, min(args.steps, 3))):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            bd = beta_h.to("cuda", non_blocking=True)
+            md = meas_h.to("cuda", non_blocking=True)
+            o = grid.render_grad(bd, params, md, images=False)
+            grad_h.copy_(o["grad"], non_blocking=True)
+            loss_h.copy_(o["loss"], non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        e_mean = sum(e_ms) / len(e_ms)
+        e2e = {"value": segs_job / (e_mean * 1e-3) if dist is None else segs / (e_mean * 1e-3) * world,
+               "unit": UNIT, "h2d_bytes_per_step": int(beta_np.nbytes + meas.numel() * 8),
+               "d2h_bytes_per_step": int(sc.nvox * 8 + 8), "ms_per_step": e_mean}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc.with_beta(beta_np.astype(np.float64)), p, meas.cpu().numpy(), args.ref_photons * 5)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_job, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "photons_per_gpu": n, "grad_mode": args.grad,
+                           "grid_dtype": args.grid_dtype, "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": f"photon-id shards x{world}" if world > 1 else "1 GPU"},
+                "segments_per_step": {"forward": segs, "replay": st["replay_segments"],
+                                      "los": st["los_segments"], "pixel": st["pixel_segments"],
+                                      "backproject": st["backproj_segments"], "los_adjoint": st["losadj_segments"]},
+                "events_per_step": st["events"], "step_ms_all": step_ms, "wall_s": wall,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * mst.h - C ABI of the GB300 library for in-situ multi-scattering tomography
+ * (Holodovsky, Schechner, Levin, Levis, Aides, "In-situ multi-scattering tomography", 2015).
+ *
+ * The library renders the paper's voxelised forward Monte-Carlo model and its per-voxel
+ * gradient on one CUDA GPU (sm_103a). All arrays passed in or out are device pointers unless
+ * a name ends in _host. Nothing here allocates or frees caller memory.
+ *
+ * Units: lengths in metres, extinction beta in 1/m, angles in radians.
+ *
+ * Layouts:
+ *   voxel k = ix + nx*(iy + ny*iz), x fastest; voxel (ix,iy,iz) covers
+ *     [origin + i*h, origin + (i+1)*h) on each axis; z is up; the top face is the top of the
+ *     atmosphere where sunlight enters (Sec. 2.1.2, step i).
+ *   per-camera fields [C][nvox]; images [sum_c W_c*H_c], camera c's block at offset
+ *     sum_{c'<c} W_c' H_c', pixel (i, j) of a block at j*W + i (i = column along `right`,
+ *     j = row along `up`).
+ *
+ * Asynchrony: every call that takes a stream only enqueues work on that stream (cudaStream_t,
+ * NULL = legacy default stream) and returns. Errors raised by kernels show up at mst_sync or
+ * at the next call. One handle owns scratch buffers, so calls on the same handle must be
+ * ordered (same stream, or synchronised by the caller).
+ *
+ * Return codes: MST_OK (0) or a negative MST_ERR_*; mst_last_error(handle) describes the last
+ * failure on that handle.
+ */
+#ifndef MST_H
+#define MST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MST_OK 0
+#define MST_ERR_INVALID_ARG (-1) /* rejected before any launch; nothing was enqueued */
+#define MST_ERR_CUDA (-2)        /* a CUDA call or kernel failed */
+#define MST_ERR_OOM (-3)         /* device allocation failed in mst_create_grid */
+#define MST_ERR_NO_DEVICE (-4)   /* no usable CUDA device */
+#define MST_ERR_UNSUPPORTED (-5) /* combination of options not implemented */
+
+#define MST_MAX_CAMERAS 16
+#define MST_MAX_SUBPIXEL_RAYS 64
+#define MST_NSTATS 32
+
+/* local estimate used by the forward render */
+enum { MST_EST_VOXEL = 0, MST_EST_CLASSIC = 1 };
+/* storage type of the staged extinction grid (arithmetic is always FP32) */
+enum { MST_GRID_F32 = 0, MST_GRID_F16 = 1, MST_GRID_BF16 = 2 };
+/* gradient of mst_render_grad */
+enum { MST_GRAD_SURROGATE = 0, MST_GRAD_FULL = 1 };
+/* diagonal conditioning Q_c of the surrogate gradient (Sec. 6) */
+enum { MST_COND_NONE = 0, MST_COND_INV_COUNT = 1, MST_COND_COUNT = 2 };
+
+/* indices into the statistics block (mst_get_stats) */
+enum {
+    MST_ST_ESC_XM = 0, MST_ST_ESC_XP, MST_ST_ESC_YM, MST_ST_ESC_YP, MST_ST_ESC_ZM, MST_ST_ESC_ZP,
+    MST_ST_ABSORBED = 6, MST_ST_RR_KILLED = 7, MST_ST_RR_GAINED = 8, MST_ST_FORCED = 9,
+    MST_ST_EVENTS = 10, MST_ST_SEGMENTS = 11, MST_ST_CAPPED = 12, MST_ST_ESCAPED_N = 13,
+    MST_ST_LAUNCHED = 14, MST_ST_TRACED = 15,
+    MST_ST_REPLAY_SEGMENTS = 16, MST_ST_REPLAY_EVENTS = 17, MST_ST_LOS_SEGMENTS = 18,
+    MST_ST_PIXEL_SEGMENTS = 19, MST_ST_BACKPROJ_SEGMENTS = 20, MST_ST_LOSADJ_SEGMENTS = 21,
+    MST_ST_REPLAY_SCATTERS = 22, MST_ST_LOST = 23 /* walks abandoned (non-finite direction); 0 in valid use */
+};
+
+/* phases timed by the profiler (mst_get_phase_times) */
+enum {
+    MST_PH_STAGE = 0, MST_PH_TRANSPORT = 1, MST_PH_FOLD = 2, MST_PH_LOS = 3, MST_PH_IMAGES = 4,
+    MST_PH_BACKPROJECT = 5, MST_PH_LOS_ADJOINT = 6, MST_PH_REPLAY = 7, MST_PH_COMBINE = 8, MST_NPHASES = 9
+};
+
+typedef struct mst_grid mst_grid; /* opaque; owned by the library */
+
+/* Voxel grid of cuboid voxels (Sec. 3: beta, albedo and g constant per voxel). */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double origin[3];
+} mst_grid_desc;
+
+/* Pinhole camera c with centre of projection X_c = pos (Sec. 2.1). rot holds the
+ * world-from-camera axes right, up, forward as three consecutive 3-vectors, orthonormal to
+ * 1e-3 (mst_create_grid rejects other bases). The ray through
+ * image-plane point (px, py), px in [0, W], py in [0, H], has direction
+ * normalize(forward + x right + y up), x = (2 px/W - 1) tan(fov_x/2),
+ * y = (2 py/H - 1) tan(fov_x/2) H/W. */
+typedef struct {
+    double pos[3];
+    double rot[9];
+    int width, height;
+    double fov_x_rad;
+} mst_camera;
+
+/* Parameters of one render (Sec. 2.1.2, Sec. 3.2, Sec. 5-6). */
+typedef struct {
+    double albedo;          /* single-scattering albedo, in [0, 1] */
+    double g;               /* Henyey-Greenstein anisotropy, in (-1, 1) (Eq. Phg) */
+    double sun_zenith_rad;  /* direction TO the sun: zenith angle ...                        */
+    double sun_azimuth_rad; /* ... and azimuth from +x; photons travel along the opposite     */
+    double sun_irradiance;  /* F: irradiance on a surface normal to the sun (images in F units) */
+    double rr_threshold;    /* Russian roulette below rr_threshold * I0 (0 disables)          */
+    double rr_survival;     /* survival probability of the roulette, in (0, 1]                */
+    uint64_t n_photons;     /* photons traced by this call (>= 1)                             */
+    uint64_t photon_offset; /* global id of the first photon (sharding)                      */
+    uint64_t n_photons_total; /* normaliser N in I0 = F cos(theta0) Lx Ly / N; 0 = n_photons  */
+    uint64_t seed;          /* Philox key                                                      */
+    int max_order;          /* stop after this many scattering events (0 = no limit)          */
+    int max_events;         /* hard cap on events per photon, counted in MST_ST_CAPPED        */
+    int estimator;          /* MST_EST_VOXEL (the paper's method) or MST_EST_CLASSIC (Eq. fle) */
+    int grid_dtype;         /* MST_GRID_F32 / F16 / BF16 storage of the staged beta            */
+    int grad_mode;          /* MST_GRAD_SURROGATE or MST_GRAD_FULL                             */
+    int conditioning;       /* MST_COND_*: applies to MST_GRAD_SURROGATE only                  */
+    double reg_eta;         /* weight eta of the Laplacian regulariser (Eq. Cost, Sec. 6)      */
+} mst_params;
+
+/* Fills defaults: albedo 0.99, g 0.85, sun at zenith, F = 1, roulette 0.01 / 0.1,
+ * 1e6 photons, seed 3, max_events 100000, voxel estimator, FP32 grid, surrogate gradient,
+ * no conditioning, eta 0. */
+void mst_default_params(mst_params *p);
+
+/* Geometry pre-calculation (Sec. 3, step i). Copies the grid and cameras into a new handle
+ * on the current CUDA device and allocates its scratch buffers. n_subpixel_rays = N_rays of
+ * Eq. PIc (1..MST_MAX_SUBPIXEL_RAYS); the sub-pixel points are the 2-D Halton points (bases 2
+ * and 3, indices 1..N_rays). Requires 1 <= n_cams <= MST_MAX_CAMERAS, positive sizes.
+ * On failure *out is NULL. */
+int mst_create_grid(const mst_grid_desc *grid, int n_cams, const mst_camera *cams, int n_subpixel_rays,
+                    mst_grid **out);
+
+/* Releases the handle and everything it owns. NULL-safe. Synchronises the device first. */
+void mst_destroy(mst_grid *g);
+
+/* Forward render (Sec. 2.1.2 steps i-vi; Eq. Lcupdate; Eq. taoKtoc-Tck; Eq. Icpixel).
+ *   beta_dev   [nvox] float, >= 0, read only.
+ *   images_dev [sum W*H] double or NULL: voxel estimator -> i_c = Pi_c (L_c . T_c);
+ *              classic estimator -> the local-estimate images of Eq. fle.
+ *   L_dev      [C][nvox] double or NULL: L_c(k) of Eq. Lcupdate (voxel estimator only).
+ * Photon p (global id photon_offset + p) draws from Philox-4x32-10 with key = seed and
+ * counter (id lo, id hi, event, 0). */
+int mst_render(mst_grid *g, const float *beta_dev, const mst_params *p, double *images_dev, double *L_dev,
+               void *stream);
+
+/* Forward render plus the masked L2 loss of Eq. Cost and its gradient dE/dbeta.
+ *   images_meas_dev [sum W*H] double: measured images.
+ *   mask_dev        [sum W*H] uint8 or NULL (all ones): the sun mask M_c.
+ *   images_dev      [sum W*H] double or NULL: rendered images.
+ *   grad_dev        [nvox] double: written (not accumulated).
+ *   loss_dev        [1] double or NULL: E = sum M (i - i_meas)^2 + eta Psi.
+ * MST_GRAD_SURROGATE: the paper's gradient with j = L/beta held fixed (Eq. divCost1 with
+ * Eq. Jaco1, Eq. TcofJaco1, Eq. DivTc) and conditioning Q_c.
+ * MST_GRAD_FULL: the full gradient of Eq. DirectJacob applied to the residual, where
+ * dL/dbeta is estimated by the score of the free-flight density (Eq. beer-lambert,
+ * Eq. MCextinct) over paths replayed from their Philox keys (no paths are stored).
+ * Requires the voxel estimator. */
+int mst_render_grad(mst_grid *g, const float *beta_dev, const mst_params *p, const double *images_meas_dev,
+                    const uint8_t *mask_dev, double *images_dev, double *grad_dev, double *loss_dev, void *stream);
+
+/* LOS transmittance T_c(k) = exp(-tau_c(k)), tau_c = W_c beta, from the centre of voxel k to
+ * X_c (Eq. taoKtoc, Eq. Dvc, Eq. bTck, Eq. Tck). T_dev [C][nvox] float. grid_dtype as above. */
+int mst_transmittance(mst_grid *g, const float *beta_dev, int grid_dtype, float *T_dev, void *stream);
+
+/* Image formation from a given L (Eq. Rc, Eq. IcPJbetaT, Eq. Icpixel):
+ * i_c(p) = 1/(N_rays V) sum_rho sum_k l^rho_{c,p}(k) L_c(k) T_c(k), T from beta_dev.
+ * L_dev [C][nvox] double, images_dev [sum W*H] double. */
+int mst_form_images(mst_grid *g, const float *beta_dev, int grid_dtype, const double *L_dev, double *images_dev,
+                    void *stream);
+
+/* Surrogate gradient with j = L_ref/beta_ref held fixed (Sec. 5.2; Eq. minobjectiveBetaQplus1,
+ * Eq. Jaco1-DivTc; j = 0 where beta_ref = 0): images i_c = Pi_c(j . beta . T_c(beta)), loss
+ * and dE/dbeta at beta_dev, with p->conditioning and p->reg_eta. Only p->conditioning,
+ * p->reg_eta and p->grid_dtype are read. No photons are traced: this is the inner step of
+ * the N_GD loop of Eq. GD. L_ref_dev [C][nvox] double, beta_ref_dev [nvox] float. */
+int mst_surrogate_grad(mst_grid *g, const float *beta_dev, const double *L_ref_dev, const float *beta_ref_dev,
+                       const mst_params *p, const double *images_meas_dev, const uint8_t *mask_dev,
+                       double *images_dev, double *grad_dev, double *loss_dev, void *stream);
+
+/* Q_c(k): number of sub-pixel rays with a positive chord in voxel k (Sec. 6).
+ * Q_dev [C][nvox] float. */
+int mst_ray_counts(mst_grid *g, float *Q_dev, void *stream);
+
+/* Laplacian regulariser Psi = ||Lap beta||^2 with the 6-neighbour graph Laplacian and W = I
+ * (Sec. 6). psi_dev [1] double or NULL; grad_dev [nvox] double or NULL, receives += eta dPsi. */
+int mst_regularizer(mst_grid *g, const float *beta_dev, double eta, double *psi_dev, double *grad_dev,
+                    void *stream);
+
+/* Validation aids for the forward render, kept on the handle until replaced:
+ *   photon_hash_dev [n_photons] uint32 or NULL: per-photon path checksum (FNV-1a over the
+ *     event voxels, then the event count and the termination code 1 escape, 2 absorbed,
+ *     3 roulette, 4 max_order, 5 event cap); 0 for skipped photons.
+ *   photon_skip_dev [n_photons] uint8 or NULL: photons with a nonzero entry are not traced.
+ * Both are indexed by the call's photon index (0 .. n_photons-1). */
+int mst_set_debug(mst_grid *g, uint32_t *photon_hash_dev, const uint8_t *photon_skip_dev);
+
+/* Copies the statistics of the last render call (MST_NSTATS doubles: escaped weight per face,
+ * absorbed, roulette, segment and event counts) to the host. Synchronises the device. */
+int mst_get_stats(mst_grid *g, double *stats_host);
+
+/* Enables (1) or disables (0) the phase profiler: every later call records a CUDA event pair on
+ * its stream around each kernel launch, grouped by MST_PH_* phase. */
+int mst_set_profiling(mst_grid *g, int enable);
+
+/* Per-phase device time of the last call, in ms (ms_host[MST_NPHASES]), and the number of
+ * launches per phase (launches_host[MST_NPHASES], may be NULL). Synchronises the device.
+ * Returns MST_ERR_INVALID_ARG when profiling is off. */
+int mst_get_phase_times(mst_grid *g, double *ms_host, int *launches_host);
+
+/* Waits for the handle's work and reports any asynchronous error. */
+int mst_sync(mst_grid *g);
+
+/* Message of the last error on the handle ("" if none); valid until the next call. */
+const char *mst_last_error(mst_grid *g);
+
+/* Library version (integer, increases with the ABI). */
+int mst_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MST_H */

@@ -1,0 +1,292 @@
+"""Python binding of libmst (include/mst.h): GB300-native in-situ multi-scattering tomography.
+
+Argument marshalling only. Every step of the render and gradient runs in the CUDA library;
+torch provides device memory and the current stream. If libmst.so has not been built this
+module raises at import time: there is no CPU fallback.
+
+Units: metres, 1/m, radians. Layouts follow include/mst.h: voxel k = ix + nx*(iy + ny*iz);
+per-camera fields [C, nvox]; images flat [sum_c W_c*H_c], camera blocks in order, pixel
+(i, j) of a block at j*W + i.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmst.so")
+
+MST_OK = 0
+ERRORS = {-1: "invalid argument", -2: "CUDA error", -3: "out of device memory", -4: "no CUDA device",
+          -5: "unsupported"}
+EST = {"voxel": 0, "classic": 1}
+GRID_DTYPE = {"f32": 0, "f16": 1, "bf16": 2}
+GRAD = {"surrogate": 0, "full": 1}
+COND = {"none": 0, "inv_count": 1, "count": 2}
+NSTATS = 32
+STAT_NAMES = ["esc_xm", "esc_xp", "esc_ym", "esc_yp", "esc_zm", "esc_zp", "absorbed", "rr_killed", "rr_gained",
+              "forced", "events", "segments", "capped", "escaped_n", "launched", "traced", "replay_segments",
+              "replay_events", "los_segments", "pixel_segments", "backproj_segments", "losadj_segments",
+              "replay_scatters", "lost"]
+EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy", "mst_render", "mst_render_grad",
+           "mst_transmittance", "mst_form_images", "mst_surrogate_grad", "mst_ray_counts", "mst_regularizer",
+           "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
+           "mst_get_phase_times"]
+PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine"]
+
+
+class MSTError(RuntimeError):
+    pass
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("dz", ctypes.c_double), ("origin", ctypes.c_double * 3)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_double * 3), ("rot", ctypes.c_double * 9), ("width", ctypes.c_int),
+                ("height", ctypes.c_int), ("fov_x_rad", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("albedo", ctypes.c_double), ("g", ctypes.c_double), ("sun_zenith_rad", ctypes.c_double),
+                ("sun_azimuth_rad", ctypes.c_double), ("sun_irradiance", ctypes.c_double),
+                ("rr_threshold", ctypes.c_double), ("rr_survival", ctypes.c_double),
+                ("n_photons", ctypes.c_uint64), ("photon_offset", ctypes.c_uint64),
+                ("n_photons_total", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("max_order", ctypes.c_int), ("max_events", ctypes.c_int), ("estimator", ctypes.c_int),
+                ("grid_dtype", ctypes.c_int), ("grad_mode", ctypes.c_int), ("conditioning", ctypes.c_int),
+                ("reg_eta", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+    L.mst_version.restype = I
+    L.mst_default_params.argtypes = [P]
+    L.mst_create_grid.argtypes = [P, I, P, I, ctypes.POINTER(P)]
+    L.mst_create_grid.restype = I
+    L.mst_destroy.argtypes = [P]
+    L.mst_render.argtypes = [P, P, P, P, P, P]
+    L.mst_render_grad.argtypes = [P, P, P, P, P, P, P, P, P]
+    L.mst_transmittance.argtypes = [P, P, I, P, P]
+    L.mst_form_images.argtypes = [P, P, I, P, P, P]
+    L.mst_surrogate_grad.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
+    L.mst_ray_counts.argtypes = [P, P, P]
+    L.mst_regularizer.argtypes = [P, P, D, P, P, P]
+    L.mst_set_debug.argtypes = [P, P, P]
+    L.mst_get_stats.argtypes = [P, P]
+    L.mst_set_profiling.argtypes = [P, I]
+    L.mst_get_phase_times.argtypes = [P, P, P]
+    L.mst_sync.argtypes = [P]
+    L.mst_last_error.argtypes = [P]
+    L.mst_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("mst_last_error", "mst_default_params", "mst_destroy", "mst_version"):
+            getattr(L, name).restype = I
+    L.mst_destroy.restype = None
+    L.mst_default_params.restype = None
+    return L
+
+
+lib = _load()
+
+
+def default_params() -> Params:
+    p = Params()
+    lib.mst_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(src=None, **kw) -> Params:
+    """mst_params from any object with the fields of synth.Params (albedo, g, sun_zenith, ...)
+    plus keyword overrides (estimator, grid_dtype, grad_mode, conditioning, reg_eta, ...)."""
+    p = default_params()
+    alias = {"sun_zenith": "sun_zenith_rad", "sun_azimuth": "sun_azimuth_rad"}
+    fields = {f for f, _ in Params._fields_}
+    items = {}
+    if src is not None:
+        d = dataclasses.asdict(src) if dataclasses.is_dataclass(src) else dict(vars(src))
+        items.update(d)
+    items.update(kw)
+    for k, v in items.items():
+        k = alias.get(k, k)
+        if k == "estimator" and isinstance(v, str):
+            v = EST[v]
+        elif k == "grid_dtype" and isinstance(v, str):
+            v = GRID_DTYPE[v]
+        elif k == "grad_mode" and isinstance(v, str):
+            v = GRAD[v]
+        elif k == "conditioning" and isinstance(v, str):
+            v = COND[v]
+        if k in fields:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Grid:
+    """A handle (mst_grid) with its cameras: geometry pre-calculation of Sec. 3."""
+
+    def __init__(self, shape, h, origin, cam_pos, cam_rot, cam_w, cam_h, cam_fov, n_rays: int = 10):
+        self.shape = tuple(int(s) for s in shape)
+        self.nvox = int(np.prod(self.shape))
+        cam_pos = np.asarray(cam_pos, dtype=np.float64).reshape(-1, 3)
+        self.n_cams = cam_pos.shape[0]
+        cam_rot = np.asarray(cam_rot, dtype=np.float64).reshape(self.n_cams, 9)
+        cam_w = np.asarray(cam_w).reshape(-1)
+        cam_h = np.asarray(cam_h).reshape(-1)
+        cam_fov = np.asarray(cam_fov, dtype=np.float64).reshape(-1)
+        self.cam_w, self.cam_h = cam_w.astype(np.int64), cam_h.astype(np.int64)
+        self.n_pix = int(np.sum(self.cam_w * self.cam_h))
+        self.pix_off = np.concatenate([[0], np.cumsum(self.cam_w * self.cam_h)]).astype(np.int64)
+        desc = GridDesc(self.shape[0], self.shape[1], self.shape[2], float(h[0]), float(h[1]), float(h[2]),
+                        (ctypes.c_double * 3)(*[float(o) for o in origin]))
+        cams = (Camera * self.n_cams)()
+        for c in range(self.n_cams):
+            cams[c].pos = (ctypes.c_double * 3)(*cam_pos[c])
+            cams[c].rot = (ctypes.c_double * 9)(*cam_rot[c])
+            cams[c].width, cams[c].height = int(cam_w[c]), int(cam_h[c])
+            cams[c].fov_x_rad = float(cam_fov[c])
+        handle = ctypes.c_void_p()
+        rc = lib.mst_create_grid(ctypes.byref(desc), self.n_cams, cams, int(n_rays), ctypes.byref(handle))
+        if rc != MST_OK:
+            raise MSTError(f"mst_create_grid: {ERRORS.get(rc, rc)}")
+        self._h = handle
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @classmethod
+    def from_scene(cls, scene) -> "Grid":
+        return cls(scene.shape, scene.h, scene.origin, scene.cam_pos, scene.cam_rot, scene.cam_w, scene.cam_h,
+                   scene.cam_fov, scene.n_rays)
+
+    # -- helpers ------------------------------------------------------------------------------
+    def _check(self, rc, what):
+        if rc != MST_OK:
+            msg = lib.mst_last_error(self._h)
+            raise MSTError(f"{what}: {ERRORS.get(rc, rc)}: {msg.decode() if msg else ''}")
+
+    def _t(self, t, n, dtype, name):
+        if t is None:
+            return None
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() == n):
+            raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor of {n} elements, got "
+                             f"{t.device} {t.dtype} {tuple(t.shape)}")
+        return t
+
+    def _new(self, n, dtype=torch.float64):
+        return torch.empty(n, dtype=dtype, device=self.device)
+
+    # -- calls --------------------------------------------------------------------------------
+    def render(self, beta, params: Params, images=True, L=False, stream=None):
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        img = self._new(self.n_pix) if images else None
+        Lt = self._new(self.n_cams * self.nvox) if L else None
+        self._check(lib.mst_render(self._h, _ptr(beta), ctypes.byref(params), _ptr(img), _ptr(Lt), _stream(stream)),
+                    "mst_render")
+        return dict(images=img, L=None if Lt is None else Lt.view(self.n_cams, self.nvox))
+
+    def render_grad(self, beta, params: Params, meas, mask=None, images=True, stream=None):
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        meas = self._t(meas, self.n_pix, torch.float64, "images_meas")
+        mask = self._t(mask, self.n_pix, torch.uint8, "mask")
+        img = self._new(self.n_pix) if images else None
+        grad = self._new(self.nvox)
+        loss = self._new(1)
+        self._check(lib.mst_render_grad(self._h, _ptr(beta), ctypes.byref(params), _ptr(meas), _ptr(mask), _ptr(img),
+                                        _ptr(grad), _ptr(loss), _stream(stream)), "mst_render_grad")
+        return dict(loss=loss, grad=grad, images=img)
+
+    def transmittance(self, beta, grid_dtype: int = 0, stream=None):
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        T = self._new(self.n_cams * self.nvox, torch.float32)
+        self._check(lib.mst_transmittance(self._h, _ptr(beta), int(grid_dtype), _ptr(T), _stream(stream)),
+                    "mst_transmittance")
+        return T.view(self.n_cams, self.nvox)
+
+    def form_images(self, beta, L, grid_dtype: int = 0, stream=None):
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        L = self._t(L.reshape(-1), self.n_cams * self.nvox, torch.float64, "L")
+        img = self._new(self.n_pix)
+        self._check(lib.mst_form_images(self._h, _ptr(beta), int(grid_dtype), _ptr(L), _ptr(img), _stream(stream)),
+                    "mst_form_images")
+        return img
+
+    def surrogate_grad(self, beta, L_ref, beta_ref, params: Params, meas, mask=None, stream=None):
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        L_ref = self._t(L_ref.reshape(-1), self.n_cams * self.nvox, torch.float64, "L_ref")
+        beta_ref = self._t(beta_ref, self.nvox, torch.float32, "beta_ref")
+        meas = self._t(meas, self.n_pix, torch.float64, "images_meas")
+        mask = self._t(mask, self.n_pix, torch.uint8, "mask")
+        img, grad, loss = self._new(self.n_pix), self._new(self.nvox), self._new(1)
+        self._check(lib.mst_surrogate_grad(self._h, _ptr(beta), _ptr(L_ref), _ptr(beta_ref), ctypes.byref(params),
+                                           _ptr(meas), _ptr(mask), _ptr(img), _ptr(grad), _ptr(loss),
+                                           _stream(stream)), "mst_surrogate_grad")
+        return dict(loss=loss, grad=grad, images=img)
+
+    def ray_counts(self, stream=None):
+        Q = self._new(self.n_cams * self.nvox, torch.float32)
+        self._check(lib.mst_ray_counts(self._h, _ptr(Q), _stream(stream)), "mst_ray_counts")
+        return Q.view(self.n_cams, self.nvox)
+
+    def regularizer(self, beta, eta: float = 1.0, grad=None, stream=None):
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        grad = self._t(grad, self.nvox, torch.float64, "grad")
+        psi = self._new(1)
+        self._check(lib.mst_regularizer(self._h, _ptr(beta), float(eta), _ptr(psi), _ptr(grad), _stream(stream)),
+                    "mst_regularizer")
+        return psi
+
+    def set_debug(self, photon_hash=None, photon_skip=None):
+        self._check(lib.mst_set_debug(self._h, _ptr(photon_hash), _ptr(photon_skip)), "mst_set_debug")
+        self._dbg = (photon_hash, photon_skip)  # keep alive while attached
+
+    def stats(self) -> dict:
+        out = np.zeros(NSTATS)
+        self._check(lib.mst_get_stats(self._h, out.ctypes.data_as(ctypes.c_void_p)), "mst_get_stats")
+        return dict(zip(STAT_NAMES, out.tolist()))
+
+    def set_profiling(self, enable: bool = True):
+        self._check(lib.mst_set_profiling(self._h, int(bool(enable))), "mst_set_profiling")
+
+    def phase_times(self) -> dict:
+        """{phase: (ms, launches)} of the last call; needs set_profiling(True) before it."""
+        ms = np.zeros(len(PHASES))
+        n = np.zeros(len(PHASES), dtype=np.int32)
+        self._check(lib.mst_get_phase_times(self._h, ms.ctypes.data_as(ctypes.c_void_p),
+                                            n.ctypes.data_as(ctypes.c_void_p)), "mst_get_phase_times")
+        return {k: (float(a), int(b)) for k, a, b in zip(PHASES, ms, n)}
+
+    def sync(self):
+        self._check(lib.mst_sync(self._h), "mst_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mst_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+from .autograd import RenderLoss, reconstruct  # noqa: E402  (needs `lib` above)

@@ -1,0 +1,636 @@
+// C ABI of the library: argument validation, handle ownership and the order of kernel
+// launches for each call. No computation of the method happens on the host.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "mst_internal.h"
+
+using namespace mst;
+
+namespace {
+
+constexpr int kVersion = 1;
+
+int fail(mst_grid* g, int code, const std::string& msg) {
+    if (g) g->err = msg;
+    return code;
+}
+
+#define MST_CK(expr)                                                                                   \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess) return fail(g, MST_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+// Phase profiler: an event pair on the call's stream around each launch, when enabled.
+void prof_reset(mst_grid* g) {
+    g->ev_next = 0;
+    g->prof_recs.clear();
+}
+
+cudaEvent_t prof_event(mst_grid* g) {
+    if (g->ev_next == g->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        g->ev_pool.push_back(e);
+    }
+    return g->ev_pool[g->ev_next++];
+}
+
+struct Phase {
+    mst_grid* g;
+    int phase;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    Phase(mst_grid* g_, int ph, cudaStream_t s) : g(g_), phase(ph), st(s) {
+        if (g->prof && (a = prof_event(g)) != nullptr) cudaEventRecord(a, st);
+    }
+    ~Phase() {
+        if (!a) return;
+        cudaEvent_t b = prof_event(g);
+        if (!b) return;
+        cudaEventRecord(b, st);
+        g->prof_recs.push_back({phase, a, b});
+    }
+};
+
+bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int check_params(mst_grid* g, const mst_params* p, bool photons) {
+    if (!p) return fail(g, MST_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->albedo >= 0.0 && p->albedo <= 1.0)) return fail(g, MST_ERR_INVALID_ARG, "albedo must be in [0, 1]");
+    if (!(p->g > -1.0 && p->g < 1.0)) return fail(g, MST_ERR_INVALID_ARG, "g must be in (-1, 1)");
+    if (!(p->sun_zenith_rad >= 0.0 && p->sun_zenith_rad < 0.5 * M_PI))
+        return fail(g, MST_ERR_INVALID_ARG, "sun zenith must be in [0, pi/2)");
+    if (!std::isfinite(p->sun_azimuth_rad)) return fail(g, MST_ERR_INVALID_ARG, "sun azimuth must be finite");
+    if (!(p->sun_irradiance >= 0.0 && std::isfinite(p->sun_irradiance)))
+        return fail(g, MST_ERR_INVALID_ARG, "sun irradiance must be finite and >= 0");
+    if (!(p->rr_threshold >= 0.0 && std::isfinite(p->rr_threshold)))
+        return fail(g, MST_ERR_INVALID_ARG, "rr_threshold must be >= 0");
+    if (!(p->rr_survival > 0.0 && p->rr_survival <= 1.0))
+        return fail(g, MST_ERR_INVALID_ARG, "rr_survival must be in (0, 1]");
+    if (p->grid_dtype < 0 || p->grid_dtype > 2) return fail(g, MST_ERR_INVALID_ARG, "unknown grid_dtype");
+    if (p->estimator < 0 || p->estimator > 1) return fail(g, MST_ERR_INVALID_ARG, "unknown estimator");
+    if (p->grad_mode < 0 || p->grad_mode > 1) return fail(g, MST_ERR_INVALID_ARG, "unknown grad_mode");
+    if (p->conditioning < 0 || p->conditioning > 2) return fail(g, MST_ERR_INVALID_ARG, "unknown conditioning");
+    if (!std::isfinite(p->reg_eta)) return fail(g, MST_ERR_INVALID_ARG, "reg_eta must be finite");
+    if (photons) {
+        if (p->n_photons == 0) return fail(g, MST_ERR_INVALID_ARG, "n_photons must be >= 1");
+        if (p->n_photons > kChunk * (uint64_t)kMaxChunks)
+            return fail(g, MST_ERR_INVALID_ARG, "n_photons above the per-call limit (split the call)");
+        if (p->max_events < 1) return fail(g, MST_ERR_INVALID_ARG, "max_events must be >= 1");
+        if (p->max_order < 0) return fail(g, MST_ERR_INVALID_ARG, "max_order must be >= 0");
+        if (p->n_photons_total != 0 && p->n_photons_total < p->n_photons)
+            return fail(g, MST_ERR_INVALID_ARG, "n_photons_total must be 0 or >= n_photons");
+    }
+    return MST_OK;
+}
+
+TransportArgs transport_args(mst_grid* g, const mst_params* p) {
+    TransportArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = g->geo;
+    a.cams = g->cams;
+    const double gg = p->g;
+    a.hg.g = (float)gg;
+    a.hg.k1 = (float)((1.0 - gg * gg) / (4.0 * M_PI));
+    a.hg.a = (float)(1.0 + gg * gg);
+    a.hg.b = (float)(2.0 * gg);
+    a.hg.omg2 = (float)(1.0 - gg * gg);
+    a.hg.omg = (float)(1.0 - gg);
+    a.hg.tg = (float)(2.0 * gg);
+    a.hg.iso = std::fabs(gg) < 1e-6;
+    a.hg.inv2g = a.hg.iso ? 0.f : (float)(1.0 / (2.0 * gg));
+    a.beta = g->bricks;
+    const double th = p->sun_zenith_rad, ph = p->sun_azimuth_rad;
+    a.sun = make_float3((float)(-std::sin(th) * std::cos(ph)), (float)(-std::sin(th) * std::sin(ph)),
+                        (float)(-std::cos(th)));
+    const double N = (double)(p->n_photons_total ? p->n_photons_total : p->n_photons);
+    const double I0 = p->sun_irradiance * std::cos(th) * (double)g->geo.ex * (double)g->geo.ey / N;
+    a.albedo = (float)p->albedo;
+    a.I0 = (float)I0;
+    a.rr_below = (float)(p->rr_threshold * I0);
+    a.rr_survival = (float)p->rr_survival;
+    a.inv_rr_survival = (float)(1.0 / p->rr_survival);
+    a.key = make_uint2((uint32_t)p->seed, (uint32_t)(p->seed >> 32));
+    a.max_order = p->max_order;
+    a.max_events = p->max_events;
+    a.cp = g->cp;
+    a.Lacc = g->Lacc;
+    a.omega = g->omega;
+    a.adj = g->adj;
+    a.gacc = g->gacc;
+    a.stats = g->stats;
+    a.hash = g->dbg_hash;
+    a.skip = g->dbg_skip;
+    return a;
+}
+
+// Runs the photon transport (forward or replay) in chunks; after each chunk the FP32 tiles
+// are folded into the FP64 results.
+int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cudaStream_t st) {
+    TransportArgs a = transport_args(g, p);
+    a.cimg = cimg;
+    const uint64_t n = p->n_photons;
+    const int nchunks = (int)((n + kChunk - 1) / kChunk);
+    MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * nchunks, st));
+    const int est = replay ? 0 : p->estimator;
+    const int blocks = g->sm_count * transport_blocks_per_sm(p->grid_dtype, est, replay);
+    for (int c = 0; c < nchunks; ++c) {
+        const uint64_t base = (uint64_t)c * kChunk;
+        a.first_id = p->photon_offset + base;
+        a.out_base = (uint32_t)base;
+        a.n = (uint32_t)((n - base) < kChunk ? (n - base) : kChunk);
+        a.ticket = g->tickets + c;
+        if (replay) {
+            {
+                Phase ph(g, MST_PH_REPLAY, st);
+                MST_CK(launch_replay(g, a, p->grid_dtype, blocks, st));
+            }
+            Phase ph(g, MST_PH_FOLD, st);
+            MST_CK(launch_fold_grad(g, st));
+        } else {
+            {
+                Phase ph(g, MST_PH_TRANSPORT, st);
+                MST_CK(launch_transport(g, a, p->grid_dtype, est, blocks, st));
+            }
+            if (est == MST_EST_VOXEL) {
+                Phase ph(g, MST_PH_FOLD, st);
+                MST_CK(launch_fold_L(g, st));
+            }
+        }
+    }
+    return MST_OK;
+}
+
+int ensure_q(mst_grid* g, int mode, cudaStream_t st) {
+    if (mode == MST_COND_NONE) return MST_OK;
+    if (!g->Qw) MST_CK(cudaMalloc(&g->Qw, sizeof(float) * (size_t)g->n_cams * g->geo.nvox));
+    if (g->qw_mode != mode) {
+        MST_CK(launch_ray_counts(g, g->Qw, mode, st));
+        g->qw_mode = mode;
+    }
+    return MST_OK;
+}
+
+double rect_solid_angle(double x1, double x2, double y1, double y2) {
+    auto F = [](double x, double y) { return std::atan(x * y / std::sqrt(1.0 + x * x + y * y)); };
+    return F(x2, y2) - F(x1, y2) - F(x2, y1) + F(x1, y1);
+}
+
+double radical_inverse(int base, int i) {
+    double f = 1.0, r = 0.0;
+    while (i > 0) {
+        f /= base;
+        r += f * (i % base);
+        i /= base;
+    }
+    return r;
+}
+
+void free_all(mst_grid* g) {
+    void* ptrs[] = {g->bricks, g->Lacc, g->L64, g->T, g->R, g->bacc, g->gT, g->adj, g->gacc, g->g64,
+                    g->resid, g->lap, g->omega, g->Qw, g->stats, g->tickets};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mst_version(void) { return kVersion; }
+
+void mst_default_params(mst_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->albedo = 0.99;
+    p->g = 0.85;
+    p->sun_irradiance = 1.0;
+    p->rr_threshold = 0.01;
+    p->rr_survival = 0.1;
+    p->n_photons = 1000000;
+    p->seed = 3;
+    p->max_events = 100000;
+    p->estimator = MST_EST_VOXEL;
+    p->grid_dtype = MST_GRID_F32;
+    p->grad_mode = MST_GRAD_SURROGATE;
+    p->conditioning = MST_COND_NONE;
+}
+
+int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, int n_rays, mst_grid** out) {
+    mst_grid* g = nullptr;
+    if (!out) return MST_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d || !cams) return MST_ERR_INVALID_ARG;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return MST_ERR_INVALID_ARG;
+    if ((long long)d->nx * d->ny * d->nz > (1ll << 30)) return MST_ERR_INVALID_ARG;
+    if (!(d->dx > 0 && d->dy > 0 && d->dz > 0) || !std::isfinite(d->dx + d->dy + d->dz) || !finite3(d->origin))
+        return MST_ERR_INVALID_ARG;
+    if (n_cams < 1 || n_cams > MST_MAX_CAMERAS) return MST_ERR_INVALID_ARG;
+    if (n_rays < 1 || n_rays > MST_MAX_SUBPIXEL_RAYS) return MST_ERR_INVALID_ARG;
+    long long total_pix = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const mst_camera& cm = cams[c];
+        if (cm.width < 1 || cm.height < 1 || !(cm.fov_x_rad > 0 && cm.fov_x_rad < M_PI) || !finite3(cm.pos))
+            return MST_ERR_INVALID_ARG;
+        for (int q = 0; q < 9; ++q)
+            if (!std::isfinite(cm.rot[q])) return MST_ERR_INVALID_ARG;
+        for (int u = 0; u < 3; ++u)
+            for (int v = u; v < 3; ++v) {
+                const double* A = cm.rot + 3 * u;
+                const double* B = cm.rot + 3 * v;
+                const double dot = A[0] * B[0] + A[1] * B[1] + A[2] * B[2];
+                if (std::fabs(dot - (u == v ? 1.0 : 0.0)) > 1e-3) return MST_ERR_INVALID_ARG;
+            }
+        total_pix += (long long)cm.width * cm.height;
+    }
+    if (total_pix > (1ll << 30)) return MST_ERR_INVALID_ARG;
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return MST_ERR_NO_DEVICE;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MST_ERR_NO_DEVICE;
+
+    g = new mst_grid();
+    g->device = dev;
+    cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (g->sm_count < 1) g->sm_count = 1;
+    Geo& geo = g->geo;
+    geo.nx = d->nx; geo.ny = d->ny; geo.nz = d->nz;
+    geo.nbx = (d->nx + 7) / 8; geo.nby = (d->ny + 7) / 8; geo.nbz = (d->nz + 7) / 8;
+    geo.hx = (float)d->dx; geo.hy = (float)d->dy; geo.hz = (float)d->dz;
+    geo.ex = (float)(d->nx * d->dx); geo.ey = (float)(d->ny * d->dy); geo.ez = (float)(d->nz * d->dz);
+    geo.nvox = d->nx * d->ny * d->nz;
+    geo.max_steps = d->nx + d->ny + d->nz + 8;
+    for (int a = 0; a < 3; ++a) g->origin[a] = d->origin[a];
+    g->voxel_volume = d->dx * d->dy * d->dz;
+    g->n_cams = n_cams;
+    g->cp = (n_cams + 3) / 4 * 4;
+    g->n_rays = n_rays;
+    g->cams.n = n_cams;
+    int off = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const mst_camera& s = cams[c];
+        Cam& t = g->cams.c[c];
+        t.px = (float)(s.pos[0] - d->origin[0]);
+        t.py = (float)(s.pos[1] - d->origin[1]);
+        t.pz = (float)(s.pos[2] - d->origin[2]);
+        t.rx = (float)s.rot[0]; t.ry = (float)s.rot[1]; t.rz = (float)s.rot[2];
+        t.ux = (float)s.rot[3]; t.uy = (float)s.rot[4]; t.uz = (float)s.rot[5];
+        t.fx = (float)s.rot[6]; t.fy = (float)s.rot[7]; t.fz = (float)s.rot[8];
+        const double tx = std::tan(0.5 * s.fov_x_rad);
+        t.tx = (float)tx;
+        t.ty = (float)(tx * s.height / s.width);
+        t.w = s.width;
+        t.h = s.height;
+        t.pix_off = off;
+        off += s.width * s.height;
+    }
+    g->total_pix = off;
+    g->halton.n = n_rays;
+    for (int r = 0; r < n_rays; ++r) {
+        g->halton.a[r] = (float)radical_inverse(2, r + 1);
+        g->halton.b[r] = (float)radical_inverse(3, r + 1);
+    }
+
+    const size_t nvox = (size_t)geo.nvox, C = (size_t)n_cams;
+    const size_t nbrick_vox = (size_t)geo.nbx * geo.nby * geo.nbz * kBrickVox;
+    struct A {
+        void** p;
+        size_t bytes;
+    } allocs[] = {
+        {&g->bricks, nbrick_vox * 4},
+        {(void**)&g->Lacc, nvox * g->cp * 4},
+        {(void**)&g->L64, C * nvox * 8},
+        {(void**)&g->T, C * nvox * 4},
+        {(void**)&g->R, C * nvox * 4},
+        {(void**)&g->bacc, C * nvox * 4},
+        {(void**)&g->gT, C * nvox * 4},
+        {(void**)&g->adj, nvox * g->cp * 4},
+        {(void**)&g->gacc, nvox * 4},
+        {(void**)&g->g64, nvox * 8},
+        {(void**)&g->resid, (size_t)off * 8},
+        {(void**)&g->lap, nvox * 8},
+        {(void**)&g->omega, (size_t)off * 4},
+        {(void**)&g->stats, MST_NSTATS * 8 + 64},
+        {(void**)&g->tickets, (size_t)kMaxChunks * 4},
+    };
+    for (auto& a : allocs) {
+        if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_all(g);
+            delete g;
+            return MST_ERR_OOM;
+        }
+    }
+    // pixel solid angles for the classic estimator (exact rectangle formula, FP64 on the host)
+    float* om = new float[off];
+    for (int c = 0; c < n_cams; ++c) {
+        const Cam& t = g->cams.c[c];
+        const double tx = std::tan(0.5 * cams[c].fov_x_rad), ty = tx * t.h / t.w;
+        for (int j = 0; j < t.h; ++j)
+            for (int i = 0; i < t.w; ++i) {
+                const double x1 = (2.0 * i / t.w - 1.0) * tx, x2 = (2.0 * (i + 1) / t.w - 1.0) * tx;
+                const double y1 = (2.0 * j / t.h - 1.0) * ty, y2 = (2.0 * (j + 1) / t.h - 1.0) * ty;
+                om[t.pix_off + j * t.w + i] = (float)rect_solid_angle(x1, x2, y1, y2);
+            }
+    }
+    cudaError_t e = cudaMemcpy(g->omega, om, sizeof(float) * off, cudaMemcpyHostToDevice);
+    delete[] om;
+    if (e == cudaSuccess) e = cudaMemset(g->Lacc, 0, nvox * g->cp * 4);
+    if (e == cudaSuccess) e = cudaMemset(g->gacc, 0, nvox * 4);
+    if (e == cudaSuccess) e = cudaMemset(g->stats, 0, MST_NSTATS * 8 + 64);
+    if (e != cudaSuccess) {
+        free_all(g);
+        delete g;
+        return MST_ERR_CUDA;
+    }
+    *out = g;
+    return MST_OK;
+}
+
+void mst_destroy(mst_grid* g) {
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+    free_all(g);
+    delete g;
+}
+
+int mst_render(mst_grid* g, const float* beta, const mst_params* p, double* images, double* L, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta) return fail(g, MST_ERR_INVALID_ARG, "beta is NULL");
+    int rc = check_params(g, p, true);
+    if (rc) return rc;
+    if (p->estimator == MST_EST_CLASSIC && L) return fail(g, MST_ERR_INVALID_ARG, "L is not defined for the classic estimator");
+    DeviceGuard dg(g->device);
+    cudaStream_t st = as_stream(stream);
+    prof_reset(g);
+    {
+        Phase ph(g, MST_PH_STAGE, st);
+        MST_CK(launch_stage(g, beta, p->grid_dtype, st));
+    }
+    MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
+    const size_t nL = (size_t)g->n_cams * g->geo.nvox;
+    if (p->estimator == MST_EST_CLASSIC) {
+        if (!images) return MST_OK;
+        MST_CK(cudaMemsetAsync(images, 0, sizeof(double) * g->total_pix, st));
+        return run_photons(g, p, false, images, st);
+    }
+    MST_CK(cudaMemsetAsync(g->L64, 0, sizeof(double) * nL, st));
+    rc = run_photons(g, p, false, nullptr, st);
+    if (rc) return rc;
+    if (L) MST_CK(cudaMemcpyAsync(L, g->L64, sizeof(double) * nL, cudaMemcpyDeviceToDevice, st));
+    if (images) {
+        {
+            Phase ph(g, MST_PH_LOS, st);
+            MST_CK(launch_los(g, p->grid_dtype, g->L64, nullptr, nullptr, beta, g->T, g->R, st));
+        }
+        {
+            Phase ph(g, MST_PH_IMAGES, st);
+            MST_CK(launch_images(g, g->R, images, nullptr, nullptr, nullptr, nullptr, st));
+        }
+    }
+    return MST_OK;
+}
+
+int mst_render_grad(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const uint8_t* mask,
+                    double* images, double* grad, double* loss, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta || !meas || !grad) return fail(g, MST_ERR_INVALID_ARG, "beta, images_meas and grad are required");
+    int rc = check_params(g, p, true);
+    if (rc) return rc;
+    if (p->estimator != MST_EST_VOXEL) return fail(g, MST_ERR_UNSUPPORTED, "gradients need the voxel estimator");
+    DeviceGuard dg(g->device);
+    cudaStream_t st = as_stream(stream);
+    prof_reset(g);
+    const size_t nL = (size_t)g->n_cams * g->geo.nvox;
+    double* lossp = loss ? loss : g->stats + MST_NSTATS;
+    {
+        Phase ph(g, MST_PH_STAGE, st);
+        MST_CK(launch_stage(g, beta, p->grid_dtype, st));
+    }
+    MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
+    MST_CK(cudaMemsetAsync(g->L64, 0, sizeof(double) * nL, st));
+    rc = run_photons(g, p, false, nullptr, st);
+    if (rc) return rc;
+    {
+        Phase ph(g, MST_PH_LOS, st);
+        MST_CK(launch_los(g, p->grid_dtype, g->L64, nullptr, nullptr, beta, g->T, g->R, st));
+    }
+    MST_CK(cudaMemsetAsync(lossp, 0, sizeof(double), st));
+    {
+        Phase ph(g, MST_PH_IMAGES, st);
+        MST_CK(launch_images(g, g->R, images, meas, mask, g->resid, lossp, st));
+    }
+    MST_CK(cudaMemsetAsync(g->bacc, 0, sizeof(float) * nL, st));
+    {
+        Phase ph(g, MST_PH_BACKPROJECT, st);
+        MST_CK(launch_backproject(g, g->resid, g->bacc, st));
+    }
+    MST_CK(cudaMemsetAsync(g->gT, 0, sizeof(float) * nL, st));
+    {
+        Phase ph(g, MST_PH_LOS_ADJOINT, st);
+        MST_CK(launch_los_adjoint(g, g->R, g->bacc, g->gT, st));
+    }
+    if (p->grad_mode == MST_GRAD_SURROGATE) {
+        rc = ensure_q(g, p->conditioning, st);
+        if (rc) return rc;
+        {
+            Phase ph(g, MST_PH_COMBINE, st);
+            MST_CK(launch_combine_surrogate(g, g->L64, nullptr, beta, beta, g->T, g->bacc, g->gT,
+                                            p->conditioning ? g->Qw : nullptr, grad, st));
+        }
+    } else {
+        {
+            Phase ph(g, MST_PH_COMBINE, st);
+            MST_CK(launch_adjoint_tiles(g, g->T, g->bacc, g->adj, st));
+        }
+        MST_CK(cudaMemsetAsync(g->g64, 0, sizeof(double) * g->geo.nvox, st));
+        rc = run_photons(g, p, true, nullptr, st);
+        if (rc) return rc;
+        {
+            Phase ph(g, MST_PH_COMBINE, st);
+            MST_CK(launch_combine_full(g, g->gT, g->g64, grad, st));
+        }
+    }
+    if (p->reg_eta != 0.0) {
+        Phase ph(g, MST_PH_COMBINE, st);
+        MST_CK(launch_regularizer(g, beta, p->reg_eta, g->lap, g->stats + MST_NSTATS + 1, lossp, grad, st));
+    }
+    return MST_OK;
+}
+
+int mst_transmittance(mst_grid* g, const float* beta, int dtype, float* T, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta || !T) return fail(g, MST_ERR_INVALID_ARG, "beta and T are required");
+    if (dtype < 0 || dtype > 2) return fail(g, MST_ERR_INVALID_ARG, "unknown grid_dtype");
+    DeviceGuard dg(g->device);
+    cudaStream_t st = as_stream(stream);
+    prof_reset(g);
+    {
+        Phase ph(g, MST_PH_STAGE, st);
+        MST_CK(launch_stage(g, beta, dtype, st));
+    }
+    {
+        Phase ph(g, MST_PH_LOS, st);
+        MST_CK(launch_los(g, dtype, nullptr, nullptr, nullptr, beta, T, nullptr, st));
+    }
+    return MST_OK;
+}
+
+int mst_form_images(mst_grid* g, const float* beta, int dtype, const double* L, double* images, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta || !L || !images) return fail(g, MST_ERR_INVALID_ARG, "beta, L and images are required");
+    if (dtype < 0 || dtype > 2) return fail(g, MST_ERR_INVALID_ARG, "unknown grid_dtype");
+    DeviceGuard dg(g->device);
+    cudaStream_t st = as_stream(stream);
+    prof_reset(g);
+    {
+        Phase ph(g, MST_PH_STAGE, st);
+        MST_CK(launch_stage(g, beta, dtype, st));
+    }
+    {
+        Phase ph(g, MST_PH_LOS, st);
+        MST_CK(launch_los(g, dtype, L, nullptr, nullptr, beta, g->T, g->R, st));
+    }
+    {
+        Phase ph(g, MST_PH_IMAGES, st);
+        MST_CK(launch_images(g, g->R, images, nullptr, nullptr, nullptr, nullptr, st));
+    }
+    return MST_OK;
+}
+
+int mst_surrogate_grad(mst_grid* g, const float* beta, const double* L_ref, const float* beta_ref, const mst_params* p,
+                       const double* meas, const uint8_t* mask, double* images, double* grad, double* loss,
+                       void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta || !L_ref || !beta_ref || !meas || !grad)
+        return fail(g, MST_ERR_INVALID_ARG, "beta, L_ref, beta_ref, images_meas and grad are required");
+    int rc = check_params(g, p, false);
+    if (rc) return rc;
+    DeviceGuard dg(g->device);
+    cudaStream_t st = as_stream(stream);
+    prof_reset(g);
+    const size_t nL = (size_t)g->n_cams * g->geo.nvox;
+    double* lossp = loss ? loss : g->stats + MST_NSTATS;
+    {
+        Phase ph(g, MST_PH_STAGE, st);
+        MST_CK(launch_stage(g, beta, p->grid_dtype, st));
+    }
+    {
+        Phase ph(g, MST_PH_LOS, st);
+        MST_CK(launch_los(g, p->grid_dtype, L_ref, nullptr, beta_ref, beta, g->T, g->R, st));
+    }
+    MST_CK(cudaMemsetAsync(lossp, 0, sizeof(double), st));
+    {
+        Phase ph(g, MST_PH_IMAGES, st);
+        MST_CK(launch_images(g, g->R, images, meas, mask, g->resid, lossp, st));
+    }
+    MST_CK(cudaMemsetAsync(g->bacc, 0, sizeof(float) * nL, st));
+    {
+        Phase ph(g, MST_PH_BACKPROJECT, st);
+        MST_CK(launch_backproject(g, g->resid, g->bacc, st));
+    }
+    MST_CK(cudaMemsetAsync(g->gT, 0, sizeof(float) * nL, st));
+    {
+        Phase ph(g, MST_PH_LOS_ADJOINT, st);
+        MST_CK(launch_los_adjoint(g, g->R, g->bacc, g->gT, st));
+    }
+    rc = ensure_q(g, p->conditioning, st);
+    if (rc) return rc;
+    {
+        Phase ph(g, MST_PH_COMBINE, st);
+        MST_CK(launch_combine_surrogate(g, L_ref, nullptr, beta_ref, beta, g->T, g->bacc, g->gT,
+                                        p->conditioning ? g->Qw : nullptr, grad, st));
+    }
+    if (p->reg_eta != 0.0) {
+        Phase ph(g, MST_PH_COMBINE, st);
+        MST_CK(launch_regularizer(g, beta, p->reg_eta, g->lap, g->stats + MST_NSTATS + 1, lossp, grad, st));
+    }
+    return MST_OK;
+}
+
+int mst_ray_counts(mst_grid* g, float* Q, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!Q) return fail(g, MST_ERR_INVALID_ARG, "Q is NULL");
+    DeviceGuard dg(g->device);
+    MST_CK(launch_ray_counts(g, Q, 0, as_stream(stream)));
+    return MST_OK;
+}
+
+int mst_regularizer(mst_grid* g, const float* beta, double eta, double* psi, double* grad, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta) return fail(g, MST_ERR_INVALID_ARG, "beta is NULL");
+    if (!std::isfinite(eta)) return fail(g, MST_ERR_INVALID_ARG, "eta must be finite");
+    DeviceGuard dg(g->device);
+    double* ps = psi ? psi : g->stats + MST_NSTATS + 1;
+    MST_CK(launch_regularizer(g, beta, eta, g->lap, ps, nullptr, grad, as_stream(stream)));
+    return MST_OK;
+}
+
+int mst_set_debug(mst_grid* g, uint32_t* hash, const uint8_t* skip) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    g->dbg_hash = hash;
+    g->dbg_skip = skip;
+    return MST_OK;
+}
+
+int mst_get_stats(mst_grid* g, double* out) {
+    if (!g || !out) return MST_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    MST_CK(cudaDeviceSynchronize());
+    MST_CK(cudaMemcpy(out, g->stats, sizeof(double) * MST_NSTATS, cudaMemcpyDeviceToHost));
+    return MST_OK;
+}
+
+int mst_set_profiling(mst_grid* g, int enable) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    g->prof = enable != 0;
+    prof_reset(g);
+    return MST_OK;
+}
+
+int mst_get_phase_times(mst_grid* g, double* ms, int* launches) {
+    if (!g || !ms) return MST_ERR_INVALID_ARG;
+    if (!g->prof) return fail(g, MST_ERR_INVALID_ARG, "profiling is off (mst_set_profiling)");
+    DeviceGuard dg(g->device);
+    MST_CK(cudaDeviceSynchronize());
+    for (int i = 0; i < MST_NPHASES; ++i) {
+        ms[i] = 0.0;
+        if (launches) launches[i] = 0;
+    }
+    for (const auto& r : g->prof_recs) {
+        float t = 0.f;
+        MST_CK(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.phase] += (double)t;
+        if (launches) launches[r.phase] += 1;
+    }
+    return MST_OK;
+}
+
+int mst_sync(mst_grid* g) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    MST_CK(cudaDeviceSynchronize());
+    MST_CK(cudaGetLastError());
+    return MST_OK;
+}
+
+const char* mst_last_error(mst_grid* g) { return g ? g->err.c_str() : "null handle"; }
+
+}  // extern "C"

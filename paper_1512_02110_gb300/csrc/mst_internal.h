@@ -1,0 +1,116 @@
+// Host-side handle and kernel argument blocks shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mst.h"
+#include "mst_dev.cuh"
+
+namespace mst {
+
+// Photons per transport launch. Each launch accumulates into FP32 tiles that are then folded
+// into the FP64 results and cleared, which bounds the number of FP32 additions per bin.
+constexpr uint64_t kChunk = 1ull << 22;
+constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
+constexpr int kMaxChunks = 4096;
+
+struct TransportArgs {
+    Geo g;
+    CamSet cams;
+    HG hg;
+    const void* beta;          // staged bricks
+    float3 sun;                // photon direction at launch
+    float albedo, I0, rr_below, rr_survival, inv_rr_survival;
+    uint2 key;
+    uint64_t first_id;         // global id of chunk photon 0
+    uint32_t n;                // photons in this chunk
+    uint32_t out_base;         // call-relative index of chunk photon 0 (hash / skip arrays)
+    int max_order, max_events;
+    int cp;                    // padded camera stride of the [nvox][cp] tiles (multiple of 4)
+    float* Lacc;               // [nvox][cp] FP32 accumulator (voxel estimator)
+    double* cimg;              // classic images (classic estimator)
+    const float* omega;        // [total pix] pixel solid angles (classic estimator)
+    const float* adj;          // [nvox][cp] a_c(k) = T_c(k) b_c(k) (replay)
+    float* gacc;               // [nvox] FP32 gradient accumulator (replay)
+    double* stats;             // [MST_NSTATS]
+    uint32_t* hash;            // per-photon checksum or NULL
+    const uint8_t* skip;       // per-photon skip mask or NULL
+    unsigned int* ticket;      // per-chunk photon ticket
+};
+
+}  // namespace mst
+
+struct mst_grid {
+    int device = 0;
+    int sm_count = 0;
+    mst::Geo geo{};
+    mst::CamSet cams{};
+    mst::Halton halton{};
+    int n_cams = 0, cp = 0, total_pix = 0, n_rays = 0;
+    double origin[3] = {0, 0, 0};
+    double voxel_volume = 0;
+
+    // device buffers owned by the handle
+    void* bricks = nullptr;       // nbricks * 512 * 4 bytes
+    float* Lacc = nullptr;        // [nvox][cp]
+    double* L64 = nullptr;        // [C][nvox]
+    float* T = nullptr;           // [C][nvox]
+    float* R = nullptr;           // [C][nvox]  L_c T_c
+    float* bacc = nullptr;        // [C][nvox]  Pi_c^T (2 r_c)
+    float* gT = nullptr;          // [C][nvox]  W_c^T (L T b)
+    float* adj = nullptr;         // [nvox][cp] T_c b_c
+    float* gacc = nullptr;        // [nvox]
+    double* g64 = nullptr;        // [nvox]
+    double* resid = nullptr;      // [total_pix] 2 M (i - i_meas)
+    double* lap = nullptr;        // [nvox] Lap beta
+    float* omega = nullptr;       // [total_pix]
+    float* Qw = nullptr;          // [C][nvox] conditioning weights for qw_mode
+    int qw_mode = -1;
+    double* stats = nullptr;      // [MST_NSTATS]
+    unsigned int* tickets = nullptr;  // [kMaxChunks]
+
+    // phase profiler: event pairs recorded on the call's stream
+    struct ProfRec {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+    std::vector<ProfRec> prof_recs;
+
+    uint32_t* dbg_hash = nullptr;
+    const uint8_t* dbg_skip = nullptr;
+    std::string err;
+};
+
+namespace mst {
+
+// launchers (all enqueue on `st`; return cudaGetLastError())
+cudaError_t launch_stage(const mst_grid* g, const float* beta, int dtype, cudaStream_t st);
+cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int estimator, int blocks,
+                             cudaStream_t st);
+cudaError_t launch_replay(const mst_grid* g, const TransportArgs& a, int dtype, int blocks, cudaStream_t st);
+cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st);
+cudaError_t launch_fold_grad(const mst_grid* g, cudaStream_t st);
+cudaError_t launch_los(const mst_grid* g, int dtype, const double* L, const double* jfix, const float* beta_ref,
+                       const float* beta, float* T_out, float* R_out, cudaStream_t st);
+cudaError_t launch_images(const mst_grid* g, const float* R, double* images, const double* meas, const uint8_t* mask,
+                          double* resid, double* loss, cudaStream_t st);
+cudaError_t launch_backproject(const mst_grid* g, const double* resid, float* bacc, cudaStream_t st);
+cudaError_t launch_los_adjoint(const mst_grid* g, const float* R, const float* bacc, float* gT, cudaStream_t st);
+cudaError_t launch_ray_counts(const mst_grid* g, float* Q, int mode, cudaStream_t st);
+cudaError_t launch_adjoint_tiles(const mst_grid* g, const float* T, const float* bacc, float* adj, cudaStream_t st);
+cudaError_t launch_combine_surrogate(const mst_grid* g, const double* Lsrc, const double* jfix, const float* beta_ref,
+                                     const float* beta, const float* T, const float* bacc, const float* gT,
+                                     const float* Qw, double* grad, cudaStream_t st);
+cudaError_t launch_combine_full(const mst_grid* g, const float* gT, const double* gL, double* grad, cudaStream_t st);
+cudaError_t launch_regularizer(const mst_grid* g, const float* beta, double eta, double* lap, double* psi,
+                               double* loss, double* grad, cudaStream_t st);
+int transport_blocks_per_sm(int dtype, int estimator, bool replay);
+
+}  // namespace mst

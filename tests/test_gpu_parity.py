@@ -1,0 +1,279 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances (derived from the arithmetic: FP32 walks and weights, FP64 final sums):
+  deterministic ray kernels (T, images from a given L, surrogate gradient): 1e-4 relative
+    per element where the value is not negligible, FP32 walk lengths carry ~1e-6 relative.
+  MC forward on photons whose path checksum agrees on both sides: 1e-4 relative per L bin
+    and per pixel (spec tolerance); photons whose FP32/FP64 face or roulette
+    decisions differ are excluded from both sides through the skip mask.
+  gradients: 1e-3 relative L2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import dev, f32_scene, gpu_hashes, max_rel, need_gpu, quantised, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def _small_scene():
+    shape, h = (12, 10, 9), (40.0, 45.0, 50.0)
+    beta = synth.blob_field(shape, h, 3, (60.0, 150.0), 15 * synth.KM, 0.02 * synth.KM, seed=5)
+    pos = [(250.0, 230.0, 1.0), (120.0, 300.0, 230.0), (-60.0, 200.0, 210.0)]
+    rots = [synth.look_up_rot(), synth.look_at_rot([0.3, -0.2, 1.0]), synth.look_at_rot([1.0, 0.1, 0.2])]
+    cams = synth.make_cameras(pos, 24, 20, 60.0, rots=rots)
+    return synth.make_scene(shape, h, beta, cams)
+
+
+SCENES = {"blobs16": lambda: synth.cfg_blobs16()[0], "small": _small_scene,
+          "lognormal32": lambda: synth.cfg_lognormal32()[0]}
+
+
+# ------------------------------------------------------------------------------------------
+# deterministic kernels fed identical inputs
+
+
+@pytest.mark.parametrize("name", ["blobs16", "small", "lognormal32"])
+def test_transmittance(m, name):
+    sc = f32_scene(SCENES[name]())
+    grid = m.Grid.from_scene(sc)
+    T = grid.transmittance(dev(sc.beta, np.float32)).cpu().numpy()
+    tau, T_or = oracle.transmittance(sc)
+    err = np.abs(T - T_or) / np.maximum(T_or, 1e-30)
+    tol = 2e-5 * np.maximum(tau, 1.0) + 2e-6
+    assert np.all(err <= tol), (float(np.max(err / tol)), name)
+
+
+@pytest.mark.parametrize("name", ["blobs16", "small"])
+def test_images_from_given_L(m, name):
+    sc = f32_scene(SCENES[name]())
+    p = synth.Params(n_photons=20_000, seed=11)
+    L = oracle.render(sc, p)["L"]
+    _, T = oracle.transmittance(sc)
+    ref = oracle.images(sc, L, T)
+    grid = m.Grid.from_scene(sc)
+    img = grid.form_images(dev(sc.beta, np.float32), dev(L, np.float64)).cpu().numpy()
+    assert max_rel(img, ref, 1e-3 * np.abs(ref).max()) < 1e-4
+
+
+def test_ray_counts(m):
+    sc = f32_scene(_small_scene())
+    Q = m.Grid.from_scene(sc).ray_counts().cpu().numpy()
+    ref = oracle.ray_counts(sc)
+    diff = np.abs(Q - ref)
+    assert diff.max() <= 2  # only rays grazing a voxel edge can be counted differently
+    assert np.mean(diff == 0) > 0.999
+
+
+def test_regularizer(m, torch):
+    sc = f32_scene(_small_scene())
+    grid = m.Grid.from_scene(sc)
+    g = torch.zeros(sc.nvox, dtype=torch.float64, device="cuda")
+    psi = grid.regularizer(dev(sc.beta, np.float32), 0.7, g)
+    psi_or, g_or = oracle.laplacian(sc)
+    assert abs(psi.item() - psi_or) <= 1e-12 * psi_or
+    assert rel_l2(g.cpu().numpy(), 0.7 * g_or) < 1e-12
+
+
+@pytest.mark.parametrize("cond", ["none", "inv_count"])
+def test_surrogate_gradient(m, cond):
+    sc0 = f32_scene(synth.cfg_blobs16()[0])
+    p = synth.Params(n_photons=30_000, seed=3)
+    L_ref = oracle.render(sc0, p)["L"]
+    beta_ref = sc0.beta.copy()
+    meas = oracle.forward_images(sc0, p.replace(seed=4))[0]
+    beta = synth.smoothed(beta_ref, sc0.shape, 0.3).astype(np.float32).astype(np.float64)
+    sc = sc0.with_beta(beta)
+    mask = (np.arange(sc.n_pix) % 5 != 0).astype(np.uint8)
+    ref = oracle.surrogate_grad(sc, L_ref, beta_ref, meas, mask, cond, eta=0.3)
+    grid = m.Grid.from_scene(sc)
+    out = grid.surrogate_grad(dev(beta, np.float32), dev(L_ref, np.float64), dev(beta_ref, np.float32),
+                              m.make_params(conditioning=cond, reg_eta=0.3), dev(meas, np.float64),
+                              dev(mask, np.uint8))
+    assert max_rel(out["images"].cpu().numpy(), ref["images"], 1e-3 * np.abs(ref["images"]).max()) < 1e-4
+    assert abs(out["loss"].item() - ref["loss"]) < 1e-4 * ref["loss"]
+    assert rel_l2(out["grad"].cpu().numpy(), ref["grad"]) < 1e-3
+
+
+# ------------------------------------------------------------------------------------------
+# Monte-Carlo forward: same Philox streams, per-photon checksums
+
+
+def _diverged(m, grid, sc, params, beta_dev):
+    h_gpu = gpu_hashes(m, grid, beta_dev, m.make_params(params), params.n_photons)
+    h_or = oracle.render(sc, params, want_L=False, hashes=True)["hash"]
+    return (h_gpu != h_or).astype(np.uint8), h_gpu, h_or
+
+
+def _forward_parity(m, torch, sc, params, kind="f32", tol=1e-4):
+    sc = sc.with_beta(quantised(sc.beta, kind))
+    grid = m.Grid.from_scene(sc)
+    beta_dev = dev(sc.beta, np.float32)
+    mp = m.make_params(params, grid_dtype=kind)
+    skip, h_gpu, h_or = _diverged(m, grid, sc, params, beta_dev)
+    frac = skip.mean()
+    assert frac < 2e-3, frac
+    skip_dev = dev(skip, np.uint8)
+    grid.set_debug(None, skip_dev)
+    out = grid.render(beta_dev, mp, images=True, L=True)
+    st = grid.stats()
+    grid.set_debug(None, None)
+    ref = oracle.render(sc, params, skip=skip)
+    _, T = oracle.transmittance(sc)
+    img_ref = oracle.images(sc, ref["L"], T)
+    L = out["L"].cpu().numpy()
+    Lr = ref["L"]
+    assert max_rel(L, Lr, 1e-3 * np.abs(Lr).max()) < tol
+    assert max_rel(out["images"].cpu().numpy(), img_ref, 1e-3 * np.abs(img_ref).max()) < tol
+    rs = ref["stats"]
+    for k in ["events", "segments", "traced", "escaped_n", "capped"]:
+        assert st[k] == rs[k], (k, st[k], rs[k])
+    for k in ["esc_xm", "esc_xp", "esc_ym", "esc_yp", "esc_zm", "esc_zp", "absorbed", "launched"]:
+        assert abs(st[k] - rs[k]) <= 1e-5 * rs["launched"], (k, st[k], rs[k])
+    return grid, skip, out
+
+
+def test_forward_blobs16(m, torch):
+    sc, p = synth.cfg_blobs16(100_000)
+    _forward_parity(m, torch, f32_scene(sc), p)
+
+
+def test_forward_small_scene_roulette_and_order(m, torch):
+    sc = _small_scene()
+    p = synth.Params(albedo=0.9, g=0.6, sun_zenith=math.radians(50), sun_azimuth=1.1, n_photons=60_001, seed=77,
+                     rr_threshold=0.2, rr_survival=0.3, max_order=6)
+    _forward_parity(m, torch, f32_scene(sc), p)
+
+
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+def test_forward_half_precision_grid(m, torch, kind):
+    sc, p = synth.cfg_blobs16(50_000)
+    _forward_parity(m, torch, sc, p, kind=kind)
+
+
+def test_forward_isotropic_vertical_sun(m, torch):
+    sc = _small_scene()
+    p = synth.Params(albedo=0.95, g=0.0, sun_zenith=0.0, n_photons=30_000, seed=5)
+    _forward_parity(m, torch, f32_scene(sc), p)
+
+
+def test_zero_albedo_and_single_photon(m, torch):
+    sc = f32_scene(_small_scene())
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    out = grid.render(beta, m.make_params(synth.Params(albedo=0.0, n_photons=5000)), images=True, L=True)
+    assert float(out["L"].abs().max()) == 0.0 and float(out["images"].abs().max()) == 0.0
+    p1 = synth.Params(n_photons=1, photon_offset=123456, n_photons_total=1000, seed=9)
+    h = gpu_hashes(m, grid, beta, m.make_params(p1), 1)
+    assert h[0] == oracle.render(sc, p1, want_L=False, hashes=True)["hash"][0]
+
+
+def test_chunk_boundary_and_ragged_count(m, torch):
+    """More photons than one transport launch takes (2^22), with a ragged tail."""
+    shape, h = (4, 4, 4), (60.0, 60.0, 60.0)
+    beta = synth.blob_field(shape, h, 1, (60.0, 90.0), 8 * synth.KM, 0.1 * synth.KM, seed=2)
+    sc = f32_scene(synth.make_scene(shape, h, beta, synth.make_cameras([(121.0, 117.0, 1.0)], 8, 8, 70.0)))
+    p = synth.Params(albedo=0.99, g=0.85, sun_zenith=0.5, n_photons=(1 << 22) + 1003, seed=17)
+    _forward_parity(m, torch, sc, p)
+
+
+def test_photon_offset_split(m, torch):
+    sc, p = synth.cfg_blobs16(40_000)
+    sc = f32_scene(sc)
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    full = grid.render(beta, m.make_params(p), images=False, L=True)["L"].cpu().numpy()
+    a = grid.render(beta, m.make_params(p, n_photons=15_000, n_photons_total=40_000), images=False,
+                    L=True)["L"].cpu().numpy()
+    b = grid.render(beta, m.make_params(p, n_photons=25_000, photon_offset=15_000, n_photons_total=40_000),
+                    images=False, L=True)["L"].cpu().numpy()
+    assert max_rel(a + b, full, 1e-3 * np.abs(full).max()) < 1e-5
+
+
+def test_classic_estimator(m, torch):
+    shape, h = (10, 10, 8), (50.0, 50.0, 50.0)
+    beta = synth.blob_field(shape, h, 2, (80.0, 150.0), 6 * synth.KM, 0.2 * synth.KM, seed=8)
+    cams = synth.make_cameras([(262.0, 238.0, -40.0), (130.0, 140.0, -25.0)], 12, 12, 60.0)
+    sc = f32_scene(synth.make_scene(shape, h, beta, cams))
+    p = synth.Params(albedo=0.99, g=0.7, sun_zenith=0.4, n_photons=50_000, seed=19)
+    grid = m.Grid.from_scene(sc)
+    beta_dev = dev(sc.beta, np.float32)
+    skip, _, _ = _diverged(m, grid, sc, p, beta_dev)
+    grid.set_debug(None, dev(skip, np.uint8))
+    img = grid.render(beta_dev, m.make_params(p, estimator="classic"), images=True)["images"].cpu().numpy()
+    grid.set_debug(None, None)
+    ref = oracle.render(sc, p, want_L=False, classic=True, skip=skip)["classic"]
+    assert max_rel(img, ref, 1e-3 * np.abs(ref).max()) < 2e-4
+
+
+# ------------------------------------------------------------------------------------------
+# gradients through mst_render_grad
+
+
+def _grad_case():
+    sc, p = synth.cfg_blobs16(30_000)
+    sc = f32_scene(sc)
+    meas = oracle.forward_images(sc, p.replace(seed=4))[0]
+    beta = synth.smoothed(sc.beta, sc.shape, 0.3).astype(np.float32).astype(np.float64)
+    mask = (np.arange(sc.n_pix) % 7 != 3).astype(np.uint8)
+    return sc.with_beta(beta), p, meas, mask
+
+
+def test_full_gradient(m, torch):
+    sc, p, meas, mask = _grad_case()
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    skip, _, _ = _diverged(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render_grad(beta, m.make_params(p, grad_mode="full", reg_eta=0.05), dev(meas, np.float64),
+                           dev(mask, np.uint8))
+    grid.set_debug(None, None)
+    ref = oracle.full_grad(sc, p, meas, mask, eta=0.05, skip=skip)
+    assert max_rel(out["images"].cpu().numpy(), ref["images"], 1e-3 * np.abs(ref["images"]).max()) < 1e-4
+    assert abs(out["loss"].item() - ref["loss"]) < 1e-4 * ref["loss"]
+    assert rel_l2(out["grad"].cpu().numpy(), ref["grad"]) < 1e-3
+
+
+def test_surrogate_mode_of_render_grad(m, torch):
+    sc, p, meas, mask = _grad_case()
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    skip, _, _ = _diverged(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render_grad(beta, m.make_params(p, grad_mode="surrogate", conditioning="inv_count"),
+                           dev(meas, np.float64), dev(mask, np.uint8))
+    grid.set_debug(None, None)
+    L = oracle.render(sc, p, skip=skip)["L"]
+    ref = oracle.surrogate_grad(sc, L, sc.beta, meas, mask, "inv_count")
+    assert abs(out["loss"].item() - ref["loss"]) < 1e-4 * ref["loss"]
+    assert rel_l2(out["grad"].cpu().numpy(), ref["grad"]) < 1e-3
+
+
+def test_invalid_arguments_raise(m, torch):
+    sc = f32_scene(_small_scene())
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    with pytest.raises(m.MSTError, match="invalid"):
+        grid.render(beta, m.make_params(g=1.0))
+    with pytest.raises(m.MSTError, match="invalid"):
+        grid.render(beta, m.make_params(estimator="classic"), L=True)
+    with pytest.raises(m.MSTError, match="unsupported"):
+        grid.render_grad(beta, m.make_params(estimator="classic"), dev(np.zeros(sc.n_pix), np.float64))
+    with pytest.raises(ValueError):
+        grid.render(dev(sc.beta, np.float64), m.make_params())
+    grid.sync()
