@@ -7,8 +7,8 @@ def need_gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_1512_02110_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1512_02110_gb300 as m
     return m
 

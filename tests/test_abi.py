@@ -14,8 +14,8 @@ HEADER = os.path.join(ROOT, "include", "mst.h")
 
 @pytest.fixture(scope="module")
 def pkg():
-    from paper_1512_02110_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1512_02110_gb300 as m
     return m
 
