@@ -175,7 +175,8 @@ int mst_surrogate_grad(mst_grid *g, const float *beta_dev, const double *L_ref_d
                        const mst_params *p, const double *images_meas_dev, const uint8_t *mask_dev,
                        double *images_dev, double *grad_dev, double *loss_dev, void *stream);
 
-/* Q_c(k): number of sub-pixel rays with a positive chord in voxel k (Sec. 6).
+/* Q_c(k): number of sub-pixel rays through voxel k (Sec. 6); a ray counts when its chord in
+ * the voxel is at least 1e-4 of the smallest voxel edge.
  * Q_dev [C][nvox] float. */
 int mst_ray_counts(mst_grid *g, float *Q_dev, void *stream);
 

@@ -692,19 +692,24 @@ void or_backproject(const or_scene *s, const double *rr, double *b) {
     }
 }
 
-typedef struct { double *q; } cnt_ctx;
+typedef struct { double *q; double eps; } cnt_ctx;
 static void cnt_visit(void *cc, long k, double len) {
-    if (len > 0) ((cnt_ctx *)cc)->q[k] += 1.0;
+    cnt_ctx *c = (cnt_ctx *)cc;
+    if (len >= c->eps) c->q[k] += 1.0;
 }
 
-/* Q_c(k): number of sub-pixel rays with a positive chord in voxel k (Sec. 6) */
+/* Q_c(k): number of sub-pixel rays through voxel k (Sec. 6). A ray counts when its chord in
+ * the voxel is at least 1e-4 of the smallest voxel edge, so rays that only graze an edge or a
+ * corner (chord ~ 0) are not counted. */
 void or_ray_counts(const or_scene *s, double *Q) {
     const long nvox = nvox_of(s);
     memset(Q, 0, sizeof(double) * (size_t)s->n_cams * nvox);
     for (int c = 0; c < s->n_cams; ++c) {
         const int W = s->cam_w[c], H = s->cam_h[c];
         const double *Pc = s->cam_pos + 3 * c;
-        cnt_ctx cc = {Q + (long)c * nvox};
+        double hmin = s->h[0] < s->h[1] ? s->h[0] : s->h[1];
+        if (s->h[2] < hmin) hmin = s->h[2];
+        cnt_ctx cc = {Q + (long)c * nvox, 1e-4 * hmin};
         for (long p = 0; p < (long)W * H; ++p) {
             int i = (int)(p % W), j = (int)(p / W);
             for (int rho = 1; rho <= s->n_rays; ++rho) {

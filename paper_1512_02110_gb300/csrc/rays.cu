@@ -213,9 +213,11 @@ __global__ void __launch_bounds__(kTB) k_los_adjoint(const Geo g, const CamSet c
     if (stats) flush_count(stats, MST_ST_LOSADJ_SEGMENTS, nseg);
 }
 
-// Q_c(k): number of sub-pixel rays with a positive chord in voxel k
+// Q_c(k): number of sub-pixel rays through voxel k; a ray counts when its chord is at least
+// 1e-4 of the smallest voxel edge (grazing rays with chords ~ 0 are not counted)
 __global__ void __launch_bounds__(kTB) k_ray_counts(const Geo g, const CamSet cs, const Halton hs, float* __restrict__ Q,
                                                     int total_pix) {
+    const float eps = 1e-4f * fminf(g.hx, fminf(g.hy, g.hz));
     const int gp = blockIdx.x * blockDim.x + threadIdx.x;
     if (gp >= total_pix) return;
     const int c = cam_of_pixel(cs, gp);
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kTB) k_ray_counts(const Geo g, const CamSet cs
         for (;;) {
             float tn;
             const int a = walk_axis(w, tn);
-            if (tn - t > 0.f) atomicAdd(qc + lin_index(g, w.ix, w.iy, w.iz), 1.f);
+            if (tn - t >= eps) atomicAdd(qc + lin_index(g, w.ix, w.iy, w.iz), 1.f);
             t = tn;
             if (walk_step(w, g, a) >= 0) break;
         }

@@ -15,7 +15,8 @@ def need_gpu():
 
 def dev(x, dtype):
     import torch
-    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda").contiguous()
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    return torch.from_numpy(a).to("cuda").contiguous()
 
 
 def f32_scene(scene):

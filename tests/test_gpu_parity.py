@@ -76,8 +76,9 @@ def test_ray_counts(m):
     Q = m.Grid.from_scene(sc).ray_counts().cpu().numpy()
     ref = oracle.ray_counts(sc)
     diff = np.abs(Q - ref)
-    assert diff.max() <= 2  # only rays grazing a voxel edge can be counted differently
-    assert np.mean(diff == 0) > 0.999
+    # a count differs only where a chord lies within FP32 rounding of the 1e-4 h threshold
+    assert diff.max() <= 1
+    assert np.mean(diff == 0) > 0.9995
 
 
 def test_regularizer(m, torch):
