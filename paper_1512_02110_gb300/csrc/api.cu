@@ -1,5 +1,6 @@
 // C ABI of the library: argument validation, handle ownership and the order of kernel
 // launches for each call. No computation of the method happens on the host.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -248,6 +249,11 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
         const mst_camera& cm = cams[c];
         if (cm.width < 1 || cm.height < 1 || !(cm.fov_x_rad > 0 && cm.fov_x_rad < M_PI) || !finite3(cm.pos))
             return MST_ERR_INVALID_ARG;
+        // the camera may sit outside the grid, but within 1e6 voxels of it
+        const double hh[3] = {d->dx, d->dy, d->dz};
+        const int nn[3] = {d->nx, d->ny, d->nz};
+        for (int a = 0; a < 3; ++a)
+            if (std::fabs(cm.pos[a] - d->origin[a]) > (nn[a] + 1e6) * hh[a]) return MST_ERR_INVALID_ARG;
         for (int q = 0; q < 9; ++q)
             if (!std::isfinite(cm.rot[q])) return MST_ERR_INVALID_ARG;
         for (int u = 0; u < 3; ++u)
@@ -288,6 +294,25 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
         t.px = (float)(s.pos[0] - d->origin[0]);
         t.py = (float)(s.pos[1] - d->origin[1]);
         t.pz = (float)(s.pos[2] - d->origin[2]);
+        // voxel holding the centre of projection (may be outside the grid) and the offset inside
+        // it, in FP64 here so the device sees the camera to ~1e-6 m
+        const double hh[3] = {d->dx, d->dy, d->dz};
+        const int nn[3] = {d->nx, d->ny, d->nz};
+        int iv[3];
+        float lv[3];
+        bool inside = true;
+        for (int a = 0; a < 3; ++a) {
+            const double x = s.pos[a] - d->origin[a];
+            const double f = std::floor(x / hh[a]);
+            iv[a] = (int)std::max(-1e9, std::min(1e9, f));
+            double off = x - f * hh[a];
+            off = std::min(std::max(off, 0.0), hh[a]);
+            lv[a] = (float)off;
+            if (iv[a] < 0 || iv[a] >= nn[a]) inside = false;
+        }
+        t.ix = iv[0]; t.iy = iv[1]; t.iz = iv[2];
+        t.lx = lv[0]; t.ly = lv[1]; t.lz = lv[2];
+        t.inside = inside ? 1 : 0;
         t.rx = (float)s.rot[0]; t.ry = (float)s.rot[1]; t.rz = (float)s.rot[2];
         t.ux = (float)s.rot[3]; t.uy = (float)s.rot[4]; t.uz = (float)s.rot[5];
         t.fx = (float)s.rot[6]; t.fy = (float)s.rot[7]; t.fz = (float)s.rot[8];

@@ -27,7 +27,10 @@ struct Geo {
 };
 
 struct Cam {
-    float px, py, pz;              // centre of projection, grid-local
+    float px, py, pz;              // centre of projection, grid-local metres
+    int ix, iy, iz;                // voxel holding the centre (may lie outside the grid)
+    float lx, ly, lz;              // offset of the centre inside that voxel
+    int inside;                    // centre inside the grid
     float rx, ry, rz;              // right
     float ux, uy, uz;              // up
     float fx, fy, fz;              // forward
@@ -152,63 +155,106 @@ struct BetaFetch<2> {
 };
 
 // ------------------------------------------------------------------------------------------
-// Voxel walk. t_a is the ray parameter of the next face on axis a; ties go to x, then y, then z.
+// Voxel walk in voxel-local form. A point is (voxel index, offset inside the voxel); the walk
+// keeps, per axis, the distance along the ray from the current point to the next face. A step
+// of length s across axis a subtracts s from the other two axes and resets axis a to h_a/|d_a|,
+// so every quantity stays of the size of one voxel and FP32 keeps ~1e-6 m resolution however
+// large the grid. Ties go to x, then y, then z.
 
 struct Walk {
-    float ox, oy, oz;     // ray origin
-    float vx, vy, vz;     // 1 / direction
-    float tx, ty, tz;     // next face crossing
+    float tx, ty, tz;     // distance to the next face per axis (INF when parallel)
+    float qx, qy, qz;     // h / |d| per axis
+    float ax, ay, az;     // |d| per axis
+    float p0x, p0y, p0z;  // offset at the start (kept on axes the ray does not move along)
     int ix, iy, iz;       // current voxel
     int sx, sy, sz;       // step per axis (0 when the direction component is 0)
     int left;             // face crossings left before the walk is abandoned
 };
 
-__device__ __forceinline__ float face_t(int i, int s, float h, float o, float inv) {
-    return s == 0 ? CUDART_INF_F : (__int2float_rn(i + (s > 0)) * h - o) * inv;
+__device__ __forceinline__ void axis_init(float p, float d, float h, float& t, float& q, float& a, int& s) {
+    if (d > 0.f) {
+        a = d;
+        const float inv = 1.f / d;
+        t = (h - p) * inv;
+        q = h * inv;
+        s = 1;
+    } else if (d < 0.f) {
+        a = -d;
+        const float inv = 1.f / a;
+        t = p * inv;
+        q = h * inv;
+        s = -1;
+    } else {
+        a = 0.f;
+        t = CUDART_INF_F;
+        q = CUDART_INF_F;
+        s = 0;
+    }
 }
 
-__device__ __forceinline__ void walk_init(Walk& w, const Geo& g, float3 o, float3 d, int ix, int iy, int iz) {
-    w.ox = o.x; w.oy = o.y; w.oz = o.z;
+// p: offset of the start point inside voxel (ix, iy, iz), each in [0, h]
+__device__ __forceinline__ void walk_init(Walk& w, const Geo& g, float3 p, float3 d, int ix, int iy, int iz) {
+    axis_init(fminf(fmaxf(p.x, 0.f), g.hx), d.x, g.hx, w.tx, w.qx, w.ax, w.sx);
+    axis_init(fminf(fmaxf(p.y, 0.f), g.hy), d.y, g.hy, w.ty, w.qy, w.ay, w.sy);
+    axis_init(fminf(fmaxf(p.z, 0.f), g.hz), d.z, g.hz, w.tz, w.qz, w.az, w.sz);
+    w.p0x = p.x; w.p0y = p.y; w.p0z = p.z;
     w.ix = ix; w.iy = iy; w.iz = iz;
-    w.sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
-    w.sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
-    w.sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
-    w.vx = 1.f / d.x; w.vy = 1.f / d.y; w.vz = 1.f / d.z;
-    w.tx = face_t(ix, w.sx, g.hx, o.x, w.vx);
-    w.ty = face_t(iy, w.sy, g.hy, o.y, w.vy);
-    w.tz = face_t(iz, w.sz, g.hz, o.z, w.vz);
     w.left = g.max_steps;
 }
 
+// distance to the next face and its axis
 __device__ __forceinline__ int walk_axis(const Walk& w, float& tn) {
     int a = 0;
     tn = w.tx;
     if (w.ty < tn) { a = 1; tn = w.ty; }
     if (w.tz < tn) { a = 2; tn = w.tz; }
+    tn = fmaxf(tn, 0.f);
     return a;
 }
 
 constexpr int kWalkOverflow = 6;
 
-// Crosses the face on axis a. Returns the exit face (0..5: x-, x+, y-, y+, z-, z+) if the
-// walk left the grid, kWalkOverflow if it made more crossings than any straight line through
-// the grid can (only possible with a non-finite direction), else -1.
-__device__ __forceinline__ int walk_step(Walk& w, const Geo& g, int a) {
+// Moves seg along the ray and crosses the face on axis a. Returns the exit face (0..5: x-, x+,
+// y-, y+, z-, z+) if the walk left the grid, kWalkOverflow if it made more crossings than any
+// straight line through the grid can (only possible with a non-finite direction), else -1.
+__device__ __forceinline__ int walk_step(Walk& w, const Geo& g, int a, float seg) {
     if (--w.left < 0) return kWalkOverflow;
     if (a == 0) {
+        w.ty -= seg; w.tz -= seg; w.tx = w.qx;
         w.ix += w.sx;
-        w.tx = face_t(w.ix, w.sx, g.hx, w.ox, w.vx);
         if ((unsigned)w.ix >= (unsigned)g.nx) return w.sx > 0 ? 1 : 0;
     } else if (a == 1) {
+        w.tx -= seg; w.tz -= seg; w.ty = w.qy;
         w.iy += w.sy;
-        w.ty = face_t(w.iy, w.sy, g.hy, w.oy, w.vy);
         if ((unsigned)w.iy >= (unsigned)g.ny) return w.sy > 0 ? 3 : 2;
     } else {
+        w.tx -= seg; w.ty -= seg; w.tz = w.qz;
         w.iz += w.sz;
-        w.tz = face_t(w.iz, w.sz, g.hz, w.oz, w.vz);
         if ((unsigned)w.iz >= (unsigned)g.nz) return w.sz > 0 ? 5 : 4;
     }
     return -1;
+}
+
+__device__ __forceinline__ float axis_local(float t, float a, int s, float h, float p0, float l) {
+    const float v = s > 0 ? h - (t - l) * a : (s < 0 ? (t - l) * a : p0);
+    return fminf(fmaxf(v, 0.f), h);
+}
+
+// offset inside the current voxel of the point a distance l past the current point
+__device__ __forceinline__ float3 walk_local(const Walk& w, const Geo& g, float l) {
+    return make_float3(axis_local(w.tx, w.ax, w.sx, g.hx, w.p0x, l), axis_local(w.ty, w.ay, w.sy, g.hy, w.p0y, l),
+                       axis_local(w.tz, w.az, w.sz, g.hz, w.p0z, l));
+}
+
+__device__ __forceinline__ bool walk_at(const Walk& w, int ix, int iy, int iz) {
+    return w.ix == ix && w.iy == iy && w.iz == iz;
+}
+
+// vector from the point (voxel i, offset p) to the point (voxel j, offset q)
+__device__ __forceinline__ float3 local_delta(const Geo& g, int ix, int iy, int iz, float3 p, int jx, int jy, int jz,
+                                              float3 q) {
+    return make_float3((float)(jx - ix) * g.hx + (q.x - p.x), (float)(jy - iy) * g.hy + (q.y - p.y),
+                       (float)(jz - iz) * g.hz + (q.z - p.z));
 }
 
 __device__ __forceinline__ int coord_vox(float x, float h, int n) {
@@ -216,11 +262,25 @@ __device__ __forceinline__ int coord_vox(float x, float h, int n) {
     return f < 0.f ? 0 : (f > (float)(n - 1) ? n - 1 : (int)f);
 }
 
-// Clips the ray o + t d to the grid box. Returns false if it misses; else the entry
-// parameter t0 >= 0 and the entry voxel.
-__device__ __forceinline__ bool ray_enter(const Geo& g, float3 o, float3 d, float& t0, int& ix, int& iy, int& iz) {
+__device__ __forceinline__ float3 pixel_dir(const Cam& c, float px, float py) {
+    const float x = (2.f * px / (float)c.w - 1.f) * c.tx;
+    const float y = (2.f * py / (float)c.h - 1.f) * c.ty;
+    float3 d = make_float3(c.fx + x * c.rx + y * c.ux, c.fy + x * c.ry + y * c.uy, c.fz + x * c.rz + y * c.uz);
+    const float n = 1.f / sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    return make_float3(d.x * n, d.y * n, d.z * n);
+}
+
+// Start of a ray from a camera: inside the grid it starts at the camera's own voxel and offset;
+// outside, the ray is clipped to the grid box (entry point in grid-local metres). Returns
+// false if it misses the grid.
+__device__ __forceinline__ bool ray_start(const Geo& g, const Cam& c, float3 d, float3& p, int& ix, int& iy, int& iz) {
+    if (c.inside) {
+        ix = c.ix; iy = c.iy; iz = c.iz;
+        p = make_float3(c.lx, c.ly, c.lz);
+        return true;
+    }
     float tn = 0.f, tf = CUDART_INF_F;
-    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z}, hi[3] = {g.ex, g.ey, g.ez};
+    const float oo[3] = {c.px, c.py, c.pz}, dd[3] = {d.x, d.y, d.z}, hi[3] = {g.ex, g.ey, g.ez};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (dd[a] == 0.f) {
@@ -233,19 +293,12 @@ __device__ __forceinline__ bool ray_enter(const Geo& g, float3 o, float3 d, floa
         }
     }
     if (!(tn < tf)) return false;
-    t0 = tn;
-    ix = coord_vox(o.x + tn * d.x, g.hx, g.nx);
-    iy = coord_vox(o.y + tn * d.y, g.hy, g.ny);
-    iz = coord_vox(o.z + tn * d.z, g.hz, g.nz);
+    const float3 e = make_float3(c.px + tn * d.x, c.py + tn * d.y, c.pz + tn * d.z);
+    ix = coord_vox(e.x, g.hx, g.nx);
+    iy = coord_vox(e.y, g.hy, g.ny);
+    iz = coord_vox(e.z, g.hz, g.nz);
+    p = make_float3(e.x - (float)ix * g.hx, e.y - (float)iy * g.hy, e.z - (float)iz * g.hz);
     return true;
-}
-
-__device__ __forceinline__ float3 pixel_dir(const Cam& c, float px, float py) {
-    const float x = (2.f * px / (float)c.w - 1.f) * c.tx;
-    const float y = (2.f * py / (float)c.h - 1.f) * c.ty;
-    float3 d = make_float3(c.fx + x * c.rx + y * c.ux, c.fy + x * c.ry + y * c.uy, c.fz + x * c.rz + y * c.uz);
-    const float n = 1.f / sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-    return make_float3(d.x * n, d.y * n, d.z * n);
 }
 
 __device__ __forceinline__ int cam_of_pixel(const CamSet& cs, int gp) {
@@ -253,6 +306,60 @@ __device__ __forceinline__ int cam_of_pixel(const CamSet& cs, int gp) {
     for (int i = 1; i < cs.n; ++i)
         if (gp >= cs.c[i].pix_off) c = i;
     return c;
+}
+
+// Walks the segment from the point (voxel i, offset p) to the centre of projection of camera c,
+// calling fn(ix, iy, iz, length) for every voxel it crosses. The walk ends in the
+// camera's voxel (last length = distance to the camera inside it) or, for a camera outside the
+// grid, at the grid face; the remaining distance guards both ends against rounding.
+template <typename F>
+__device__ __forceinline__ void walk_to_camera(const Geo& g, const Cam& c, int ix, int iy, int iz, float3 p, F&& fn,
+                                               unsigned long long& nseg) {
+    const float3 lc = make_float3(c.lx, c.ly, c.lz);
+    const float3 v = local_delta(g, ix, iy, iz, p, c.ix, c.iy, c.iz, lc);
+    const float dist = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    if (!(dist > 0.f)) return;
+    const float inv = 1.f / dist;
+    const float3 d = make_float3(v.x * inv, v.y * inv, v.z * inv);
+    Walk w;
+    walk_init(w, g, p, d, ix, iy, iz);
+    float rem = dist;
+    for (;;) {
+        ++nseg;
+        if (walk_at(w, c.ix, c.iy, c.iz)) {
+            const float3 q = walk_local(w, g, 0.f);
+            const float len = (lc.x - q.x) * d.x + (lc.y - q.y) * d.y + (lc.z - q.z) * d.z;
+            fn(w.ix, w.iy, w.iz, fminf(fmaxf(len, 0.f), rem));
+            return;
+        }
+        float seg;
+        const int a = walk_axis(w, seg);
+        if (seg >= rem) {
+            fn(w.ix, w.iy, w.iz, rem);
+            return;
+        }
+        fn(w.ix, w.iy, w.iz, seg);
+        rem -= seg;
+        if (walk_step(w, g, a, seg) >= 0) return;
+    }
+}
+
+// Walks the pixel ray from camera c along d to the grid exit, calling fn(ix, iy, iz, length).
+template <typename F>
+__device__ __forceinline__ void walk_from_camera(const Geo& g, const Cam& c, float3 d, F&& fn,
+                                                 unsigned long long& nseg) {
+    float3 p;
+    int ix, iy, iz;
+    if (!ray_start(g, c, d, p, ix, iy, iz)) return;
+    Walk w;
+    walk_init(w, g, p, d, ix, iy, iz);
+    for (;;) {
+        ++nseg;
+        float seg;
+        const int a = walk_axis(w, seg);
+        fn(w.ix, w.iy, w.iz, seg);
+        if (walk_step(w, g, a, seg) >= 0) return;
+    }
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

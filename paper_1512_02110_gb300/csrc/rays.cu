@@ -29,10 +29,6 @@ __global__ void k_stage(const float* __restrict__ beta, void* __restrict__ brick
     }
 }
 
-__device__ __forceinline__ float3 voxel_centre(const Geo& g, int ix, int iy, int iz) {
-    return make_float3(((float)ix + 0.5f) * g.hx, ((float)iy + 0.5f) * g.hy, ((float)iz + 0.5f) * g.hz);
-}
-
 __device__ __forceinline__ void flush_count(double* stats, int slot, unsigned long long n) {
     n = warp_sumu(n);
     if ((threadIdx.x & 31u) == 0u && n) atomicAdd(stats + slot, (double)n);
@@ -52,28 +48,12 @@ __global__ void __launch_bounds__(kTB) k_los(const Geo g, const CamSet cs, const
     if (idx < total) {
         const int c = (int)(idx / g.nvox), k = (int)(idx - (long long)c * g.nvox);
         const int ix = k % g.nx, iy = (k / g.nx) % g.ny, iz = k / (g.nx * g.ny);
-        const float3 o = voxel_centre(g, ix, iy, iz);
-        const Cam& cm = cs.c[c];
-        float3 d = make_float3(cm.px - o.x, cm.py - o.y, cm.pz - o.z);
-        const float dist = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
         float tau = 0.f;
-        if (dist > 0.f) {
-            const float inv = 1.f / dist;
-            d = make_float3(d.x * inv, d.y * inv, d.z * inv);
-            Walk w;
-            walk_init(w, g, o, d, ix, iy, iz);
-            float t = 0.f;
-            for (;;) {
-                float tn;
-                const int a = walk_axis(w, tn);
-                const float te = fminf(tn, dist);
-                tau += BetaFetch<DT>::get(bricks, brick_addr(g, w.ix, w.iy, w.iz)) * fmaxf(te - t, 0.f);
-                ++nseg;
-                if (tn >= dist) break;
-                t = tn;
-                if (walk_step(w, g, a) >= 0) break;
-            }
-        }
+        walk_to_camera(g, cs.c[c], ix, iy, iz, make_float3(0.5f * g.hx, 0.5f * g.hy, 0.5f * g.hz),
+                       [&](int jx, int jy, int jz, float len) {
+                           tau += BetaFetch<DT>::get(bricks, brick_addr(g, jx, jy, jz)) * len;
+                       },
+                       nseg);
         const float T = expf(-tau);
         if (T_out) T_out[idx] = T;
         if (R_out) {
@@ -103,24 +83,12 @@ __global__ void __launch_bounds__(kTB) k_images(const Geo g, const CamSet cs, co
         const Cam& cm = cs.c[c];
         const int p = gp - cm.pix_off, i = p % cm.w, j = p / cm.w;
         const float* Rc = R + (size_t)c * g.nvox;
-        const float3 o = make_float3(cm.px, cm.py, cm.pz);
         double acc = 0.0;
         for (int rho = 0; rho < hs.n; ++rho) {
             const float3 d = pixel_dir(cm, (float)i + hs.a[rho], (float)j + hs.b[rho]);
-            float t;
-            int ix, iy, iz;
-            if (!ray_enter(g, o, d, t, ix, iy, iz)) continue;
-            Walk w;
-            walk_init(w, g, o, d, ix, iy, iz);
             float s = 0.f;
-            for (;;) {
-                float tn;
-                const int a = walk_axis(w, tn);
-                s += fmaxf(tn - t, 0.f) * __ldg(Rc + lin_index(g, w.ix, w.iy, w.iz));
-                ++nseg;
-                t = tn;
-                if (walk_step(w, g, a) >= 0) break;
-            }
+            walk_from_camera(g, cm, d, [&](int x, int y, int z, float len) { s += len * __ldg(Rc + lin_index(g, x, y, z)); },
+                             nseg);
             acc += (double)s;
         }
         const double img = acc * (double)inv_nv;
@@ -151,23 +119,11 @@ __global__ void __launch_bounds__(kTB) k_backproject(const Geo g, const CamSet c
             const Cam& cm = cs.c[c];
             const int p = gp - cm.pix_off, i = p % cm.w, j = p / cm.w;
             float* bc = bacc + (size_t)c * g.nvox;
-            const float3 o = make_float3(cm.px, cm.py, cm.pz);
             for (int rho = 0; rho < hs.n; ++rho) {
                 const float3 d = pixel_dir(cm, (float)i + hs.a[rho], (float)j + hs.b[rho]);
-                float t;
-                int ix, iy, iz;
-                if (!ray_enter(g, o, d, t, ix, iy, iz)) continue;
-                Walk w;
-                walk_init(w, g, o, d, ix, iy, iz);
-                for (;;) {
-                    float tn;
-                    const int a = walk_axis(w, tn);
-                    const float len = fmaxf(tn - t, 0.f);
-                    if (len > 0.f) atomicAdd(bc + lin_index(g, w.ix, w.iy, w.iz), wgt * len);
-                    ++nseg;
-                    t = tn;
-                    if (walk_step(w, g, a) >= 0) break;
-                }
+                walk_from_camera(g, cm, d, [&](int x, int y, int z, float len) {
+                    if (len > 0.f) atomicAdd(bc + lin_index(g, x, y, z), wgt * len);
+                }, nseg);
             }
         }
     }
@@ -186,28 +142,12 @@ __global__ void __launch_bounds__(kTB) k_los_adjoint(const Geo g, const CamSet c
         if (s != 0.f) {
             const int c = (int)(idx / g.nvox), k = (int)(idx - (long long)c * g.nvox);
             const int ix = k % g.nx, iy = (k / g.nx) % g.ny, iz = k / (g.nx * g.ny);
-            const float3 o = voxel_centre(g, ix, iy, iz);
-            const Cam& cm = cs.c[c];
-            float3 d = make_float3(cm.px - o.x, cm.py - o.y, cm.pz - o.z);
-            const float dist = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-            if (dist > 0.f) {
-                const float inv = 1.f / dist;
-                d = make_float3(d.x * inv, d.y * inv, d.z * inv);
-                float* gc = gT + (size_t)c * g.nvox;
-                Walk w;
-                walk_init(w, g, o, d, ix, iy, iz);
-                float t = 0.f;
-                for (;;) {
-                    float tn;
-                    const int a = walk_axis(w, tn);
-                    const float len = fmaxf(fminf(tn, dist) - t, 0.f);
-                    if (len > 0.f) atomicAdd(gc + lin_index(g, w.ix, w.iy, w.iz), s * len);
-                    ++nseg;
-                    if (tn >= dist) break;
-                    t = tn;
-                    if (walk_step(w, g, a) >= 0) break;
-                }
-            }
+            float* gc = gT + (size_t)c * g.nvox;
+            walk_to_camera(g, cs.c[c], ix, iy, iz, make_float3(0.5f * g.hx, 0.5f * g.hy, 0.5f * g.hz),
+                           [&](int x, int y, int z, float len) {
+                               if (len > 0.f) atomicAdd(gc + lin_index(g, x, y, z), s * len);
+                           },
+                           nseg);
         }
     }
     if (stats) flush_count(stats, MST_ST_LOSADJ_SEGMENTS, nseg);
@@ -224,21 +164,12 @@ __global__ void __launch_bounds__(kTB) k_ray_counts(const Geo g, const CamSet cs
     const Cam& cm = cs.c[c];
     const int p = gp - cm.pix_off, i = p % cm.w, j = p / cm.w;
     float* qc = Q + (size_t)c * g.nvox;
-    const float3 o = make_float3(cm.px, cm.py, cm.pz);
+    unsigned long long nseg = 0;
     for (int rho = 0; rho < hs.n; ++rho) {
         const float3 d = pixel_dir(cm, (float)i + hs.a[rho], (float)j + hs.b[rho]);
-        float t;
-        int ix, iy, iz;
-        if (!ray_enter(g, o, d, t, ix, iy, iz)) continue;
-        Walk w;
-        walk_init(w, g, o, d, ix, iy, iz);
-        for (;;) {
-            float tn;
-            const int a = walk_axis(w, tn);
-            if (tn - t >= eps) atomicAdd(qc + lin_index(g, w.ix, w.iy, w.iz), 1.f);
-            t = tn;
-            if (walk_step(w, g, a) >= 0) break;
-        }
+        walk_from_camera(g, cm, d, [&](int x, int y, int z, float len) {
+            if (len >= eps) atomicAdd(qc + lin_index(g, x, y, z), 1.f);
+        }, nseg);
     }
 }
 

@@ -18,7 +18,7 @@ constexpr uint32_t kFnvOffset = 2166136261u;
 constexpr uint32_t kFnvPrime = 16777619u;
 
 struct Photon {
-    float3 X, d;
+    float3 p, d;     // offset inside voxel (ix, iy, iz) and unit direction
     int ix, iy, iz;
     float I, tau;
     uint32_t s;      // scattering events so far
@@ -42,43 +42,50 @@ __device__ __forceinline__ void tally_zero(Tally& t) {
     t.capped = t.escaped = t.traced = t.lost = 0u;
 }
 
-// step i: launch at the top of the atmosphere along the sun direction with weight I0
+// Voxel and offset of u * n voxels, u = (2m + 1) / 2^24 from a Philox word: (2m + 1) n / 2^24 is
+// split exactly in integers, so the offset keeps all 24 bits of u.
+__device__ __forceinline__ void launch_coord(uint32_t x, int n, float h, int& i, float& off) {
+    const uint64_t q = (uint64_t)(2u * (x >> 9) + 1u) * (uint64_t)n;
+    i = (int)(q >> 24);
+    off = __uint2float_rn((uint32_t)(q & 0xFFFFFFu)) * 5.9604644775390625e-08f * h;
+}
+
+// step i: launch uniformly over the top of the atmosphere along the sun direction, weight I0
 __device__ __forceinline__ void launch_photon(const TransportArgs& A, Photon& ph, uint32_t pid) {
     ph.idx = A.out_base + pid;
     ph.id = A.first_id + pid;
-    const float4 u = draws(A.key, ph.id, 0u);
-    ph.X = make_float3(u.x * A.g.ex, u.y * A.g.ey, A.g.ez);
-    ph.ix = coord_vox(ph.X.x, A.g.hx, A.g.nx);
-    ph.iy = coord_vox(ph.X.y, A.g.hy, A.g.ny);
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)ph.id, (uint32_t)(ph.id >> 32), 0u, 0u), A.key);
+    float ox, oy;
+    launch_coord(x.x, A.g.nx, A.g.hx, ph.ix, ox);
+    launch_coord(x.y, A.g.ny, A.g.hy, ph.iy, oy);
     ph.iz = A.g.nz - 1;
+    ph.p = make_float3(ox, oy, A.g.hz);
     ph.d = A.sun;
     ph.I = A.I0;
-    ph.tau = -logf(1.f - u.z);  // Eq. taurand
+    ph.tau = -logf(1.f - u01(x.z));  // Eq. taurand
     ph.s = 0u;
     ph.hash = kFnvOffset;
 }
 
 // steps ii-iii: free flight of optical depth ph.tau (Eq. MCextinct). Returns -1 on a collision
-// (ph.X and the voxel updated) or the exit face 0..5. With S != 0 it also scatters the score
-// of this flight into the gradient tile: -S * length in every voxel crossed and
-// S * (1/beta - length) in the collision voxel.
+// (ph.p and the voxel updated) or the exit face 0..5 (kWalkOverflow if the walk was abandoned).
+// With S != 0 it also scatters the score of this flight into the gradient tile: -S * length in
+// every voxel crossed and S * (1/beta - length) in the collision voxel.
 template <int DT>
 __device__ __forceinline__ int flight(const TransportArgs& A, Photon& ph, unsigned long long& nseg,
                                       unsigned long long& nsc, float S) {
     Walk w;
-    walk_init(w, A.g, ph.X, ph.d, ph.ix, ph.iy, ph.iz);
-    float t = 0.f, tau = ph.tau;
+    walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+    float tau = ph.tau;
     for (;;) {
         const float b = BetaFetch<DT>::get(A.beta, brick_addr(A.g, w.ix, w.iy, w.iz));
         ++nseg;
-        float tn;
-        const int a = walk_axis(w, tn);
-        const float seg = fmaxf(tn - t, 0.f);
+        float seg;
+        const int a = walk_axis(w, seg);
         const float bs = b * seg;
         if (tau <= bs) {
             const float l = tau / b;
-            const float tc = t + l;
-            ph.X = make_float3(ph.X.x + tc * ph.d.x, ph.X.y + tc * ph.d.y, ph.X.z + tc * ph.d.z);
+            ph.p = walk_local(w, A.g, l);
             ph.ix = w.ix;
             ph.iy = w.iy;
             ph.iz = w.iz;
@@ -93,10 +100,17 @@ __device__ __forceinline__ int flight(const TransportArgs& A, Photon& ph, unsign
             ++nsc;
         }
         tau -= bs;
-        t = tn;
-        const int f = walk_step(w, A.g, a);
+        const int f = walk_step(w, A.g, a, seg);
         if (f >= 0) return f;
     }
+}
+
+// cosine between the photon direction and the direction from the photon to camera c, and the
+// squared distance; r2 = 0 when the photon sits on the centre of projection
+__device__ __forceinline__ float cam_cosine(const TransportArgs& A, const Photon& ph, const Cam& cm, float& r2) {
+    const float3 v = local_delta(A.g, ph.ix, ph.iy, ph.iz, ph.p, cm.ix, cm.iy, cm.iz, make_float3(cm.lx, cm.ly, cm.lz));
+    r2 = v.x * v.x + v.y * v.y + v.z * v.z;
+    return r2 > 0.f ? (ph.d.x * v.x + ph.d.y * v.y + ph.d.z * v.z) * rsqrtf(r2) : 0.f;
 }
 
 // Eq. Lcupdate: L_c(k) += albedo I_s P(angle between the incoming ray and X_c - X_s), for all
@@ -110,10 +124,9 @@ __device__ __forceinline__ void le_voxel(const TransportArgs& A, const Photon& p
             const int c = c0 + j;
             float val = 0.f;
             if (c < A.cams.n) {
-                const Cam& cm = A.cams.c[c];
-                const float vx = cm.px - ph.X.x, vy = cm.py - ph.X.y, vz = cm.pz - ph.X.z;
-                const float r2 = vx * vx + vy * vy + vz * vz;
-                if (r2 > 0.f) val = w * hg_phase(A.hg, (ph.d.x * vx + ph.d.y * vy + ph.d.z * vz) * rsqrtf(r2));
+                float r2;
+                const float mu = cam_cosine(A, ph, A.cams.c[c], r2);
+                if (r2 > 0.f) val = w * hg_phase(A.hg, mu);
             }
             v[j] = val;
         }
@@ -132,36 +145,13 @@ __device__ __forceinline__ float le_adjoint(const TransportArgs& A, const Photon
         for (int j = 0; j < 4; ++j) {
             const int c = c0 + j;
             if (c < A.cams.n && aa[j] != 0.f) {
-                const Cam& cm = A.cams.c[c];
-                const float vx = cm.px - ph.X.x, vy = cm.py - ph.X.y, vz = cm.pz - ph.X.z;
-                const float r2 = vx * vx + vy * vy + vz * vz;
-                if (r2 > 0.f) acc += aa[j] * w * hg_phase(A.hg, (ph.d.x * vx + ph.d.y * vy + ph.d.z * vz) * rsqrtf(r2));
+                float r2;
+                const float mu = cam_cosine(A, ph, A.cams.c[c], r2);
+                if (r2 > 0.f) acc += aa[j] * w * hg_phase(A.hg, mu);
             }
         }
     }
     return acc;
-}
-
-// optical depth from X (in voxel ix,iy,iz) to point P, clipped to the grid
-template <int DT>
-__device__ __forceinline__ float shadow_tau(const TransportArgs& A, float3 X, int ix, int iy, int iz, float3 P) {
-    float3 d = make_float3(P.x - X.x, P.y - X.y, P.z - X.z);
-    const float dist = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-    if (dist == 0.f) return 0.f;
-    const float inv = 1.f / dist;
-    d = make_float3(d.x * inv, d.y * inv, d.z * inv);
-    Walk w;
-    walk_init(w, A.g, X, d, ix, iy, iz);
-    float t = 0.f, tau = 0.f;
-    for (;;) {
-        float tn;
-        const int a = walk_axis(w, tn);
-        const float te = fminf(tn, dist);
-        tau += BetaFetch<DT>::get(A.beta, brick_addr(A.g, w.ix, w.iy, w.iz)) * fmaxf(te - t, 0.f);
-        if (tn >= dist) return tau;
-        t = tn;
-        if (walk_step(w, A.g, a) >= 0) return tau;
-    }
 }
 
 // Eq. fle: pixel p(X_s) of camera c += albedo I_s P t_{s->c} / (|V|^2 Omega_p)
@@ -169,20 +159,26 @@ template <int DT>
 __device__ __forceinline__ void le_classic(const TransportArgs& A, const Photon& ph, float w) {
     for (int c = 0; c < A.cams.n; ++c) {
         const Cam& cm = A.cams.c[c];
-        const float vx = ph.X.x - cm.px, vy = ph.X.y - cm.py, vz = ph.X.z - cm.pz;
-        const float zc = vx * cm.fx + vy * cm.fy + vz * cm.fz;
+        // point relative to the camera
+        const float3 v = local_delta(A.g, cm.ix, cm.iy, cm.iz, make_float3(cm.lx, cm.ly, cm.lz), ph.ix, ph.iy, ph.iz,
+                                     ph.p);
+        const float zc = v.x * cm.fx + v.y * cm.fy + v.z * cm.fz;
         if (!(zc > 0.f)) continue;
-        const float x = (vx * cm.rx + vy * cm.ry + vz * cm.rz) / zc;
-        const float y = (vx * cm.ux + vy * cm.uy + vz * cm.uz) / zc;
+        const float x = (v.x * cm.rx + v.y * cm.ry + v.z * cm.rz) / zc;
+        const float y = (v.x * cm.ux + v.y * cm.uy + v.z * cm.uz) / zc;
         const float px = floorf((x / cm.tx + 1.f) * 0.5f * (float)cm.w);
         const float py = floorf((y / cm.ty + 1.f) * 0.5f * (float)cm.h);
         if (px < 0.f || py < 0.f || px >= (float)cm.w || py >= (float)cm.h) continue;
         const int gp = cm.pix_off + (int)py * cm.w + (int)px;
-        const float r2 = vx * vx + vy * vy + vz * vz;
+        const float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
         if (!(r2 > 0.f)) continue;
-        const float mu = -(ph.d.x * vx + ph.d.y * vy + ph.d.z * vz) * rsqrtf(r2);
-        const float tr = expf(-shadow_tau<DT>(A, ph.X, ph.ix, ph.iy, ph.iz, make_float3(cm.px, cm.py, cm.pz)));
-        const float val = w * hg_phase(A.hg, mu) * tr / (r2 * A.omega[gp]);
+        const float mu = -(ph.d.x * v.x + ph.d.y * v.y + ph.d.z * v.z) * rsqrtf(r2);
+        float tau = 0.f;
+        unsigned long long ns = 0;
+        walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p, [&](int jx, int jy, int jz, float len) {
+            tau += BetaFetch<DT>::get(A.beta, brick_addr(A.g, jx, jy, jz)) * len;
+        }, ns);
+        const float val = w * hg_phase(A.hg, mu) * expf(-tau) / (r2 * A.omega[gp]);
         atomicAdd(A.cimg + gp, (double)val);
     }
 }

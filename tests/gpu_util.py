@@ -34,6 +34,16 @@ def quantised(beta, kind):
     return beta.astype(np.float32).astype(np.float64)
 
 
+def record(name, **vals):
+    """Appends measured parity errors to the JSON-lines file named by MST_PARITY_REPORT."""
+    import json
+    import os
+    path = os.environ.get("MST_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": name, **{k: float(v) for k, v in vals.items()}}) + "\n")
+
+
 def rel_l2(a, b):
     a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

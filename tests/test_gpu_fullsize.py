@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import dev, f32_scene, max_rel, need_gpu, rel_l2
+from tests.gpu_util import dev, f32_scene, max_rel, need_gpu, record, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +45,7 @@ def test_sampled_photon_paths(case):
         ho = oracle.render(sc, q, want_L=False, hashes=True)["hash"]
         agree += int(np.sum(ho == h[s:s + 200]))
         total += 200
+    record("fullsize_photon_paths", agree_frac=agree / total)
     assert agree / total > 0.99, agree / total
 
 
@@ -55,6 +56,8 @@ def test_energy_balance_full_size(case):
     incident = math.cos(p.sun_zenith) * sc.extent()[0] * sc.extent()[1]
     assert st["traced"] == p.n_photons
     assert abs(st["launched"] - incident) < 1e-5 * incident
+    record("fullsize_energy", launched_rel=abs(st["launched"] - incident) / incident,
+           balance_rel=abs(out - incident) / incident)
     assert abs(out - incident) < 1e-4 * incident
     assert st["replay_segments"] > st["segments"]  # the replay walks each scoring path twice
     g = case["out"]["grad"].cpu().numpy()
@@ -66,7 +69,10 @@ def test_transmittance_full_size(m, case):
     T = grid.transmittance(case["beta"]).cpu().numpy()
     tau, T_or = oracle.transmittance(sc)
     err = np.abs(T - T_or) / np.maximum(T_or, 1e-30)
-    assert np.all(err <= 2e-5 * np.maximum(tau, 1.0) + 2e-6)
+    tol = 2e-5 * np.maximum(tau, 1.0) + 2e-6
+    worst = np.unravel_index(np.argmax(err / tol), err.shape)
+    record("fullsize_transmittance", max_rel_T=err.max(), worst_over_tol=(err / tol).max())
+    assert np.all(err <= tol), ((err / tol).max(), worst, tau[worst], T[worst], T_or[worst])
 
 
 def test_images_full_size_from_oracle_L(m, case):
@@ -75,4 +81,6 @@ def test_images_full_size_from_oracle_L(m, case):
     _, T = oracle.transmittance(sc)
     ref = oracle.images(sc, L, T)
     img = grid.form_images(case["beta"], dev(L, np.float64)).cpu().numpy()
-    assert max_rel(img, ref, 1e-3 * np.abs(ref).max()) < 1e-4
+    e = max_rel(img, ref, 1e-3 * np.abs(ref).max())
+    record("fullsize_images_from_L", max_rel=e)
+    assert e < 1e-4
