@@ -113,9 +113,9 @@ TransportArgs transport_args(mst_grid* g, const mst_params* p) {
     a.hg.b = (float)(2.0 * gg);
     a.hg.omg2 = (float)(1.0 - gg * gg);
     a.hg.omg = (float)(1.0 - gg);
+    a.hg.opg = (float)(1.0 + gg);
     a.hg.tg = (float)(2.0 * gg);
     a.hg.iso = std::fabs(gg) < 1e-6;
-    a.hg.inv2g = a.hg.iso ? 0.f : (float)(1.0 / (2.0 * gg));
     a.beta = g->bricks;
     const double th = p->sun_zenith_rad, ph = p->sun_azimuth_rad;
     a.sun = make_float3((float)(-std::sin(th) * std::cos(ph)), (float)(-std::sin(th) * std::sin(ph)),

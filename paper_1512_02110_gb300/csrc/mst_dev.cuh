@@ -78,7 +78,7 @@ __device__ __forceinline__ float4 draws(uint2 key, uint64_t photon, uint32_t eve
 
 struct HG {
     float g, k1, a, b;             // P = k1 * (a - b mu)^(-3/2)
-    float omg2, omg, tg, inv2g;    // sampler constants
+    float omg, opg, omg2, tg;      // 1 - g, 1 + g, 1 - g^2, 2 g
     bool iso;
 };
 
@@ -88,17 +88,29 @@ __device__ __forceinline__ float hg_phase(const HG& h, float mu) {
     return h.k1 * r * r * r;
 }
 
-__device__ __forceinline__ float hg_sample(const HG& h, float u) {
-    if (h.iso) return 2.f * u - 1.f;
-    const float s = h.omg2 / (h.omg + h.tg * u);
-    const float c = (h.a - s * s) * h.inv2g;
-    return fminf(1.f, fmaxf(-1.f, c));
+// Inverse CDF of Eq. Phg (squared reading of Eq. thetaHG): cos = (1 + g^2 - s^2) / (2 g) with
+// s = (1 - g^2) / (1 - g + 2 g u). 1 - cos and 1 + cos are evaluated in factored form,
+//   1 - cos = (1-g)(1-u)(s + 1 - g) / D,  1 + cos = (1+g) u (s + 1 + g) / D,  D = 1 - g + 2 g u,
+// so sin = sqrt((1 - cos)(1 + cos)) keeps full FP32 precision for forward scattering, where
+// sqrt(1 - cos^2) would cancel. 1 - u is exact for the 24-bit uniforms.
+__device__ __forceinline__ void hg_sample(const HG& h, float u, float& ct, float& st) {
+    float omc, opc;
+    if (h.iso) {
+        omc = 2.f * (1.f - u);
+        opc = 2.f * u;
+    } else {
+        const float D = h.omg + h.tg * u;
+        const float s = h.omg2 / D;
+        omc = h.omg * (1.f - u) * (s + h.omg) / D;
+        opc = h.opg * u * (s + h.opg) / D;
+    }
+    ct = fminf(1.f, fmaxf(-1.f, 0.5f * (opc - omc)));
+    st = sqrtf(fmaxf(omc * opc, 0.f));
 }
 
-// New unit direction at polar cosine ct and azimuth 2 pi u1 about d. Transverse frame:
-// e2 = normalize(axis x d), e1 = e2 x d, axis = z unless |d_z| >= 0.9, then x.
-__device__ __forceinline__ float3 rotate_dir(float3 d, float ct, float u1) {
-    const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+// New unit direction at polar angle (cos ct, sin st) and azimuth 2 pi u1 about d. Transverse
+// frame: e2 = normalize(axis x d), e1 = e2 x d, axis = z unless |d_z| >= 0.9, then x.
+__device__ __forceinline__ float3 rotate_dir(float3 d, float ct, float st, float u1) {
     float sp, cp;
     sincospif(2.f * u1, &sp, &cp);
     float3 e2;

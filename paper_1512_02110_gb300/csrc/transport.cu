@@ -208,7 +208,9 @@ __device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, T
             return 3;
         }
     }
-    ph.d = rotate_dir(ph.d, hg_sample(A.hg, u.x), u.y);
+    float ct, st;
+    hg_sample(A.hg, u.x, ct, st);
+    ph.d = rotate_dir(ph.d, ct, st, u.y);
     ph.tau = -logf(1.f - u.w);
     return 0;
 }
