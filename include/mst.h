@@ -121,7 +121,8 @@ typedef struct {
 void mst_default_params(mst_params *p);
 
 /* Geometry pre-calculation (Sec. 3, step i). Copies the grid and cameras into a new handle
- * on the current CUDA device and allocates its scratch buffers. n_subpixel_rays = N_rays of
+ * on the current CUDA device and allocates its scratch buffers. Grid limits: nx, ny <= 2048,
+ * nz <= 1024, nx*ny*nz <= 2^30. n_subpixel_rays = N_rays of
  * Eq. PIc (1..MST_MAX_SUBPIXEL_RAYS); the sub-pixel points are the 2-D Halton points (bases 2
  * and 3, indices 1..N_rays). Requires 1 <= n_cams <= MST_MAX_CAMERAS, positive sizes.
  * On failure *out is NULL. */

@@ -240,6 +240,7 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
     if (!d || !cams) return MST_ERR_INVALID_ARG;
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return MST_ERR_INVALID_ARG;
     if ((long long)d->nx * d->ny * d->nz > (1ll << 30)) return MST_ERR_INVALID_ARG;
+    if (d->nx > 2048 || d->ny > 2048 || d->nz > 1024) return MST_ERR_INVALID_ARG;  // packed voxel index
     if (!(d->dx > 0 && d->dy > 0 && d->dz > 0) || !std::isfinite(d->dx + d->dy + d->dz) || !finite3(d->origin))
         return MST_ERR_INVALID_ARG;
     if (n_cams < 1 || n_cams > MST_MAX_CAMERAS) return MST_ERR_INVALID_ARG;

@@ -67,42 +67,38 @@ __device__ __forceinline__ void launch_photon(const TransportArgs& A, Photon& ph
     ph.hash = kFnvOffset;
 }
 
-// steps ii-iii: free flight of optical depth ph.tau (Eq. MCextinct). Returns -1 on a collision
-// (ph.p and the voxel updated) or the exit face 0..5 (kWalkOverflow if the walk was abandoned).
-// With S != 0 it also scatters the score of this flight into the gradient tile: -S * length in
-// every voxel crossed and S * (1/beta - length) in the collision voxel.
+// steps ii-iii, one voxel of a free flight (Eq. MCextinct). Returns -1 while the flight goes
+// on, kCollided on a collision (ph.p and the voxel updated) or the exit face 0..5
+// (kWalkOverflow if the walk was abandoned). With S != 0 it also scatters the score of the
+// flight into the gradient tile: -S * length in every voxel crossed and S * (1/beta - length)
+// in the collision voxel.
+constexpr int kCollided = -2;
+
 template <int DT>
-__device__ __forceinline__ int flight(const TransportArgs& A, Photon& ph, unsigned long long& nseg,
-                                      unsigned long long& nsc, float S) {
-    Walk w;
-    walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
-    float tau = ph.tau;
-    for (;;) {
-        const float b = BetaFetch<DT>::get(A.beta, brick_addr(A.g, w.ix, w.iy, w.iz));
-        ++nseg;
-        float seg;
-        const int a = walk_axis(w, seg);
-        const float bs = b * seg;
-        if (tau <= bs) {
-            const float l = tau / b;
-            ph.p = walk_local(w, A.g, l);
-            ph.ix = w.ix;
-            ph.iy = w.iy;
-            ph.iz = w.iz;
-            if (S != 0.f) {
-                atomicAdd(A.gacc + lin_index(A.g, w.ix, w.iy, w.iz), S * (1.f / b - l));
-                ++nsc;
-            }
-            return -1;
-        }
-        if (S != 0.f && seg > 0.f) {
-            atomicAdd(A.gacc + lin_index(A.g, w.ix, w.iy, w.iz), -S * seg);
+__device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, Walk& w, float& tau, float S,
+                                           unsigned long long& nsc) {
+    const float b = BetaFetch<DT>::get(A.beta, brick_addr(A.g, w.ix, w.iy, w.iz));
+    float seg;
+    const int a = walk_axis(w, seg);
+    const float bs = b * seg;
+    if (tau <= bs) {
+        const float l = tau / b;
+        ph.p = walk_local(w, A.g, l);
+        ph.ix = w.ix;
+        ph.iy = w.iy;
+        ph.iz = w.iz;
+        if (S != 0.f) {
+            atomicAdd(A.gacc + lin_index(A.g, w.ix, w.iy, w.iz), S * (1.f / b - l));
             ++nsc;
         }
-        tau -= bs;
-        const int f = walk_step(w, A.g, a, seg);
-        if (f >= 0) return f;
+        return kCollided;
     }
+    if (S != 0.f && seg > 0.f) {
+        atomicAdd(A.gacc + lin_index(A.g, w.ix, w.iy, w.iz), -S * seg);
+        ++nsc;
+    }
+    tau -= bs;
+    return walk_step(w, A.g, a, seg);
 }
 
 // cosine between the photon direction and the direction from the photon to camera c, and the
@@ -215,18 +211,94 @@ __device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, T
     return 0;
 }
 
-__device__ __forceinline__ void finish_photon(const TransportArgs& A, Photon& ph, int term) {
+__device__ __forceinline__ void finish_photon(const TransportArgs& A, const Photon& ph, int term) {
     uint32_t h = (ph.hash ^ ph.s) * kFnvPrime;
     h = (h ^ (uint32_t)term) * kFnvPrime;
     if (A.hash) A.hash[ph.idx] = h;
 }
 
-// Warp-uniform refill: lanes without a photon take the next ids of the warp's pool.
-// Returns false once the pool is dry and no lane holds a photon.
+// ------------------------------------------------------------------------------------------
+// Per-warp photon stacks in shared memory (structure of arrays: lane i touches word i, so
+// pushes and pops are free of bank conflicts). A warp holds at most 32 flying photons, fewer
+// than kEvCap queued events (events are processed 32 at a time as soon as 32 are queued) and
+// a ready stack that only grows while no new photon is launched, so at most 32 + 63 photons
+// per warp exist and the stacks cannot overflow.
+
+constexpr int kEvCap = 64;
+constexpr int kRdCap = 96;
+
+template <int NW>
+struct Stack {
+    uint32_t* w;  // NW arrays of cap words
+    int cap;
+};
+
+template <bool REPLAY>
+struct Rec {
+    static constexpr int NW = REPLAY ? 15 : 12;
+};
+
+template <int NW>
+__device__ __forceinline__ void put(const Stack<NW>& q, int slot, const Photon& ph, uint32_t nev, double acc) {
+    uint32_t* b = q.w + slot;
+    const int c = q.cap;
+    b[0 * c] = __float_as_uint(ph.p.x);
+    b[1 * c] = __float_as_uint(ph.p.y);
+    b[2 * c] = __float_as_uint(ph.p.z);
+    b[3 * c] = __float_as_uint(ph.d.x);
+    b[4 * c] = __float_as_uint(ph.d.y);
+    b[5 * c] = __float_as_uint(ph.d.z);
+    b[6 * c] = (uint32_t)ph.ix | ((uint32_t)ph.iy << 11) | ((uint32_t)ph.iz << 22);
+    b[7 * c] = __float_as_uint(ph.I);
+    b[8 * c] = __float_as_uint(ph.tau);
+    b[9 * c] = ph.s;
+    b[10 * c] = ph.hash;
+    b[11 * c] = ph.idx;
+    if (NW > 12) {
+        b[12 * c] = nev;
+        b[13 * c] = (uint32_t)__double_as_longlong(acc);
+        b[14 * c] = (uint32_t)((unsigned long long)__double_as_longlong(acc) >> 32);
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void get(const Stack<NW>& q, int slot, const TransportArgs& A, Photon& ph, uint32_t& nev,
+                                    double& acc) {
+    const uint32_t* b = q.w + slot;
+    const int c = q.cap;
+    ph.p = make_float3(__uint_as_float(b[0]), __uint_as_float(b[c]), __uint_as_float(b[2 * c]));
+    ph.d = make_float3(__uint_as_float(b[3 * c]), __uint_as_float(b[4 * c]), __uint_as_float(b[5 * c]));
+    const uint32_t v = b[6 * c];
+    ph.ix = (int)(v & 0x7FFu);
+    ph.iy = (int)((v >> 11) & 0x7FFu);
+    ph.iz = (int)(v >> 22);
+    ph.I = __uint_as_float(b[7 * c]);
+    ph.tau = __uint_as_float(b[8 * c]);
+    ph.s = b[9 * c];
+    ph.hash = b[10 * c];
+    ph.idx = b[11 * c];
+    ph.id = A.first_id + (ph.idx - A.out_base);
+    if (NW > 12) {
+        nev = b[12 * c];
+        acc = __longlong_as_double((long long)((unsigned long long)b[13 * c] | ((unsigned long long)b[14 * c] << 32)));
+    } else {
+        nev = 0u;
+        acc = 0.0;
+    }
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Warp-uniform refill from the photon id pool: lanes without a photon take the next ids of the
+// warp's slice, lane 0 refilling the slice from the chunk's global ticket.
 template <typename LaunchFn>
-__device__ __forceinline__ void refill(const TransportArgs& A, bool& alive, bool& dry, uint32_t& wbase, uint32_t& wend,
+__device__ __forceinline__ void refill(const TransportArgs& A, bool& fly, bool& dry, uint32_t& wbase, uint32_t& wend,
                                        unsigned lane, LaunchFn&& on_launch) {
-    unsigned need = __ballot_sync(kFull, !alive);
+    unsigned need = __ballot_sync(kFull, !fly);
     while (need != 0u && !dry) {
         if (wbase >= wend) {
             unsigned t0 = 0u;
@@ -239,19 +311,19 @@ __device__ __forceinline__ void refill(const TransportArgs& A, bool& alive, bool
             wbase = t0;
             wend = min(t0 + (unsigned)kTicketBatch, A.n);
         }
-        const unsigned rank = __popc(need & ((1u << lane) - 1u));
+        const unsigned rank = __popc(need & lanemask_lt());
         const unsigned avail = wend - wbase;
-        if (!alive && rank < avail) {
+        if (!fly && rank < avail) {
             const uint32_t pid = wbase + rank;
             if (A.skip && A.skip[A.out_base + pid]) {
                 if (A.hash) A.hash[A.out_base + pid] = 0u;
             } else {
                 on_launch(pid);
-                alive = true;
+                fly = true;
             }
         }
         wbase += min((unsigned)__popc(need), avail);
-        need = __ballot_sync(kFull, !alive);
+        need = __ballot_sync(kFull, !fly);
     }
 }
 
@@ -285,112 +357,155 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
     }
 }
 
-// K1: forward transport. EST = 0 voxelised local estimate, 1 classic local estimate.
-template <int DT, int EST>
+// ------------------------------------------------------------------------------------------
+// The transport kernel. MODE 0: forward with the voxelised local estimate; 1: forward with the
+// classic local estimate; 2: replay adjoint. Every loop trip (1) fills empty lanes from the
+// ready stack, then from the id pool, (2) advances every flying photon by one voxel, pushing
+// collisions onto the event stack, and (3) whenever 32 events are queued (or the chunk is
+// draining), processes 32 events at once: local estimate, albedo, roulette, new direction;
+// photons that go on are pushed onto the ready stack.
+//
+// Replay (MODE 2): pass 1 sums W = sum_s w_s with w_s = sum_c a_c(k_s) albedo I_s P_c(s); a
+// photon that ends pass 1 with W != 0 is relaunched for pass 2, which walks the same path
+// again with S_j = W - sum_{s<j} w_s (FP64) and scatters the score of every flight that ends
+// in an event; pass 2 stops at the last event of pass 1 (nev).
+template <int DT, int MODE>
 __global__ void __launch_bounds__(kTB) k_transport(const TransportArgs A) {
+    constexpr bool REPLAY = MODE == 2;
+    constexpr int NW = Rec<REPLAY>::NW;
+    extern __shared__ uint32_t smem[];
     const unsigned lane = threadIdx.x & 31u;
-    Photon ph;
-    Tally t;
-    tally_zero(t);
-    bool alive = false, dry = false;
-    uint32_t wbase = 0u, wend = 0u;
-    for (;;) {
-        refill(A, alive, dry, wbase, wend, lane, [&](uint32_t pid) {
-            launch_photon(A, ph, pid);
-            t.launched += A.I0;
-            t.traced += 1u;
-        });
-        if (!__any_sync(kFull, alive)) break;
-        if (!alive) continue;
-        const int f = flight<DT>(A, ph, t.segments, t.scatters, 0.f);
-        if (f >= 0) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-                if (q == f) t.esc[q] += ph.I;
-            if (f == kWalkOverflow) t.lost += 1u;
-            else t.escaped += 1u;
-            finish_photon(A, ph, 1);
-            alive = false;
-            continue;
-        }
-        ph.s += 1u;
-        const int k = lin_index(A.g, ph.ix, ph.iy, ph.iz);
-        ph.hash = (ph.hash ^ (uint32_t)k) * kFnvPrime;
-        t.events += 1ull;
-        const float w = A.albedo * ph.I;
-        if (EST == 0)
-            le_voxel(A, ph, w, k);
-        else
-            le_classic<DT>(A, ph, w);
-        const int term = after_event(A, ph, t);
-        if (term) {
-            finish_photon(A, ph, term);
-            alive = false;
-        }
-    }
-    flush_tally(A, t, lane);
-}
+    const unsigned warp = threadIdx.x >> 5;
+    const Stack<NW> evq{smem + warp * NW * (kEvCap + kRdCap), kEvCap};
+    const Stack<NW> rdq{smem + warp * NW * (kEvCap + kRdCap) + NW * kEvCap, kRdCap};
+    int ev_n = 0, rd_n = 0;  // warp-uniform stack heights
 
-// K6: replay adjoint. Pass 1 replays the photon and sums W = sum_s w_s; pass 2 replays it
-// again and, with S_j = W - sum_{s<j} w_s (FP64), scatters the score of every flight that ends
-// in an event. Both passes run the same flight / event code, so they see the same path.
-template <int DT>
-__global__ void __launch_bounds__(kTB) k_replay(const TransportArgs A) {
-    const unsigned lane = threadIdx.x & 31u;
     Photon ph;
+    Walk w;
+    float tau = 0.f;
+    uint32_t nev = 0u;  // replay: events of pass 1 (0 while in pass 1)
+    double acc = 0.0;   // replay: W in pass 1, S in pass 2
+    bool fly = false, dry = false;
+    uint32_t wbase = 0u, wend = 0u;
     Tally t;
     tally_zero(t);
-    bool alive = false, dry = false;
-    uint32_t wbase = 0u, wend = 0u;
-    int phase = 1;
-    double W = 0.0, S = 0.0;
-    uint32_t nev = 0u;
+
     for (;;) {
-        refill(A, alive, dry, wbase, wend, lane, [&](uint32_t pid) {
-            launch_photon(A, ph, pid);
-            phase = 1;
-            W = 0.0;
-            S = 0.0;
-            nev = 0u;
-        });
-        if (!__any_sync(kFull, alive)) break;
-        if (!alive) continue;
-        const int f = flight<DT>(A, ph, t.segments, t.scatters, phase == 2 ? (float)S : 0.f);
-        bool ended = false;
-        if (f >= 0) {
-            ended = true;
-        } else {
-            ph.s += 1u;
-            t.events += 1ull;
-            const int k = lin_index(A.g, ph.ix, ph.iy, ph.iz);
-            const float w = le_adjoint(A, ph, A.albedo * ph.I, k);
-            if (phase == 1)
-                W += (double)w;
-            else
-                S -= (double)w;
-            if (phase == 2 && ph.s == nev) {
-                alive = false;
-                continue;
+        // (1) fill: ready photons first, new photons only when the ready stack is empty
+        unsigned empty = __ballot_sync(kFull, !fly);
+        if (empty != 0u && rd_n > 0) {
+            const int rank = __popc(empty & lanemask_lt());
+            const int take = min(__popc(empty), rd_n);
+            if (!fly && rank < take) {
+                get(rdq, rd_n - 1 - rank, A, ph, nev, acc);
+                walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+                tau = ph.tau;
+                fly = true;
             }
-            ended = after_event(A, ph, t) != 0;
+            rd_n -= take;
+            __syncwarp();
         }
-        if (ended) {
-            if (phase == 1 && W != 0.0 && ph.s > 0u) {
-                nev = ph.s;
-                const uint32_t pid = ph.idx - A.out_base;
-                launch_photon(A, ph, pid);
-                phase = 2;
-                S = W;
-            } else {
-                alive = false;
+        refill(A, fly, dry, wbase, wend, lane, [&](uint32_t pid) {
+            launch_photon(A, ph, pid);
+            walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+            tau = ph.tau;
+            nev = 0u;
+            acc = 0.0;
+            if (!REPLAY) {
+                t.launched += A.I0;
+                t.traced += 1u;
             }
+        });
+        const bool any_fly = __any_sync(kFull, fly);
+        if (!any_fly && ev_n == 0 && rd_n == 0 && dry) break;
+
+        // (2) one voxel for every flying photon
+        int r = -1;
+        if (fly) {
+            ++t.segments;
+            r = flight_step<DT>(A, ph, w, tau, (REPLAY && nev != 0u) ? (float)acc : 0.f, t.scatters);
+        }
+        const bool collided = fly && r == kCollided;
+        const unsigned cmask = __ballot_sync(kFull, collided);
+        if (collided) {
+            put(evq, ev_n + __popc(cmask & lanemask_lt()), ph, nev, acc);
+            fly = false;
+        } else if (fly && r >= 0) {
+            if (REPLAY) {
+                if (nev == 0u && acc != 0.0 && ph.s > 0u) {  // end of pass 1: replay for pass 2
+                    nev = ph.s;
+                    launch_photon(A, ph, ph.idx - A.out_base);
+                    walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+                    tau = ph.tau;
+                } else {
+                    fly = false;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    if (q == r) t.esc[q] += ph.I;
+                if (r == kWalkOverflow) t.lost += 1u;
+                else t.escaped += 1u;
+                finish_photon(A, ph, 1);
+                fly = false;
+            }
+        }
+        ev_n += __popc(cmask);
+        __syncwarp();
+
+        // (3) events, 32 at a time (fewer only while draining)
+        while (ev_n >= 32 || (ev_n > 0 && dry && rd_n == 0 && !__any_sync(kFull, fly))) {
+            const int n = min(32, ev_n);
+            Photon e;
+            uint32_t enev = 0u;
+            double eacc = 0.0;
+            int term = -1;  // -1 idle lane, 0 goes on, > 0 ended
+            if ((int)lane < n) {
+                get(evq, ev_n - 1 - (int)lane, A, e, enev, eacc);
+                e.s += 1u;
+                t.events += 1ull;
+                const int k = lin_index(A.g, e.ix, e.iy, e.iz);
+                const float wgt = A.albedo * e.I;
+                if (!REPLAY) {
+                    e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
+                    if (MODE == 0) le_voxel(A, e, wgt, k);
+                    else le_classic<DT>(A, e, wgt);
+                    term = after_event(A, e, t);
+                    if (term) finish_photon(A, e, term);
+                } else {
+                    const float we = le_adjoint(A, e, wgt, k);
+                    if (enev == 0u) eacc += (double)we;
+                    else eacc -= (double)we;
+                    if (enev != 0u && e.s == enev) {
+                        term = 1;  // last event of pass 2
+                    } else {
+                        Tally dummy;
+                        term = after_event(A, e, dummy);
+                        if (term && enev == 0u && eacc != 0.0) {  // end of pass 1: replay for pass 2
+                            enev = e.s;
+                            launch_photon(A, e, e.idx - A.out_base);
+                            term = 0;
+                        }
+                    }
+                }
+            }
+            ev_n -= n;
+            __syncwarp();
+            const unsigned gmask = __ballot_sync(kFull, term == 0);
+            if (term == 0) put(rdq, rd_n + __popc(gmask & lanemask_lt()), e, enev, eacc);
+            rd_n += __popc(gmask);
+            __syncwarp();
         }
     }
-    const unsigned long long ev = warp_sumu(t.events), sg = warp_sumu(t.segments), sc = warp_sumu(t.scatters);
-    if (lane == 0u) {
-        atomicAdd(A.stats + MST_ST_REPLAY_EVENTS, (double)ev);
-        atomicAdd(A.stats + MST_ST_REPLAY_SEGMENTS, (double)sg);
-        atomicAdd(A.stats + MST_ST_REPLAY_SCATTERS, (double)sc);
+    if (REPLAY) {
+        const unsigned long long ev = warp_sumu(t.events), sg = warp_sumu(t.segments), sc = warp_sumu(t.scatters);
+        if (lane == 0u) {
+            atomicAdd(A.stats + MST_ST_REPLAY_EVENTS, (double)ev);
+            atomicAdd(A.stats + MST_ST_REPLAY_SEGMENTS, (double)sg);
+            atomicAdd(A.stats + MST_ST_REPLAY_SCATTERS, (double)sc);
+        }
+    } else {
+        flush_tally(A, t, lane);
     }
 }
 
@@ -418,10 +533,16 @@ __global__ void k_fold_grad(float* __restrict__ gacc, double* __restrict__ g64, 
     }
 }
 
+template <bool REPLAY>
+constexpr size_t smem_bytes() {
+    return (size_t)(kTB / 32) * Rec<REPLAY>::NW * (kEvCap + kRdCap) * sizeof(uint32_t);
+}
+
 template <typename K>
-int occupancy(K kern) {
+int occupancy(K kern, size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kTB, 0) != cudaSuccess || n < 1) n = 1;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kTB, smem) != cudaSuccess || n < 1) n = 1;
     return n;
 }
 
@@ -432,11 +553,11 @@ int transport_blocks_per_sm(int dtype, int estimator, bool replay) {
     const int col = replay ? 2 : estimator;
     if (cache[dtype][col]) return cache[dtype][col];
     int n = 1;
-#define MST_OCC(DT)                                                   \
-    if (dtype == DT) {                                                \
-        if (replay) n = occupancy(k_replay<DT>);                      \
-        else if (estimator == 0) n = occupancy(k_transport<DT, 0>);   \
-        else n = occupancy(k_transport<DT, 1>);                       \
+#define MST_OCC(DT)                                                                  \
+    if (dtype == DT) {                                                               \
+        if (replay) n = occupancy(k_transport<DT, 2>, smem_bytes<true>());           \
+        else if (estimator == 0) n = occupancy(k_transport<DT, 0>, smem_bytes<false>()); \
+        else n = occupancy(k_transport<DT, 1>, smem_bytes<false>());                 \
     }
     MST_OCC(0) MST_OCC(1) MST_OCC(2)
 #undef MST_OCC
@@ -447,10 +568,11 @@ int transport_blocks_per_sm(int dtype, int estimator, bool replay) {
 cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int estimator, int blocks,
                              cudaStream_t st) {
     (void)g;
+    const size_t sm = smem_bytes<false>();
 #define MST_TR(DT)                                                                   \
     if (dtype == DT) {                                                               \
-        if (estimator == 0) k_transport<DT, 0><<<blocks, kTB, 0, st>>>(a);           \
-        else k_transport<DT, 1><<<blocks, kTB, 0, st>>>(a);                          \
+        if (estimator == 0) k_transport<DT, 0><<<blocks, kTB, sm, st>>>(a);          \
+        else k_transport<DT, 1><<<blocks, kTB, sm, st>>>(a);                         \
     }
     MST_TR(0) MST_TR(1) MST_TR(2)
 #undef MST_TR
@@ -459,9 +581,10 @@ cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtyp
 
 cudaError_t launch_replay(const mst_grid* g, const TransportArgs& a, int dtype, int blocks, cudaStream_t st) {
     (void)g;
-    if (dtype == 0) k_replay<0><<<blocks, kTB, 0, st>>>(a);
-    else if (dtype == 1) k_replay<1><<<blocks, kTB, 0, st>>>(a);
-    else k_replay<2><<<blocks, kTB, 0, st>>>(a);
+    const size_t sm = smem_bytes<true>();
+    if (dtype == 0) k_transport<0, 2><<<blocks, kTB, sm, st>>>(a);
+    else if (dtype == 1) k_transport<1, 2><<<blocks, kTB, sm, st>>>(a);
+    else k_transport<2, 2><<<blocks, kTB, sm, st>>>(a);
     return cudaGetLastError();
 }
 
