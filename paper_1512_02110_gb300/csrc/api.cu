@@ -282,6 +282,8 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
     geo.ex = (float)(d->nx * d->dx); geo.ey = (float)(d->ny * d->dy); geo.ez = (float)(d->nz * d->dz);
     geo.nvox = d->nx * d->ny * d->nz;
     geo.max_steps = d->nx + d->ny + d->nz + 8;
+    geo.wrap_y = 512 * geo.nbx - 56;
+    geo.wrap_z = 512 * geo.nbx * geo.nby - 448;
     for (int a = 0; a < 3; ++a) g->origin[a] = d->origin[a];
     g->voxel_volume = d->dx * d->dy * d->dz;
     g->n_cams = n_cams;

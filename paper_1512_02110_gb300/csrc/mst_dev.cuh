@@ -24,6 +24,7 @@ struct Geo {
     float ex, ey, ez;   // grid extent (m)
     int nvox;
     int max_steps;      // nx + ny + nz + 8: no straight walk crosses more voxels
+    int wrap_y, wrap_z; // brick-address step when a y / z step crosses into the next brick
 };
 
 struct Cam {
@@ -129,14 +130,13 @@ __device__ __forceinline__ float3 rotate_dir(float3 d, float ct, float st, float
 }
 
 // ------------------------------------------------------------------------------------------
-// Extinction storage: 8^3 bricks, Morton order inside a brick, so one 128-byte line holds a
-// 4x4x2 (FP32) or 4x4x4 (16-bit) block of neighbouring voxels.
-
-__device__ __forceinline__ int spread3(int v) { return (v & 1) | ((v & 2) << 2) | ((v & 4) << 4); }
+// Extinction storage: 8^3 bricks (2 KB in FP32), x fastest inside a brick, bricks x fastest.
+// A voxel step changes the address by +-1, +-8 or +-64 inside a brick and by a fixed stride
+// when it crosses into the next brick, so walks update it with one add.
 
 __device__ __forceinline__ int brick_addr(const Geo& g, int ix, int iy, int iz) {
     const int b = (ix >> kBrickShift) + g.nbx * ((iy >> kBrickShift) + g.nby * (iz >> kBrickShift));
-    return (b << 9) | spread3(ix & 7) | (spread3(iy & 7) << 1) | (spread3(iz & 7) << 2);
+    return (b << 9) | (ix & 7) | ((iy & 7) << 3) | ((iz & 7) << 6);
 }
 
 __device__ __forceinline__ int lin_index(const Geo& g, int ix, int iy, int iz) { return ix + g.nx * (iy + g.ny * iz); }
@@ -180,6 +180,8 @@ struct Walk {
     float p0x, p0y, p0z;  // offset at the start (kept on axes the ray does not move along)
     int ix, iy, iz;       // current voxel
     int sx, sy, sz;       // step per axis (0 when the direction component is 0)
+    int addr;             // brick address of the current voxel
+    int lin;              // linear index ix + nx (iy + ny iz) of the current voxel
     int left;             // face crossings left before the walk is abandoned
 };
 
@@ -211,6 +213,8 @@ __device__ __forceinline__ void walk_init(Walk& w, const Geo& g, float3 p, float
     axis_init(fminf(fmaxf(p.z, 0.f), g.hz), d.z, g.hz, w.tz, w.qz, w.az, w.sz);
     w.p0x = p.x; w.p0y = p.y; w.p0z = p.z;
     w.ix = ix; w.iy = iy; w.iz = iz;
+    w.addr = brick_addr(g, ix, iy, iz);
+    w.lin = lin_index(g, ix, iy, iz);
     w.left = g.max_steps;
 }
 
@@ -229,22 +233,26 @@ constexpr int kWalkOverflow = 6;
 // Moves seg along the ray and crosses the face on axis a. Returns the exit face (0..5: x-, x+,
 // y-, y+, z-, z+) if the walk left the grid, kWalkOverflow if it made more crossings than any
 // straight line through the grid can (only possible with a non-finite direction), else -1.
+// Branch-free in the axis, so lanes that cross different faces do not diverge.
 __device__ __forceinline__ int walk_step(Walk& w, const Geo& g, int a, float seg) {
+    const bool bx = a == 0, by = a == 1, bz = a == 2;
+    w.tx = bx ? w.qx : w.tx - seg;
+    w.ty = by ? w.qy : w.ty - seg;
+    w.tz = bz ? w.qz : w.tz - seg;
+    const int s = bx ? w.sx : (by ? w.sy : w.sz);
+    w.ix += bx ? s : 0;
+    w.iy += by ? s : 0;
+    w.iz += bz ? s : 0;
+    const int i = bx ? w.ix : (by ? w.iy : w.iz);
+    const bool wrap = (i & 7) == (s > 0 ? 0 : 7);
+    const int small = bx ? 1 : (by ? 8 : 64);
+    const int big = bx ? 505 : (by ? g.wrap_y : g.wrap_z);
+    w.addr += s * (wrap ? big : small);
+    w.lin += s * (bx ? 1 : (by ? g.nx : g.nx * g.ny));
+    const bool out = ((unsigned)w.ix >= (unsigned)g.nx) | ((unsigned)w.iy >= (unsigned)g.ny) |
+                     ((unsigned)w.iz >= (unsigned)g.nz);
     if (--w.left < 0) return kWalkOverflow;
-    if (a == 0) {
-        w.ty -= seg; w.tz -= seg; w.tx = w.qx;
-        w.ix += w.sx;
-        if ((unsigned)w.ix >= (unsigned)g.nx) return w.sx > 0 ? 1 : 0;
-    } else if (a == 1) {
-        w.tx -= seg; w.tz -= seg; w.ty = w.qy;
-        w.iy += w.sy;
-        if ((unsigned)w.iy >= (unsigned)g.ny) return w.sy > 0 ? 3 : 2;
-    } else {
-        w.tx -= seg; w.ty -= seg; w.tz = w.qz;
-        w.iz += w.sz;
-        if ((unsigned)w.iz >= (unsigned)g.nz) return w.sz > 0 ? 5 : 4;
-    }
-    return -1;
+    return out ? 2 * a + (s > 0) : -1;
 }
 
 __device__ __forceinline__ float axis_local(float t, float a, int s, float h, float p0, float l) {
@@ -321,7 +329,7 @@ __device__ __forceinline__ int cam_of_pixel(const CamSet& cs, int gp) {
 }
 
 // Walks the segment from the point (voxel i, offset p) to the centre of projection of camera c,
-// calling fn(ix, iy, iz, length) for every voxel it crosses. The walk ends in the
+// calling fn(walk, length) for every voxel it crosses (walk.addr / walk.lin name the voxel). The walk ends in the
 // camera's voxel (last length = distance to the camera inside it) or, for a camera outside the
 // grid, at the grid face; the remaining distance guards both ends against rounding.
 template <typename F>
@@ -341,22 +349,22 @@ __device__ __forceinline__ void walk_to_camera(const Geo& g, const Cam& c, int i
         if (walk_at(w, c.ix, c.iy, c.iz)) {
             const float3 q = walk_local(w, g, 0.f);
             const float len = (lc.x - q.x) * d.x + (lc.y - q.y) * d.y + (lc.z - q.z) * d.z;
-            fn(w.ix, w.iy, w.iz, fminf(fmaxf(len, 0.f), rem));
+            fn(w, fminf(fmaxf(len, 0.f), rem));
             return;
         }
         float seg;
         const int a = walk_axis(w, seg);
         if (seg >= rem) {
-            fn(w.ix, w.iy, w.iz, rem);
+            fn(w, rem);
             return;
         }
-        fn(w.ix, w.iy, w.iz, seg);
+        fn(w, seg);
         rem -= seg;
         if (walk_step(w, g, a, seg) >= 0) return;
     }
 }
 
-// Walks the pixel ray from camera c along d to the grid exit, calling fn(ix, iy, iz, length).
+// Walks the pixel ray from camera c along d to the grid exit, calling fn(walk, length).
 template <typename F>
 __device__ __forceinline__ void walk_from_camera(const Geo& g, const Cam& c, float3 d, F&& fn,
                                                  unsigned long long& nseg) {
@@ -369,7 +377,7 @@ __device__ __forceinline__ void walk_from_camera(const Geo& g, const Cam& c, flo
         ++nseg;
         float seg;
         const int a = walk_axis(w, seg);
-        fn(w.ix, w.iy, w.iz, seg);
+        fn(w, seg);
         if (walk_step(w, g, a, seg) >= 0) return;
     }
 }

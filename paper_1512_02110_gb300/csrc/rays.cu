@@ -13,8 +13,6 @@ namespace {
 
 constexpr int kTB = 256;
 
-__device__ __forceinline__ int compact3(int m) { return (m & 1) | ((m >> 2) & 2) | ((m >> 4) & 4); }
-
 template <int DT>
 __global__ void k_stage(const float* __restrict__ beta, void* __restrict__ bricks, const Geo g, int total) {
     typedef typename BetaFetch<DT>::T T;
@@ -22,7 +20,7 @@ __global__ void k_stage(const float* __restrict__ beta, void* __restrict__ brick
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < total; a += gridDim.x * blockDim.x) {
         const int b = a >> 9, m = a & 511;
         const int bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / (g.nbx * g.nby);
-        const int ix = bx * 8 + compact3(m), iy = by * 8 + compact3(m >> 1), iz = bz * 8 + compact3(m >> 2);
+        const int ix = bx * 8 + (m & 7), iy = by * 8 + ((m >> 3) & 7), iz = bz * 8 + (m >> 6);
         float v = 0.f;
         if (ix < g.nx && iy < g.ny && iz < g.nz) v = beta[lin_index(g, ix, iy, iz)];
         out[a] = BetaFetch<DT>::make(v);
@@ -50,9 +48,7 @@ __global__ void __launch_bounds__(kTB) k_los(const Geo g, const CamSet cs, const
         const int ix = k % g.nx, iy = (k / g.nx) % g.ny, iz = k / (g.nx * g.ny);
         double tau = 0.0;  // FP64 sum: ~1e-7 relative for optical depths up to ~100
         walk_to_camera(g, cs.c[c], ix, iy, iz, make_float3(0.5f * g.hx, 0.5f * g.hy, 0.5f * g.hz),
-                       [&](int jx, int jy, int jz, float len) {
-                           tau += (double)(BetaFetch<DT>::get(bricks, brick_addr(g, jx, jy, jz)) * len);
-                       },
+                       [&](const Walk& w, float len) { tau += (double)(BetaFetch<DT>::get(bricks, w.addr) * len); },
                        nseg);
         const float T = (float)exp(-tau);
         if (T_out) T_out[idx] = T;
@@ -86,9 +82,8 @@ __global__ void __launch_bounds__(kTB) k_images(const Geo g, const CamSet cs, co
         double acc = 0.0;
         for (int rho = 0; rho < hs.n; ++rho) {
             const float3 d = pixel_dir(cm, (float)i + hs.a[rho], (float)j + hs.b[rho]);
-            walk_from_camera(g, cm, d, [&](int x, int y, int z, float len) {
-                acc += (double)(len * __ldg(Rc + lin_index(g, x, y, z)));
-            }, nseg);
+            walk_from_camera(g, cm, d, [&](const Walk& w, float len) { acc += (double)(len * __ldg(Rc + w.lin)); },
+                             nseg);
         }
         const double img = acc * (double)inv_nv;
         if (images) images[gp] = img;
@@ -120,8 +115,8 @@ __global__ void __launch_bounds__(kTB) k_backproject(const Geo g, const CamSet c
             float* bc = bacc + (size_t)c * g.nvox;
             for (int rho = 0; rho < hs.n; ++rho) {
                 const float3 d = pixel_dir(cm, (float)i + hs.a[rho], (float)j + hs.b[rho]);
-                walk_from_camera(g, cm, d, [&](int x, int y, int z, float len) {
-                    if (len > 0.f) atomicAdd(bc + lin_index(g, x, y, z), wgt * len);
+                walk_from_camera(g, cm, d, [&](const Walk& w, float len) {
+                    if (len > 0.f) atomicAdd(bc + w.lin, wgt * len);
                 }, nseg);
             }
         }
@@ -143,8 +138,8 @@ __global__ void __launch_bounds__(kTB) k_los_adjoint(const Geo g, const CamSet c
             const int ix = k % g.nx, iy = (k / g.nx) % g.ny, iz = k / (g.nx * g.ny);
             float* gc = gT + (size_t)c * g.nvox;
             walk_to_camera(g, cs.c[c], ix, iy, iz, make_float3(0.5f * g.hx, 0.5f * g.hy, 0.5f * g.hz),
-                           [&](int x, int y, int z, float len) {
-                               if (len > 0.f) atomicAdd(gc + lin_index(g, x, y, z), s * len);
+                           [&](const Walk& w, float len) {
+                               if (len > 0.f) atomicAdd(gc + w.lin, s * len);
                            },
                            nseg);
         }
@@ -166,8 +161,8 @@ __global__ void __launch_bounds__(kTB) k_ray_counts(const Geo g, const CamSet cs
     unsigned long long nseg = 0;
     for (int rho = 0; rho < hs.n; ++rho) {
         const float3 d = pixel_dir(cm, (float)i + hs.a[rho], (float)j + hs.b[rho]);
-        walk_from_camera(g, cm, d, [&](int x, int y, int z, float len) {
-            if (len >= eps) atomicAdd(qc + lin_index(g, x, y, z), 1.f);
+        walk_from_camera(g, cm, d, [&](const Walk& w, float len) {
+            if (len >= eps) atomicAdd(qc + w.lin, 1.f);
         }, nseg);
     }
 }

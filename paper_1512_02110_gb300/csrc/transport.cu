@@ -77,7 +77,7 @@ constexpr int kCollided = -2;
 template <int DT>
 __device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, Walk& w, float& tau, float S,
                                            unsigned long long& nsc) {
-    const float b = BetaFetch<DT>::get(A.beta, brick_addr(A.g, w.ix, w.iy, w.iz));
+    const float b = BetaFetch<DT>::get(A.beta, w.addr);
     float seg;
     const int a = walk_axis(w, seg);
     const float bs = b * seg;
@@ -88,13 +88,13 @@ __device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, W
         ph.iy = w.iy;
         ph.iz = w.iz;
         if (S != 0.f) {
-            atomicAdd(A.gacc + lin_index(A.g, w.ix, w.iy, w.iz), S * (1.f / b - l));
+            atomicAdd(A.gacc + w.lin, S * (1.f / b - l));
             ++nsc;
         }
         return kCollided;
     }
     if (S != 0.f && seg > 0.f) {
-        atomicAdd(A.gacc + lin_index(A.g, w.ix, w.iy, w.iz), -S * seg);
+        atomicAdd(A.gacc + w.lin, -S * seg);
         ++nsc;
     }
     tau -= bs;
@@ -171,9 +171,8 @@ __device__ __forceinline__ void le_classic(const TransportArgs& A, const Photon&
         const float mu = -(ph.d.x * v.x + ph.d.y * v.y + ph.d.z * v.z) * rsqrtf(r2);
         float tau = 0.f;
         unsigned long long ns = 0;
-        walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p, [&](int jx, int jy, int jz, float len) {
-            tau += BetaFetch<DT>::get(A.beta, brick_addr(A.g, jx, jy, jz)) * len;
-        }, ns);
+        walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p,
+                       [&](const Walk& wk, float len) { tau += BetaFetch<DT>::get(A.beta, wk.addr) * len; }, ns);
         const float val = w * hg_phase(A.hg, mu) * expf(-tau) / (r2 * A.omega[gp]);
         atomicAdd(A.cimg + gp, (double)val);
     }
@@ -221,11 +220,13 @@ __device__ __forceinline__ void finish_photon(const TransportArgs& A, const Phot
 // Per-warp photon stacks in shared memory (structure of arrays: lane i touches word i, so
 // pushes and pops are free of bank conflicts). A warp holds at most 32 flying photons, fewer
 // than kEvCap queued events (events are processed 32 at a time as soon as 32 are queued) and
-// a ready stack that only grows while no new photon is launched, so at most 32 + 63 photons
-// per warp exist and the stacks cannot overflow.
+// a ready stack: new photons are launched only when the ready stack is empty, so right after a
+// launch a warp holds 32 flying + at most 31 queued photons and never more than 63 in total;
+// neither stack can overflow.
 
 constexpr int kEvCap = 64;
-constexpr int kRdCap = 96;
+constexpr int kRdCap = 64;
+constexpr int kStepsPerTrip = 1;  // voxels a flying lane advances per loop trip
 
 template <int NW>
 struct Stack {
@@ -422,8 +423,12 @@ __global__ void __launch_bounds__(kTB) k_transport(const TransportArgs A) {
         // (2) one voxel for every flying photon
         int r = -1;
         if (fly) {
-            ++t.segments;
-            r = flight_step<DT>(A, ph, w, tau, (REPLAY && nev != 0u) ? (float)acc : 0.f, t.scatters);
+            const float S = (REPLAY && nev != 0u) ? (float)acc : 0.f;
+#pragma unroll 1
+            for (int q = 0; q < kStepsPerTrip && r == -1; ++q) {
+                ++t.segments;
+                r = flight_step<DT>(A, ph, w, tau, S, t.scatters);
+            }
         }
         const bool collided = fly && r == kCollided;
         const unsigned cmask = __ballot_sync(kFull, collided);
