@@ -226,7 +226,12 @@ __device__ __forceinline__ void finish_photon(const TransportArgs& A, const Phot
 
 constexpr int kEvCap = 64;
 constexpr int kRdCap = 64;
-constexpr int kStepsPerTrip = 1;  // voxels a flying lane advances per loop trip
+// Voxels a flying lane advances per loop trip, and minimum resident blocks per SM (register
+// budget), per kernel mode; set from sweeps on the 64^3 cumulus workload.
+constexpr int kStepsForward = 4;
+constexpr int kStepsReplay = 2;
+constexpr int kMinBlocksForward = 1;
+constexpr int kMinBlocksReplay = 3;
 
 template <int NW>
 struct Stack {
@@ -371,8 +376,10 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
 // again with S_j = W - sum_{s<j} w_s (FP64) and scatters the score of every flight that ends
 // in an event; pass 2 stops at the last event of pass 1 (nev).
 template <int DT, int MODE>
-__global__ void __launch_bounds__(kTB) k_transport(const TransportArgs A) {
+__global__ void __launch_bounds__(kTB, MODE == 2 ? kMinBlocksReplay : kMinBlocksForward)
+    k_transport(const TransportArgs A) {
     constexpr bool REPLAY = MODE == 2;
+    constexpr int kStepsPerTrip = REPLAY ? kStepsReplay : kStepsForward;
     constexpr int NW = Rec<REPLAY>::NW;
     extern __shared__ uint32_t smem[];
     const unsigned lane = threadIdx.x & 31u;
