@@ -228,7 +228,7 @@ constexpr int kEvCap = 64;
 constexpr int kRdCap = 64;
 // Voxels a flying lane advances per loop trip, and minimum resident blocks per SM (register
 // budget), per kernel mode; set from sweeps on the 64^3 cumulus workload.
-constexpr int kStepsForward = 4;
+constexpr int kStepsForward = 8;
 constexpr int kStepsReplay = 2;
 constexpr int kMinBlocksForward = 1;
 constexpr int kMinBlocksReplay = 3;
