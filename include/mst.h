@@ -40,10 +40,12 @@ extern "C" {
 #define MST_ERR_OOM (-3)         /* device allocation failed in mst_create_grid */
 #define MST_ERR_NO_DEVICE (-4)   /* no usable CUDA device */
 #define MST_ERR_UNSUPPORTED (-5) /* combination of options not implemented */
+#define MST_ERR_TOO_LARGE (-6)   /* grid exceeds the fixed scratch of mst_transmittance_noalloc */
 
 #define MST_MAX_CAMERAS 16
 #define MST_MAX_SUBPIXEL_RAYS 64
 #define MST_NSTATS 32
+#define MST_NOALLOC_MAX_BRICK_VOXELS (1 << 21) /* 8^3-brick slots of mst_transmittance_noalloc */
 
 /* local estimate used by the forward render */
 enum { MST_EST_VOXEL = 0, MST_EST_CLASSIC = 1 };
@@ -212,6 +214,23 @@ int mst_sync(mst_grid *g);
 
 /* Message of the last error on the handle ("" if none); valid until the next call. */
 const char *mst_last_error(mst_grid *g);
+
+/* LOS transmittance without a handle and without allocating: for callers that cannot call
+ * cudaMalloc (code inside a stream capture, hosts that hand out device memory only from their
+ * own arena, plugins that may not allocate after start-up). The paper has no counterpart: it
+ * computes the same T_c(k) as mst_transmittance (FP32 grid) for the grid and cameras given.
+ *   beta_dev [nvox] float, T_dev [C][nvox] float: the caller's buffers.
+ * Scratch: a fixed device array of MST_NOALLOC_MAX_BRICK_VOXELS floats (8 MiB) inside the
+ * library, held by every GPU that loads it until the process exits. Grids whose 8^3-brick
+ * rounding (ceil(nx/8) ceil(ny/8) ceil(nz/8) * 512) exceeds it are rejected with
+ * MST_ERR_TOO_LARGE before anything is enqueued (e.g. 128^3 fits, 136 x 128 x 128 does not).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call outside any stream capture. Every call shares the one array and
+ * overwrites it; calls whose work overlaps on the GPU (other streams, other threads) race,
+ * so order them on one stream or synchronise between them. Returns MST_OK, MST_ERR_INVALID_ARG,
+ * MST_ERR_TOO_LARGE, MST_ERR_NO_DEVICE or MST_ERR_CUDA. */
+int mst_transmittance_noalloc(const mst_grid_desc *grid, int n_cams, const mst_camera *cams, const float *beta_dev,
+                              float *T_dev, void *stream);
 
 /* Library version (integer, increases with the ABI). */
 int mst_version(void);

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libmst.so")
 
 MST_OK = 0
 ERRORS = {-1: "invalid argument", -2: "CUDA error", -3: "out of device memory", -4: "no CUDA device",
-          -5: "unsupported"}
+          -5: "unsupported", -6: "grid too large for the no-allocation scratch"}
 EST = {"voxel": 0, "classic": 1}
 GRID_DTYPE = {"f32": 0, "f16": 1, "bf16": 2}
 GRAD = {"surrogate": 0, "full": 1}
@@ -37,7 +37,7 @@ STAT_NAMES = ["esc_xm", "esc_xp", "esc_ym", "esc_yp", "esc_zm", "esc_zp", "absor
 EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy", "mst_render", "mst_render_grad",
            "mst_transmittance", "mst_form_images", "mst_surrogate_grad", "mst_ray_counts", "mst_regularizer",
            "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
-           "mst_get_phase_times"]
+           "mst_get_phase_times", "mst_transmittance_noalloc"]
 PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine"]
 
 
@@ -87,6 +87,7 @@ def _load():
     L.mst_get_stats.argtypes = [P, P]
     L.mst_set_profiling.argtypes = [P, I]
     L.mst_get_phase_times.argtypes = [P, P, P]
+    L.mst_transmittance_noalloc.argtypes = [P, I, P, P, P, P]
     L.mst_sync.argtypes = [P]
     L.mst_last_error.argtypes = [P]
     L.mst_last_error.restype = ctypes.c_char_p
@@ -287,6 +288,33 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+
+def transmittance_noalloc(shape, h, origin, cam_pos, cam_rot, cam_w, cam_h, cam_fov, beta, T=None, stream=None):
+    """mst_transmittance_noalloc: T_c(k) without a handle; the library allocates nothing (its
+    scratch is a fixed device array). beta: CUDA float32 [nvox]; T: CUDA float32 [C, nvox]
+    (created here if not given). Raises MSTError with MST_ERR_TOO_LARGE for grids past the
+    array's size."""
+    nvox = int(np.prod(shape))
+    cam_pos = np.asarray(cam_pos, dtype=np.float64).reshape(-1, 3)
+    nc = cam_pos.shape[0]
+    desc = GridDesc(int(shape[0]), int(shape[1]), int(shape[2]), float(h[0]), float(h[1]), float(h[2]),
+                    (ctypes.c_double * 3)(*[float(o) for o in origin]))
+    cams = (Camera * nc)()
+    rot = np.asarray(cam_rot, dtype=np.float64).reshape(nc, 9)
+    for c in range(nc):
+        cams[c].pos = (ctypes.c_double * 3)(*cam_pos[c])
+        cams[c].rot = (ctypes.c_double * 9)(*rot[c])
+        cams[c].width, cams[c].height = int(np.ravel(cam_w)[c]), int(np.ravel(cam_h)[c])
+        cams[c].fov_x_rad = float(np.ravel(cam_fov)[c])
+    if not (beta.is_cuda and beta.dtype == torch.float32 and beta.is_contiguous() and beta.numel() == nvox):
+        raise ValueError("beta: need a contiguous CUDA float32 tensor of nvox elements")
+    if T is None:
+        T = torch.empty(nc, nvox, dtype=torch.float32, device=beta.device)
+    rc = lib.mst_transmittance_noalloc(ctypes.byref(desc), nc, cams, _ptr(beta), _ptr(T), _stream(stream))
+    if rc != MST_OK:
+        raise MSTError(f"mst_transmittance_noalloc: {ERRORS.get(rc, rc)}")
+    return T
 
 
 from .autograd import RenderLoss, reconstruct  # noqa: E402  (needs `lib` above)
