@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--ref-photons", type=float, default=2e4, help="photons per oracle step (bounded sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
+    ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
+    ap.add_argument("--study", default=None, choices=["precision"],
+                    help="FP16/BF16 brick forms against FP32 at equal photon count (prints one JSON line)")
     return ap.parse_args()
 
 
@@ -333,10 +337,138 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# single call, batched scenes, precision study
+
+
+def run_single(args):
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sc, p = synth.cfg_cumulus64(int(args.photons))
+    grid = m.Grid.from_scene(sc)
+    beta = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
+    meas = torch.zeros(sc.n_pix, dtype=torch.float64, device="cuda")
+    out = grid.render_grad(beta, m.make_params(p, grad_mode=args.grad, grid_dtype=args.grid_dtype), meas,
+                           images=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"single": True, "photons": int(args.photons), "loss": out["loss"].item(),
+                      "segments": grid.stats()["segments"]}))
+    return 0
+
+
+def _timed(fn, steps, warmup, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms), ms
+
+
+def run_batch(args):
+    """Config 5: 16 scenes of uneven size (24^3-96^3, 3-12 cameras, 1e7-1e8 photons log-uniform),
+    forward + full gradient, as one graph launch vs. 16 sequential calls."""
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(0)
+    scenes = synth.batch_scenes(16, max_photons=args.photons, min_photons=args.photons / 10)
+    grids, betas, meas, params = [], [], [], []
+    for sc, p in scenes:
+        g = m.Grid.from_scene(sc)
+        b = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
+        meas.append(g.render(b, m.make_params(p, seed=p.seed + 1000))["images"])
+        grids.append(g)
+        betas.append(torch.from_numpy(synth.smoothed(sc.beta, sc.shape, 0.2).astype(np.float32)).cuda())
+        params.append(m.make_params(p, grad_mode="full"))
+    batch = m.Batch(grids)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms_batch, all_b = _timed(lambda: batch.render_grad(betas, params, meas), args.steps, args.warmup, flush)
+
+    def sequential():
+        for g, b, q, mm in zip(grids, betas, params, meas):
+            g.render_grad(b, q, mm, images=False)
+
+    ms_seq, all_s = _timed(sequential, args.steps, args.warmup, flush)
+    segs = 0.0
+    for g, b, q, mm in zip(grids, betas, params, meas):
+        g.render_grad(b, q, mm, images=False)
+        segs += g.stats()["segments"]
+    photons = sum(int(q.n_photons) for q in params)
+    print(json.dumps({"metric": "photon path segments/s (batched forward + full gradient, 16 uneven scenes)",
+                      "value": segs / (ms_batch * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
+                      "sequential_ms_per_step": ms_seq, "sequential_value": segs / (ms_seq * 1e-3),
+                      "photons_per_step": photons, "segments_per_step": segs, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "batch16: 16 scenes 24^3-96^3 x 20 m, blob/fractal fields, albedo "
+                                             "0.99-0.999, g 0.75-0.9, sun 0-60 deg, 3-12 cams of 64/128 px, "
+                                             f"{args.photons / 10:.0e}-{args.photons:.0e} photons each",
+                                 "l2": "flushed between timed steps"}}), flush=True)
+    batch.close()
+    return 0
+
+
+def run_precision_study(args):
+    """Image and gradient error of the FP32 / FP16 / BF16 brick forms at N photons against a
+    10 N-photon FP32 reference (relative L2), and their step times."""
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(0)
+    n = int(args.photons)
+    sc, p = synth.cfg_cumulus64(n)
+    grid = m.Grid.from_scene(sc)
+    beta = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
+    meas = grid.render(beta, m.make_params(p, seed=4))["images"]
+    beta_e = torch.from_numpy(synth.smoothed(sc.beta, sc.shape, 0.2).astype(np.float32)).cuda()
+    ref_img = torch.zeros_like(meas)
+    ref_grad = torch.zeros(sc.nvox, dtype=torch.float64, device="cuda")
+    reps = 10
+    for r in range(reps):  # 10 N photons in N-photon slices with distinct ids
+        q = m.make_params(p, grad_mode="full", seed=11, photon_offset=r * n, n_photons_total=reps * n)
+        o = grid.render_grad(beta_e, q, meas)
+        ref_img += o["images"]
+        ref_grad += o["grad"]
+    # images are linear in the photon slices; the gradient is a sum over slices only to first order,
+    # so the reference gradient is taken from the slices' mean (bias O(1/N))
+    ref_grad /= reps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for kind in ("f32", "f16", "bf16"):
+        q = m.make_params(p, grad_mode="full", seed=12, grid_dtype=kind)
+        out = grid.render_grad(beta_e, q, meas)
+        ei = float((out["images"] - ref_img).norm() / ref_img.norm())
+        eg = float((out["grad"] - ref_grad).norm() / ref_grad.norm())
+        ms, _ = _timed(lambda: grid.render_grad(beta_e, q, meas, images=False), args.steps, args.warmup, flush)
+        res[kind] = {"image_rel_l2": ei, "grad_rel_l2": eg, "ms_per_step": ms}
+    print(json.dumps({"study": "precision", "photons": n, "reference": f"FP32, {reps * n} photons (seed 11)",
+                      "forms": res}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.single:
+        return run_single(args)
+    if args.study == "precision":
+        return run_precision_study(args)
+    if args.workload == "batch16":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -232,6 +232,27 @@ const char *mst_last_error(mst_grid *g);
 int mst_transmittance_noalloc(const mst_grid_desc *grid, int n_cams, const mst_camera *cams, const float *beta_dev,
                               float *T_dev, void *stream);
 
+/* Batched scenes (BASELINE config 5; Sec. 1 photon parallelism across independent scenes).
+ * A batch owns one CUDA graph holding the mst_render_grad sequences of n distinct handles, each
+ * on its own branch, so scenes of uneven size overlap on the GPU and the whole batch is one
+ * graph launch. The graph is captured on the first call (work is enqueued on internal
+ * streams; the handles' conditioning weights are prepared on `stream` first) and replayed
+ * while every pointer and parameter is unchanged; any change re-captures it. Results are
+ * those of n mst_render_grad calls with the same arguments.
+ *   grids: n distinct handles on one device (1 <= n <= MST_MAX_BATCH); the batch does not own
+ *          them and must be destroyed before them.
+ *   betas[i], params[i], meas[i], masks[i] (masks may be NULL, entries may be NULL),
+ *   images[i] (images may be NULL, entries may be NULL), grads[i]: as in mst_render_grad.
+ *   losses [n] device doubles. */
+#define MST_MAX_BATCH 64
+typedef struct mst_batch mst_batch;
+int mst_batch_create(int n, mst_grid *const *grids, mst_batch **out);
+int mst_batch_render_grad(mst_batch *b, const float *const *betas, const mst_params *params,
+                          const double *const *images_meas, const uint8_t *const *masks, double *const *images,
+                          double *const *grads, double *losses_dev, void *stream);
+const char *mst_batch_last_error(mst_batch *b);
+void mst_batch_destroy(mst_batch *b); /* NULL-safe; synchronises the device first */
+
 /* Library version (integer, increases with the ABI). */
 int mst_version(void);
 

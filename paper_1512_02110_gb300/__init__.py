@@ -37,7 +37,8 @@ STAT_NAMES = ["esc_xm", "esc_xp", "esc_ym", "esc_yp", "esc_zm", "esc_zp", "absor
 EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy", "mst_render", "mst_render_grad",
            "mst_transmittance", "mst_form_images", "mst_surrogate_grad", "mst_ray_counts", "mst_regularizer",
            "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
-           "mst_get_phase_times", "mst_transmittance_noalloc"]
+           "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
+           "mst_batch_last_error", "mst_batch_destroy"]
 PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine"]
 
 
@@ -88,13 +89,20 @@ def _load():
     L.mst_set_profiling.argtypes = [P, I]
     L.mst_get_phase_times.argtypes = [P, P, P]
     L.mst_transmittance_noalloc.argtypes = [P, I, P, P, P, P]
+    L.mst_batch_create.argtypes = [I, P, ctypes.POINTER(P)]
+    L.mst_batch_render_grad.argtypes = [P, P, P, P, P, P, P, P, P]
+    L.mst_batch_last_error.argtypes = [P]
+    L.mst_batch_last_error.restype = ctypes.c_char_p
+    L.mst_batch_destroy.argtypes = [P]
     L.mst_sync.argtypes = [P]
     L.mst_last_error.argtypes = [P]
     L.mst_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("mst_last_error", "mst_default_params", "mst_destroy", "mst_version"):
+        if name not in ("mst_last_error", "mst_default_params", "mst_destroy", "mst_version", "mst_batch_last_error",
+                        "mst_batch_destroy"):
             getattr(L, name).restype = I
     L.mst_destroy.restype = None
+    L.mst_batch_destroy.restype = None
     L.mst_default_params.restype = None
     return L
 
@@ -281,6 +289,53 @@ class Grid:
     def close(self):
         if getattr(self, "_h", None):
             lib.mst_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """mst_batch: forward + gradient of several scenes (one Grid each) in one CUDA graph."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g._h.value for g in self.grids])
+        h = ctypes.c_void_p()
+        rc = lib.mst_batch_create(len(self.grids), arr, ctypes.byref(h))
+        if rc != MST_OK:
+            raise MSTError(f"mst_batch_create: {ERRORS.get(rc, rc)}")
+        self._h = h
+        self._keep = None
+
+    def render_grad(self, betas, params, meas, masks=None, images=False, stream=None):
+        """Lists (one entry per scene) of CUDA tensors as in Grid.render_grad; returns
+        dict(loss=[n] tensor, grad=[...], images=[...] or None)."""
+        n = len(self.grids)
+        P = ctypes.c_void_p
+        for g, b, m in zip(self.grids, betas, meas):
+            g._t(b, g.nvox, torch.float32, "beta")
+            g._t(m, g.n_pix, torch.float64, "images_meas")
+        grads = [g._new(g.nvox) for g in self.grids]
+        imgs = [g._new(g.n_pix) for g in self.grids] if images else None
+        losses = torch.empty(n, dtype=torch.float64, device=self.grids[0].device)
+        pa = (Params * n)(*params)
+        arr = lambda ts: (P * n)(*[None if t is None else t.data_ptr() for t in ts])
+        self._keep = (betas, meas, masks, grads, imgs, losses)
+        rc = lib.mst_batch_render_grad(self._h, arr(betas), pa, arr(meas), None if masks is None else arr(masks),
+                                       None if imgs is None else arr(imgs), arr(grads), _ptr(losses),
+                                       _stream(stream))
+        if rc != MST_OK:
+            msg = lib.mst_batch_last_error(self._h)
+            raise MSTError(f"mst_batch_render_grad: {ERRORS.get(rc, rc)}: {msg.decode() if msg else ''}")
+        return dict(loss=losses, grad=grads, images=imgs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mst_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -210,6 +210,10 @@ void free_all(mst_grid* g) {
         if (p) cudaFree(p);
 }
 
+int check_render_grad(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const double* grad);
+int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const uint8_t* mask,
+                     double* images, double* grad, double* loss, cudaStream_t st);
+
 }  // namespace
 
 extern "C" {
@@ -439,13 +443,29 @@ int mst_render(mst_grid* g, const float* beta, const mst_params* p, double* imag
 int mst_render_grad(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const uint8_t* mask,
                     double* images, double* grad, double* loss, void* stream) {
     if (!g) return MST_ERR_INVALID_ARG;
+    int rc = check_render_grad(g, beta, p, meas, grad);
+    if (rc) return rc;
+    DeviceGuard dg(g->device);
+    prof_reset(g);
+    return render_grad_impl(g, beta, p, meas, mask, images, grad, loss, as_stream(stream));
+}
+
+}  // extern "C"
+
+namespace {
+
+int check_render_grad(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const double* grad) {
     if (!beta || !meas || !grad) return fail(g, MST_ERR_INVALID_ARG, "beta, images_meas and grad are required");
-    int rc = check_params(g, p, true);
+    const int rc = check_params(g, p, true);
     if (rc) return rc;
     if (p->estimator != MST_EST_VOXEL) return fail(g, MST_ERR_UNSUPPORTED, "gradients need the voxel estimator");
-    DeviceGuard dg(g->device);
-    cudaStream_t st = as_stream(stream);
-    prof_reset(g);
+    return MST_OK;
+}
+
+// Forward render, loss and gradient of one handle, enqueued on st (Sec. 2.1.2, Sec. 3, Sec. 5).
+int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const uint8_t* mask,
+                     double* images, double* grad, double* loss, cudaStream_t st) {
+    int rc = MST_OK;
     const size_t nL = (size_t)g->n_cams * g->geo.nvox;
     double* lossp = loss ? loss : g->stats + MST_NSTATS;
     {
@@ -502,6 +522,10 @@ int mst_render_grad(mst_grid* g, const float* beta, const mst_params* p, const d
     }
     return MST_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int mst_transmittance(mst_grid* g, const float* beta, int dtype, float* T, void* stream) {
     if (!g) return MST_ERR_INVALID_ARG;
@@ -660,5 +684,177 @@ int mst_sync(mst_grid* g) {
 }
 
 const char* mst_last_error(mst_grid* g) { return g ? g->err.c_str() : "null handle"; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Batched scenes: one CUDA graph holds the forward + gradient sequences of n handles, each on
+// its own branch, so independent scenes of uneven size overlap on the GPU and the whole batch
+// costs one graph launch. The graph is captured on the first call and replayed while every
+// pointer and parameter stays the same; any change re-captures it.
+
+struct mst_batch {
+    int n = 0;
+    int device = 0;
+    std::vector<mst_grid*> grids;
+    std::vector<cudaStream_t> branch;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> key;
+    std::string err;
+};
+
+namespace {
+
+void batch_free(mst_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaStream_t s : b->branch)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+template <typename T>
+void key_add(std::vector<unsigned char>& k, const T& v) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+    k.insert(k.end(), p, p + sizeof(T));
+}
+
+}  // namespace
+
+extern "C" {
+
+int mst_batch_create(int n, mst_grid* const* grids, mst_batch** out) {
+    if (!out) return MST_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || n > MST_MAX_BATCH || !grids) return MST_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!grids[i] || grids[i]->device != grids[0]->device) return MST_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == grids[i]) return MST_ERR_INVALID_ARG;  // each scene needs its own scratch
+    }
+    mst_batch* b = new mst_batch();
+    b->n = n;
+    b->device = grids[0]->device;
+    b->grids.assign(grids, grids + n);
+    DeviceGuard dg(b->device);
+    bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    b->branch.assign(n, nullptr);
+    b->join.assign(n, nullptr);
+    for (int i = 0; ok && i < n; ++i)
+        ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        batch_free(b);
+        delete b;
+        return MST_ERR_CUDA;
+    }
+    *out = b;
+    return MST_OK;
+}
+
+void mst_batch_destroy(mst_batch* b) {
+    if (!b) return;
+    DeviceGuard dg(b->device);
+    cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+}
+
+const char* mst_batch_last_error(mst_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_params* params,
+                          const double* const* meas, const uint8_t* const* masks, double* const* images,
+                          double* const* grads, double* losses, void* stream) {
+    if (!b) return MST_ERR_INVALID_ARG;
+    if (!betas || !params || !meas || !grads || !losses) {
+        b->err = "betas, params, images_meas, grads and losses are required";
+        return MST_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < b->n; ++i) {
+        const int rc = check_render_grad(b->grids[i], betas[i], &params[i], meas[i], grads[i]);
+        if (rc) {
+            b->err = "scene " + std::to_string(i) + ": " + b->grids[i]->err;
+            return rc;
+        }
+    }
+    DeviceGuard dg(b->device);
+    cudaStream_t st = as_stream(stream);
+    std::vector<unsigned char> key;
+    for (int i = 0; i < b->n; ++i) {
+        key_add(key, betas[i]);
+        key_add(key, params[i]);
+        key_add(key, meas[i]);
+        key_add(key, masks ? masks[i] : nullptr);
+        key_add(key, images ? images[i] : nullptr);
+        key_add(key, grads[i]);
+        key_add(key, b->grids[i]->dbg_hash);
+        key_add(key, b->grids[i]->dbg_skip);
+    }
+    key_add(key, losses);
+    if (!b->exec || key != b->key) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        // everything that allocates or sets function attributes happens before the capture
+        for (int i = 0; i < b->n; ++i) {
+            mst_grid* g = b->grids[i];
+            g->prof = false;
+            prof_reset(g);
+            const int rc = ensure_q(g, params[i].grad_mode == MST_GRAD_SURROGATE ? params[i].conditioning : 0, st);
+            if (rc) {
+                b->err = g->err;
+                return rc;
+            }
+            transport_blocks_per_sm(params[i].grid_dtype, 0, false);
+            transport_blocks_per_sm(params[i].grid_dtype, 0, true);
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            b->err = "stream error before capture";
+            return MST_ERR_CUDA;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            b->err = "cudaStreamBeginCapture failed";
+            return MST_ERR_CUDA;
+        }
+        int rc = MST_OK;
+        cudaEventRecord(b->fork, b->cap);
+        for (int i = 0; i < b->n && rc == MST_OK; ++i) {
+            cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+            rc = render_grad_impl(b->grids[i], betas[i], &params[i], meas[i], masks ? masks[i] : nullptr,
+                                  images ? images[i] : nullptr, grads[i], losses + i, b->branch[i]);
+            if (rc) b->err = "scene " + std::to_string(i) + ": " + b->grids[i]->err;
+            cudaEventRecord(b->join[i], b->branch[i]);
+            cudaStreamWaitEvent(b->cap, b->join[i], 0);
+        }
+        const cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
+        if (rc == MST_OK && (ec != cudaSuccess || !graph)) {
+            b->err = std::string("graph capture failed: ") + cudaGetErrorString(ec);
+            rc = MST_ERR_CUDA;
+        }
+        if (rc == MST_OK && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+            b->err = "cudaGraphInstantiate failed";
+            b->exec = nullptr;
+            rc = MST_ERR_CUDA;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (rc) return rc;
+        b->key = key;
+    }
+    if (cudaGraphLaunch(b->exec, st) != cudaSuccess) {
+        b->err = "cudaGraphLaunch failed";
+        return MST_ERR_CUDA;
+    }
+    return MST_OK;
+}
 
 }  // extern "C"

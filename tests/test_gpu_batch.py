@@ -1,0 +1,65 @@
+"""Batched scenes in one CUDA graph (mst_batch_*): equal to per-scene mst_render_grad calls,
+stable under graph replay, re-captured when a parameter changes."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_util import dev, f32_scene, need_gpu, record, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    return need_gpu()
+
+
+def _scenes():
+    out = []
+    sc, p = synth.cfg_blobs16(60_000)
+    out.append((f32_scene(sc), p))
+    shape, h = (24, 20, 12), (30.0, 35.0, 40.0)
+    beta = synth.fractal_field(shape, h, seed=5, max_ext=30 * synth.KM)
+    cams = synth.make_cameras([(355.0, 343.0, 1.0), (100.0, 600.0, 1.0), (600.0, 100.0, 1.0)], 40, 40, 60.0)
+    out.append((f32_scene(synth.make_scene(shape, h, beta, cams)),
+                synth.Params(albedo=0.995, g=0.8, sun_zenith=math.radians(20), n_photons=90_000, seed=8)))
+    sc3, _ = synth.cfg_lognormal32()
+    out.append((f32_scene(sc3), synth.Params(albedo=0.999, g=0.85, sun_zenith=math.radians(45), n_photons=40_000,
+                                             seed=9)))
+    return out
+
+
+def test_batch_matches_individual_calls(m):
+    import torch
+    cases = _scenes()
+    grids = [m.Grid.from_scene(sc) for sc, _ in cases]
+    betas = [dev(synth.smoothed(sc.beta, sc.shape, 0.3), np.float32) for sc, _ in cases]
+    meas = [g.render(dev(sc.beta, np.float32), m.make_params(p, seed=p.seed + 100))["images"]
+            for g, (sc, p) in zip(grids, cases)]
+    params = [m.make_params(p, grad_mode="full" if i != 1 else "surrogate", conditioning="inv_count")
+              for i, (sc, p) in enumerate(cases)]
+    refs = [g.render_grad(b, q, mm) for g, b, q, mm in zip(grids, betas, params, meas)]
+    batch = m.Batch(grids)
+    for rep in range(2):  # capture, then replay
+        out = batch.render_grad(betas, params, meas)
+        torch.cuda.synchronize()
+        for i, r in enumerate(refs):
+            eg = rel_l2(out["grad"][i].cpu().numpy(), r["grad"].cpu().numpy())
+            el = abs(out["loss"][i].item() - r["loss"].item()) / r["loss"].item()
+            record(f"batch[{i},rep{rep}]", grad_rel_l2=eg, loss_rel=el)
+            assert eg < 1e-5 and el < 1e-6, (i, rep, eg, el)
+    # a changed parameter re-captures the graph
+    params[0] = m.make_params(cases[0][1], grad_mode="full", seed=77)
+    out = batch.render_grad(betas, params, meas)
+    ref0 = grids[0].render_grad(betas[0], params[0], meas[0])
+    assert rel_l2(out["grad"][0].cpu().numpy(), ref0["grad"].cpu().numpy()) < 1e-5
+    batch.close()
+
+
+def test_batch_rejects_shared_handles(m):
+    sc, _ = synth.cfg_blobs16()
+    g = m.Grid.from_scene(f32_scene(sc))
+    with pytest.raises(m.MSTError):
+        m.Batch([g, g])
