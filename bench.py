@@ -434,17 +434,9 @@ def run_precision_study(args):
     beta = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
     meas = grid.render(beta, m.make_params(p, seed=4))["images"]
     beta_e = torch.from_numpy(synth.smoothed(sc.beta, sc.shape, 0.2).astype(np.float32)).cuda()
-    ref_img = torch.zeros_like(meas)
-    ref_grad = torch.zeros(sc.nvox, dtype=torch.float64, device="cuda")
     reps = 10
-    for r in range(reps):  # 10 N photons in N-photon slices with distinct ids
-        q = m.make_params(p, grad_mode="full", seed=11, photon_offset=r * n, n_photons_total=reps * n)
-        o = grid.render_grad(beta_e, q, meas)
-        ref_img += o["images"]
-        ref_grad += o["grad"]
-    # images are linear in the photon slices; the gradient is a sum over slices only to first order,
-    # so the reference gradient is taken from the slices' mean (bias O(1/N))
-    ref_grad /= reps
+    ref = grid.render_grad(beta_e, m.make_params(p, grad_mode="full", seed=11, n_photons=reps * n), meas)
+    ref_img, ref_grad = ref["images"], ref["grad"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     res = {}
     for kind in ("f32", "f16", "bf16"):
