@@ -135,6 +135,8 @@ TransportArgs transport_args(mst_grid* g, const mst_params* p) {
     a.omega = g->omega;
     a.adj = g->adj;
     a.gacc = g->gacc;
+    a.wbuf = g->wbuf;
+    a.nevbuf = g->nevbuf;
     a.stats = g->stats;
     a.hash = g->dbg_hash;
     a.skip = g->dbg_skip;
@@ -148,26 +150,34 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
     a.cimg = cimg;
     const uint64_t n = p->n_photons;
     const int nchunks = (int)((n + kChunk - 1) / kChunk);
-    MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * nchunks, st));
+    MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * nchunks * (replay ? 2 : 1), st));
     const int est = replay ? 0 : p->estimator;
-    const int blocks = g->sm_count * transport_blocks_per_sm(p->grid_dtype, est, replay);
+    const int b_fwd = g->sm_count * transport_blocks_per_sm(p->grid_dtype, est);
+    const int b_p1 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, 3);
+    const int b_p2 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, 2);
     for (int c = 0; c < nchunks; ++c) {
         const uint64_t base = (uint64_t)c * kChunk;
         a.first_id = p->photon_offset + base;
         a.out_base = (uint32_t)base;
         a.n = (uint32_t)((n - base) < kChunk ? (n - base) : kChunk);
-        a.ticket = g->tickets + c;
         if (replay) {
+            a.ticket = g->tickets + 2 * c;
             {
                 Phase ph(g, MST_PH_REPLAY, st);
-                MST_CK(launch_replay(g, a, p->grid_dtype, blocks, st));
+                MST_CK(launch_transport(g, a, p->grid_dtype, 3, b_p1, st));
+            }
+            a.ticket = g->tickets + 2 * c + 1;
+            {
+                Phase ph(g, MST_PH_REPLAY2, st);
+                MST_CK(launch_transport(g, a, p->grid_dtype, 2, b_p2, st));
             }
             Phase ph(g, MST_PH_FOLD, st);
             MST_CK(launch_fold_grad(g, st));
         } else {
+            a.ticket = g->tickets + c;
             {
                 Phase ph(g, MST_PH_TRANSPORT, st);
-                MST_CK(launch_transport(g, a, p->grid_dtype, est, blocks, st));
+                MST_CK(launch_transport(g, a, p->grid_dtype, est, b_fwd, st));
             }
             if (est == MST_EST_VOXEL) {
                 Phase ph(g, MST_PH_FOLD, st);
@@ -205,7 +215,7 @@ double radical_inverse(int base, int i) {
 
 void free_all(mst_grid* g) {
     void* ptrs[] = {g->bricks, g->Lacc, g->L64, g->T, g->R, g->bacc, g->gT, g->adj, g->gacc, g->g64,
-                    g->resid, g->lap, g->omega, g->Qw, g->stats, g->tickets};
+                    g->resid, g->lap, g->omega, g->Qw, g->stats, g->tickets, g->wbuf, g->nevbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -353,12 +363,14 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
         {(void**)&g->gT, C * nvox * 4},
         {(void**)&g->adj, nvox * g->cp * 4},
         {(void**)&g->gacc, nvox * 4},
+        {(void**)&g->wbuf, kChunk * 8},
+        {(void**)&g->nevbuf, kChunk * 4},
         {(void**)&g->g64, nvox * 8},
         {(void**)&g->resid, (size_t)off * 8},
         {(void**)&g->lap, nvox * 8},
         {(void**)&g->omega, (size_t)off * 4},
         {(void**)&g->stats, MST_NSTATS * 8 + 64},
-        {(void**)&g->tickets, (size_t)kMaxChunks * 4},
+        {(void**)&g->tickets, (size_t)kMaxChunks * 8},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -813,8 +825,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
                 b->err = g->err;
                 return rc;
             }
-            transport_blocks_per_sm(params[i].grid_dtype, 0, false);
-            transport_blocks_per_sm(params[i].grid_dtype, 0, true);
+            for (int mode = 0; mode < 4; ++mode) transport_blocks_per_sm(params[i].grid_dtype, mode);
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             b->err = "stream error before capture";

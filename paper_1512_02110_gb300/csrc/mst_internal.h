@@ -36,6 +36,8 @@ struct TransportArgs {
     const float* omega;        // [total pix] pixel solid angles (classic estimator)
     const float* adj;          // [nvox][cp] a_c(k) = T_c(k) b_c(k) (replay)
     float* gacc;               // [nvox] FP32 gradient accumulator (replay)
+    double* wbuf;              // [kChunk] W per photon of the chunk (replay pass 1 -> pass 2)
+    uint32_t* nevbuf;          // [kChunk] events per photon of the chunk (replay pass 1 -> pass 2)
     double* stats;             // [MST_NSTATS]
     uint32_t* hash;            // per-photon checksum or NULL
     const uint8_t* skip;       // per-photon skip mask or NULL
@@ -64,6 +66,8 @@ struct mst_grid {
     float* gT = nullptr;          // [C][nvox]  W_c^T (L T b)
     float* adj = nullptr;         // [nvox][cp] T_c b_c
     float* gacc = nullptr;        // [nvox]
+    double* wbuf = nullptr;       // [kChunk]
+    uint32_t* nevbuf = nullptr;   // [kChunk]
     double* g64 = nullptr;        // [nvox]
     double* resid = nullptr;      // [total_pix] 2 M (i - i_meas)
     double* lap = nullptr;        // [nvox] Lap beta
@@ -92,9 +96,9 @@ namespace mst {
 
 // launchers (all enqueue on `st`; return cudaGetLastError())
 cudaError_t launch_stage(const mst_grid* g, const float* beta, int dtype, cudaStream_t st);
-cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int estimator, int blocks,
+// transport kernel modes: 0 forward voxel LE, 1 forward classic LE, 3 replay pass 1, 2 replay pass 2
+cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int mode, int blocks,
                              cudaStream_t st);
-cudaError_t launch_replay(const mst_grid* g, const TransportArgs& a, int dtype, int blocks, cudaStream_t st);
 cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st);
 cudaError_t launch_fold_grad(const mst_grid* g, cudaStream_t st);
 cudaError_t launch_los(const mst_grid* g, int dtype, const double* L, const double* jfix, const float* beta_ref,
@@ -111,6 +115,6 @@ cudaError_t launch_combine_surrogate(const mst_grid* g, const double* Lsrc, cons
 cudaError_t launch_combine_full(const mst_grid* g, const float* gT, const double* gL, double* grad, cudaStream_t st);
 cudaError_t launch_regularizer(const mst_grid* g, const float* beta, double eta, double* lap, double* psi,
                                double* loss, double* grad, cudaStream_t st);
-int transport_blocks_per_sm(int dtype, int estimator, bool replay);
+int transport_blocks_per_sm(int dtype, int mode);
 
 }  // namespace mst

@@ -229,9 +229,14 @@ constexpr int kRdCap = 64;
 // Voxels a flying lane advances per loop trip, and minimum resident blocks per SM (register
 // budget), per kernel mode; set from sweeps on the 64^3 cumulus workload.
 constexpr int kStepsForward = 8;
-constexpr int kStepsReplay = 2;
+constexpr int kStepsPass1 = 8;
+constexpr int kStepsPass2 = 2;
 constexpr int kMinBlocksForward = 1;
-constexpr int kMinBlocksReplay = 3;
+constexpr int kMinBlocksPass1 = 1;
+constexpr int kMinBlocksPass2 = 3;
+
+// kernel modes
+constexpr int kFwdVoxel = 0, kFwdClassic = 1, kPass2 = 2, kPass1 = 3;
 
 template <int NW>
 struct Stack {
@@ -301,9 +306,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Warp-uniform refill from the photon id pool: lanes without a photon take the next ids of the
 // warp's slice, lane 0 refilling the slice from the chunk's global ticket.
-template <typename LaunchFn>
+template <typename LaunchFn, typename SkipFn>
 __device__ __forceinline__ void refill(const TransportArgs& A, bool& fly, bool& dry, uint32_t& wbase, uint32_t& wend,
-                                       unsigned lane, LaunchFn&& on_launch) {
+                                       unsigned lane, LaunchFn&& on_launch, SkipFn&& on_skip) {
     unsigned need = __ballot_sync(kFull, !fly);
     while (need != 0u && !dry) {
         if (wbase >= wend) {
@@ -323,9 +328,9 @@ __device__ __forceinline__ void refill(const TransportArgs& A, bool& fly, bool& 
             const uint32_t pid = wbase + rank;
             if (A.skip && A.skip[A.out_base + pid]) {
                 if (A.hash) A.hash[A.out_base + pid] = 0u;
+                on_skip(pid);
             } else {
-                on_launch(pid);
-                fly = true;
+                fly = on_launch(pid);
             }
         }
         wbase += min((unsigned)__popc(need), avail);
@@ -365,21 +370,24 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
 
 // ------------------------------------------------------------------------------------------
 // The transport kernel. MODE 0: forward with the voxelised local estimate; 1: forward with the
-// classic local estimate; 2: replay adjoint. Every loop trip (1) fills empty lanes from the
+// classic local estimate; 3 and 2: the two passes of the replay adjoint. Every loop trip (1) fills empty lanes from the
 // ready stack, then from the id pool, (2) advances every flying photon by one voxel, pushing
 // collisions onto the event stack, and (3) whenever 32 events are queued (or the chunk is
 // draining), processes 32 events at once: local estimate, albedo, roulette, new direction;
 // photons that go on are pushed onto the ready stack.
 //
-// Replay (MODE 2): pass 1 sums W = sum_s w_s with w_s = sum_c a_c(k_s) albedo I_s P_c(s); a
-// photon that ends pass 1 with W != 0 is relaunched for pass 2, which walks the same path
-// again with S_j = W - sum_{s<j} w_s (FP64) and scatters the score of every flight that ends
-// in an event; pass 2 stops at the last event of pass 1 (nev).
+// Replay adjoint, two launches per chunk. Pass 1 (MODE 3) walks every photon and stores
+// W = sum_s w_s, w_s = sum_c a_c(k_s) albedo I_s P_c(s), and its event count per photon. Pass 2
+// (MODE 2) walks again only the photons with W != 0, with S_j = W - sum_{s<j} w_s (FP64), and
+// scatters the score of every flight that ends in an event; it stops at pass 1's last event.
+// Both passes run the same flight and event arithmetic, so they see the same path.
 template <int DT, int MODE>
-__global__ void __launch_bounds__(kTB, MODE == 2 ? kMinBlocksReplay : kMinBlocksForward)
+__global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
+                                                       : (MODE == kPass1 ? kMinBlocksPass1 : kMinBlocksForward))
     k_transport(const TransportArgs A) {
-    constexpr bool REPLAY = MODE == 2;
-    constexpr int kStepsPerTrip = REPLAY ? kStepsReplay : kStepsForward;
+    constexpr bool REPLAY = MODE == kPass1 || MODE == kPass2;
+    constexpr bool PASS1 = MODE == kPass1, PASS2 = MODE == kPass2;
+    constexpr int kStepsPerTrip = PASS2 ? kStepsPass2 : (PASS1 ? kStepsPass1 : kStepsForward);
     constexpr int NW = Rec<REPLAY>::NW;
     extern __shared__ uint32_t smem[];
     const unsigned lane = threadIdx.x & 31u;
@@ -391,8 +399,8 @@ __global__ void __launch_bounds__(kTB, MODE == 2 ? kMinBlocksReplay : kMinBlocks
     Photon ph;
     Walk w;
     float tau = 0.f;
-    uint32_t nev = 0u;  // replay: events of pass 1 (0 while in pass 1)
-    double acc = 0.0;   // replay: W in pass 1, S in pass 2
+    uint32_t nev = 0u;  // pass 2: events of pass 1
+    double acc = 0.0;   // pass 1: W; pass 2: S
     bool fly = false, dry = false;
     uint32_t wbase = 0u, wend = 0u;
     Tally t;
@@ -413,24 +421,38 @@ __global__ void __launch_bounds__(kTB, MODE == 2 ? kMinBlocksReplay : kMinBlocks
             rd_n -= take;
             __syncwarp();
         }
-        refill(A, fly, dry, wbase, wend, lane, [&](uint32_t pid) {
-            launch_photon(A, ph, pid);
-            walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
-            tau = ph.tau;
-            nev = 0u;
-            acc = 0.0;
-            if (!REPLAY) {
-                t.launched += A.I0;
-                t.traced += 1u;
-            }
-        });
+        refill(
+            A, fly, dry, wbase, wend, lane,
+            [&](uint32_t pid) -> bool {
+                nev = 0u;
+                acc = 0.0;
+                if (PASS2) {
+                    acc = A.wbuf[pid];
+                    nev = A.nevbuf[pid];
+                    if (acc == 0.0 || nev == 0u) return false;
+                }
+                launch_photon(A, ph, pid);
+                walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+                tau = ph.tau;
+                if (!REPLAY) {
+                    t.launched += A.I0;
+                    t.traced += 1u;
+                }
+                return true;
+            },
+            [&](uint32_t pid) {
+                if (PASS1) {
+                    A.wbuf[pid] = 0.0;
+                    A.nevbuf[pid] = 0u;
+                }
+            });
         const bool any_fly = __any_sync(kFull, fly);
         if (!any_fly && ev_n == 0 && rd_n == 0 && dry) break;
 
         // (2) one voxel for every flying photon
         int r = -1;
         if (fly) {
-            const float S = (REPLAY && nev != 0u) ? (float)acc : 0.f;
+            const float S = PASS2 ? (float)acc : 0.f;
 #pragma unroll 1
             for (int q = 0; q < kStepsPerTrip && r == -1; ++q) {
                 ++t.segments;
@@ -444,14 +466,11 @@ __global__ void __launch_bounds__(kTB, MODE == 2 ? kMinBlocksReplay : kMinBlocks
             fly = false;
         } else if (fly && r >= 0) {
             if (REPLAY) {
-                if (nev == 0u && acc != 0.0 && ph.s > 0u) {  // end of pass 1: replay for pass 2
-                    nev = ph.s;
-                    launch_photon(A, ph, ph.idx - A.out_base);
-                    walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
-                    tau = ph.tau;
-                } else {
-                    fly = false;
+                if (PASS1) {
+                    A.wbuf[ph.idx - A.out_base] = acc;
+                    A.nevbuf[ph.idx - A.out_base] = ph.s;
                 }
+                fly = false;
             } else {
 #pragma unroll
                 for (int q = 0; q < 6; ++q)
@@ -486,18 +505,17 @@ __global__ void __launch_bounds__(kTB, MODE == 2 ? kMinBlocksReplay : kMinBlocks
                     if (term) finish_photon(A, e, term);
                 } else {
                     const float we = le_adjoint(A, e, wgt, k);
-                    if (enev == 0u) eacc += (double)we;
-                    else eacc -= (double)we;
-                    if (enev != 0u && e.s == enev) {
-                        term = 1;  // last event of pass 2
-                    } else {
-                        Tally dummy;
+                    Tally dummy;
+                    if (PASS1) {
+                        eacc += (double)we;
                         term = after_event(A, e, dummy);
-                        if (term && enev == 0u && eacc != 0.0) {  // end of pass 1: replay for pass 2
-                            enev = e.s;
-                            launch_photon(A, e, e.idx - A.out_base);
-                            term = 0;
+                        if (term) {
+                            A.wbuf[e.idx - A.out_base] = eacc;
+                            A.nevbuf[e.idx - A.out_base] = e.s;
                         }
+                    } else {
+                        eacc -= (double)we;
+                        term = e.s == enev ? 1 : after_event(A, e, dummy);  // stop at pass 1's last event
                     }
                 }
             }
@@ -558,46 +576,47 @@ int occupancy(K kern, size_t smem) {
     return n;
 }
 
+template <int DT, int MODE>
+cudaError_t launch_mode(const TransportArgs& a, int blocks, cudaStream_t st) {
+    k_transport<DT, MODE><<<blocks, kTB, smem_bytes<(MODE >= 2)>(), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int DT>
+int occupancy_mode(int mode) {
+    switch (mode) {
+        case kFwdVoxel: return occupancy(k_transport<DT, kFwdVoxel>, smem_bytes<false>());
+        case kFwdClassic: return occupancy(k_transport<DT, kFwdClassic>, smem_bytes<false>());
+        case kPass2: return occupancy(k_transport<DT, kPass2>, smem_bytes<true>());
+        default: return occupancy(k_transport<DT, kPass1>, smem_bytes<true>());
+    }
+}
+
+template <int DT>
+cudaError_t launch_dt(const TransportArgs& a, int mode, int blocks, cudaStream_t st) {
+    switch (mode) {
+        case kFwdVoxel: return launch_mode<DT, kFwdVoxel>(a, blocks, st);
+        case kFwdClassic: return launch_mode<DT, kFwdClassic>(a, blocks, st);
+        case kPass2: return launch_mode<DT, kPass2>(a, blocks, st);
+        default: return launch_mode<DT, kPass1>(a, blocks, st);
+    }
+}
+
 }  // namespace
 
-int transport_blocks_per_sm(int dtype, int estimator, bool replay) {
-    static int cache[3][3] = {{0}};
-    const int col = replay ? 2 : estimator;
-    if (cache[dtype][col]) return cache[dtype][col];
-    int n = 1;
-#define MST_OCC(DT)                                                                  \
-    if (dtype == DT) {                                                               \
-        if (replay) n = occupancy(k_transport<DT, 2>, smem_bytes<true>());           \
-        else if (estimator == 0) n = occupancy(k_transport<DT, 0>, smem_bytes<false>()); \
-        else n = occupancy(k_transport<DT, 1>, smem_bytes<false>());                 \
-    }
-    MST_OCC(0) MST_OCC(1) MST_OCC(2)
-#undef MST_OCC
-    cache[dtype][col] = n;
+int transport_blocks_per_sm(int dtype, int mode) {
+    static int cache[3][4] = {{0}};
+    if (cache[dtype][mode]) return cache[dtype][mode];
+    const int n = dtype == 0 ? occupancy_mode<0>(mode) : (dtype == 1 ? occupancy_mode<1>(mode) : occupancy_mode<2>(mode));
+    cache[dtype][mode] = n;
     return n;
 }
 
-cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int estimator, int blocks,
+cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int mode, int blocks,
                              cudaStream_t st) {
     (void)g;
-    const size_t sm = smem_bytes<false>();
-#define MST_TR(DT)                                                                   \
-    if (dtype == DT) {                                                               \
-        if (estimator == 0) k_transport<DT, 0><<<blocks, kTB, sm, st>>>(a);          \
-        else k_transport<DT, 1><<<blocks, kTB, sm, st>>>(a);                         \
-    }
-    MST_TR(0) MST_TR(1) MST_TR(2)
-#undef MST_TR
-    return cudaGetLastError();
-}
-
-cudaError_t launch_replay(const mst_grid* g, const TransportArgs& a, int dtype, int blocks, cudaStream_t st) {
-    (void)g;
-    const size_t sm = smem_bytes<true>();
-    if (dtype == 0) k_transport<0, 2><<<blocks, kTB, sm, st>>>(a);
-    else if (dtype == 1) k_transport<1, 2><<<blocks, kTB, sm, st>>>(a);
-    else k_transport<2, 2><<<blocks, kTB, sm, st>>>(a);
-    return cudaGetLastError();
+    return dtype == 0 ? launch_dt<0>(a, mode, blocks, st)
+                      : (dtype == 1 ? launch_dt<1>(a, mode, blocks, st) : launch_dt<2>(a, mode, blocks, st));
 }
 
 cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st) {
