@@ -7,6 +7,8 @@
 // time and advances it one free flight plus one event per loop trip; lanes whose photon has
 // ended take a new photon id from a warp-local pool that lane 0 refills from a global ticket,
 // so the warp stays full until the chunk runs dry.
+#include <type_traits>
+
 #include "mst_internal.h"
 
 namespace mst {
@@ -27,20 +29,47 @@ struct Photon {
     uint32_t idx;    // call-relative index (hash / skip arrays)
 };
 
+// Photon tallies of the forward render, per thread in registers (reduced over the warp at the
+// end). The replay passes keep none: their NoTally compiles every update away, which leaves
+// the registers to the walk.
 struct Tally {
     float esc[6];
     float absorbed, killed, gained, forced, launched;
-    unsigned long long events, segments, scatters;
-    unsigned int capped, escaped, traced, lost;
+    unsigned capped, escaped, traced, lost;
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) esc[q] = 0.f;
+        absorbed = killed = gained = forced = launched = 0.f;
+        capped = escaped = traced = lost = 0u;
+    }
+    __device__ __forceinline__ void add_absorbed(float v) { absorbed += v; }
+    __device__ __forceinline__ void add_forced(float v) { forced += v; }
+    __device__ __forceinline__ void add_gained(float v) { gained += v; }
+    __device__ __forceinline__ void add_killed(float v) { killed += v; }
+    __device__ __forceinline__ void add_capped() { ++capped; }
+    __device__ __forceinline__ void add_launch(float i0) {
+        launched += i0;
+        ++traced;
+    }
+    __device__ __forceinline__ void add_escape(int face, float v) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            if (q == face) esc[q] += v;
+        if (face == kWalkOverflow) ++lost;
+        else ++escaped;
+    }
 };
 
-__device__ __forceinline__ void tally_zero(Tally& t) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) t.esc[q] = 0.f;
-    t.absorbed = t.killed = t.gained = t.forced = t.launched = 0.f;
-    t.events = t.segments = t.scatters = 0ull;
-    t.capped = t.escaped = t.traced = t.lost = 0u;
-}
+struct NoTally {
+    __device__ __forceinline__ void zero() {}
+    __device__ __forceinline__ void add_absorbed(float) {}
+    __device__ __forceinline__ void add_forced(float) {}
+    __device__ __forceinline__ void add_gained(float) {}
+    __device__ __forceinline__ void add_killed(float) {}
+    __device__ __forceinline__ void add_capped() {}
+    __device__ __forceinline__ void add_launch(float) {}
+    __device__ __forceinline__ void add_escape(int, float) {}
+};
 
 // Voxel and offset of u * n voxels, u = (2m + 1) / 2^24 from a Philox word: (2m + 1) n / 2^24 is
 // split exactly in integers, so the offset keeps all 24 bits of u.
@@ -76,7 +105,7 @@ constexpr int kCollided = -2;
 
 template <int DT>
 __device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, Walk& w, float& tau, float S,
-                                           unsigned long long& nsc) {
+                                           unsigned& nsc) {
     const float b = BetaFetch<DT>::get(A.beta, w.addr);
     float seg;
     const int a = walk_axis(w, seg);
@@ -180,26 +209,27 @@ __device__ __forceinline__ void le_classic(const TransportArgs& A, const Photon&
 
 // step v (albedo weighting, Russian roulette) and step vi (HG direction, next free path).
 // Returns 0 to continue or the termination code.
-__device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, Tally& t) {
-    t.absorbed += (1.f - A.albedo) * ph.I;
+template <typename TallyT>
+__device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, TallyT& t) {
+    t.add_absorbed((1.f - A.albedo) * ph.I);
     ph.I *= A.albedo;
     if (ph.I == 0.f) return 2;
     if (A.max_order > 0 && (int)ph.s >= A.max_order) {
-        t.forced += ph.I;
+        t.add_forced(ph.I);
         return 4;
     }
     if ((int)ph.s >= A.max_events) {
-        t.forced += ph.I;
-        t.capped += 1u;
+        t.add_forced(ph.I);
+        t.add_capped();
         return 5;
     }
     const float4 u = draws(A.key, ph.id, ph.s);
     if (ph.I < A.rr_below) {
         if (u.z < A.rr_survival) {
-            t.gained += ph.I * (A.inv_rr_survival - 1.f);
+            t.add_gained(ph.I * (A.inv_rr_survival - 1.f));
             ph.I *= A.inv_rr_survival;
         } else {
-            t.killed += ph.I;
+            t.add_killed(ph.I);
             return 3;
         }
     }
@@ -232,7 +262,7 @@ constexpr int kStepsForward = 8;
 constexpr int kStepsPass1 = 8;
 constexpr int kStepsPass2 = 2;
 constexpr int kMinBlocksForward = 1;
-constexpr int kMinBlocksPass1 = 1;
+constexpr int kMinBlocksPass1 = 3;
 constexpr int kMinBlocksPass2 = 3;
 
 // kernel modes
@@ -338,7 +368,8 @@ __device__ __forceinline__ void refill(const TransportArgs& A, bool& fly, bool& 
     }
 }
 
-__device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally& t, unsigned lane) {
+__device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally& t, unsigned segments,
+                                            unsigned events, unsigned lane) {
     double v[11];
 #pragma unroll
     for (int q = 0; q < 6; ++q) v[q] = warp_sum((double)t.esc[q]);
@@ -347,7 +378,7 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
     v[8] = warp_sum((double)t.gained);
     v[9] = warp_sum((double)t.forced);
     v[10] = warp_sum((double)t.launched);
-    const unsigned long long ev = warp_sumu(t.events), sg = warp_sumu(t.segments);
+    const unsigned long long ev = warp_sumu(events), sg = warp_sumu(segments);
     const unsigned long long cap = warp_sumu(t.capped), esc = warp_sumu(t.escaped), tr = warp_sumu(t.traced);
     const unsigned long long lost = warp_sumu(t.lost);
     if (lane == 0u) {
@@ -396,6 +427,9 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
     const Stack<NW> rdq{smem + warp * NW * (kEvCap + kRdCap) + NW * kEvCap, kRdCap};
     int ev_n = 0, rd_n = 0;  // warp-uniform stack heights
 
+    typename std::conditional<REPLAY, NoTally, Tally>::type t;  // photon tallies: forward render only
+    t.zero();
+
     Photon ph;
     Walk w;
     float tau = 0.f;
@@ -403,8 +437,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
     double acc = 0.0;   // pass 1: W; pass 2: S
     bool fly = false, dry = false;
     uint32_t wbase = 0u, wend = 0u;
-    Tally t;
-    tally_zero(t);
+    unsigned segments = 0u, scatters = 0u, events = 0u;
 
     for (;;) {
         // (1) fill: ready photons first, new photons only when the ready stack is empty
@@ -434,10 +467,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                 launch_photon(A, ph, pid);
                 walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
                 tau = ph.tau;
-                if (!REPLAY) {
-                    t.launched += A.I0;
-                    t.traced += 1u;
-                }
+                t.add_launch(A.I0);
                 return true;
             },
             [&](uint32_t pid) {
@@ -455,8 +485,8 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
             const float S = PASS2 ? (float)acc : 0.f;
 #pragma unroll 1
             for (int q = 0; q < kStepsPerTrip && r == -1; ++q) {
-                ++t.segments;
-                r = flight_step<DT>(A, ph, w, tau, S, t.scatters);
+                ++segments;
+                r = flight_step<DT>(A, ph, w, tau, S, scatters);
             }
         }
         const bool collided = fly && r == kCollided;
@@ -472,11 +502,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                 }
                 fly = false;
             } else {
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    if (q == r) t.esc[q] += ph.I;
-                if (r == kWalkOverflow) t.lost += 1u;
-                else t.escaped += 1u;
+                t.add_escape(r, ph.I);
                 finish_photon(A, ph, 1);
                 fly = false;
             }
@@ -494,7 +520,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
             if ((int)lane < n) {
                 get(evq, ev_n - 1 - (int)lane, A, e, enev, eacc);
                 e.s += 1u;
-                t.events += 1ull;
+                ++events;
                 const int k = lin_index(A.g, e.ix, e.iy, e.iz);
                 const float wgt = A.albedo * e.I;
                 if (!REPLAY) {
@@ -505,17 +531,16 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                     if (term) finish_photon(A, e, term);
                 } else {
                     const float we = le_adjoint(A, e, wgt, k);
-                    Tally dummy;
                     if (PASS1) {
                         eacc += (double)we;
-                        term = after_event(A, e, dummy);
+                        term = after_event(A, e, t);
                         if (term) {
                             A.wbuf[e.idx - A.out_base] = eacc;
                             A.nevbuf[e.idx - A.out_base] = e.s;
                         }
                     } else {
                         eacc -= (double)we;
-                        term = e.s == enev ? 1 : after_event(A, e, dummy);  // stop at pass 1's last event
+                        term = e.s == enev ? 1 : after_event(A, e, t);  // stop at pass 1's last event
                     }
                 }
             }
@@ -527,15 +552,15 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
             __syncwarp();
         }
     }
-    if (REPLAY) {
-        const unsigned long long ev = warp_sumu(t.events), sg = warp_sumu(t.segments), sc = warp_sumu(t.scatters);
+    if constexpr (REPLAY) {
+        const unsigned long long ev = warp_sumu(events), sg = warp_sumu(segments), sc = warp_sumu(scatters);
         if (lane == 0u) {
             atomicAdd(A.stats + MST_ST_REPLAY_EVENTS, (double)ev);
             atomicAdd(A.stats + MST_ST_REPLAY_SEGMENTS, (double)sg);
             atomicAdd(A.stats + MST_ST_REPLAY_SCATTERS, (double)sc);
         }
     } else {
-        flush_tally(A, t, lane);
+        flush_tally(A, t, segments, events, lane);
     }
 }
 
