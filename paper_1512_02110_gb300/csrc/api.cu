@@ -137,6 +137,8 @@ TransportArgs transport_args(mst_grid* g, const mst_params* p) {
     a.gacc = g->gacc;
     a.wbuf = g->wbuf;
     a.nevbuf = g->nevbuf;
+    a.plist = g->plist;
+    a.plist_n = g->score_cnt + 2 * kScoreBins;
     a.stats = g->stats;
     a.hash = g->dbg_hash;
     a.skip = g->dbg_skip;
@@ -165,6 +167,7 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
             {
                 Phase ph(g, MST_PH_REPLAY, st);
                 MST_CK(launch_transport(g, a, p->grid_dtype, 3, b_p1, st));
+                MST_CK(launch_score_list(g, a.n, st));
             }
             a.ticket = g->tickets + 2 * c + 1;
             {
@@ -215,7 +218,7 @@ double radical_inverse(int base, int i) {
 
 void free_all(mst_grid* g) {
     void* ptrs[] = {g->bricks, g->Lacc, g->L64, g->T, g->R, g->bacc, g->gT, g->adj, g->gacc, g->g64,
-                    g->resid, g->lap, g->omega, g->Qw, g->stats, g->tickets, g->wbuf, g->nevbuf};
+                    g->resid, g->lap, g->omega, g->Qw, g->stats, g->tickets, g->wbuf, g->nevbuf, g->plist, g->score_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -365,6 +368,8 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
         {(void**)&g->gacc, nvox * 4},
         {(void**)&g->wbuf, kChunk * 8},
         {(void**)&g->nevbuf, kChunk * 4},
+        {(void**)&g->plist, kChunk * sizeof(ScoreRec)},
+        {(void**)&g->score_cnt, (2 * kScoreBins + 1) * 4},
         {(void**)&g->g64, nvox * 8},
         {(void**)&g->resid, (size_t)off * 8},
         {(void**)&g->lap, nvox * 8},

@@ -17,6 +17,14 @@ namespace mst {
 constexpr uint64_t kChunk = 1ull << 22;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
 constexpr int kMaxChunks = 4096;
+constexpr int kScoreBins = 64;  // replay pass-2 list bins over the pass-1 event count (multiple of 32)
+
+// A photon that replay pass 2 must walk: index in the chunk, event count and W of pass 1.
+struct ScoreRec {
+    uint32_t pid;
+    uint32_t nev;
+    double W;
+};
 
 struct TransportArgs {
     Geo g;
@@ -36,8 +44,10 @@ struct TransportArgs {
     const float* omega;        // [total pix] pixel solid angles (classic estimator)
     const float* adj;          // [nvox][cp] a_c(k) = T_c(k) b_c(k) (replay)
     float* gacc;               // [nvox] FP32 gradient accumulator (replay)
-    double* wbuf;              // [kChunk] W per photon of the chunk (replay pass 1 -> pass 2)
-    uint32_t* nevbuf;          // [kChunk] events per photon of the chunk (replay pass 1 -> pass 2)
+    double* wbuf;              // [kChunk] W per photon of the chunk (replay pass 1)
+    uint32_t* nevbuf;          // [kChunk] events per photon of the chunk (replay pass 1)
+    const ScoreRec* plist;     // [kChunk] photons with W != 0 (replay pass 2)
+    const unsigned int* plist_n;  // entries in plist
     double* stats;             // [MST_NSTATS]
     uint32_t* hash;            // per-photon checksum or NULL
     const uint8_t* skip;       // per-photon skip mask or NULL
@@ -68,6 +78,8 @@ struct mst_grid {
     float* gacc = nullptr;        // [nvox]
     double* wbuf = nullptr;       // [kChunk]
     uint32_t* nevbuf = nullptr;   // [kChunk]
+    mst::ScoreRec* plist = nullptr;     // [kChunk]
+    unsigned int* score_cnt = nullptr;  // [2 kScoreBins + 1] list bin counts, bin fill, list length
     double* g64 = nullptr;        // [nvox]
     double* resid = nullptr;      // [total_pix] 2 M (i - i_meas)
     double* lap = nullptr;        // [nvox] Lap beta
@@ -101,6 +113,7 @@ cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtyp
                              cudaStream_t st);
 cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st);
 cudaError_t launch_fold_grad(const mst_grid* g, cudaStream_t st);
+cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st);
 cudaError_t launch_los(const mst_grid* g, int dtype, const double* L, const double* jfix, const float* beta_ref,
                        const float* beta, float* T_out, float* R_out, cudaStream_t st);
 cudaError_t launch_images(const mst_grid* g, const float* R, double* images, const double* meas, const uint8_t* mask,

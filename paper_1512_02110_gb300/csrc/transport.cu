@@ -29,34 +29,53 @@ struct Photon {
     uint32_t idx;    // call-relative index (hash / skip arrays)
 };
 
-// Photon tallies of the forward render, per thread in registers (reduced over the warp at the
-// end). The replay passes keep none: their NoTally compiles every update away, which leaves
-// the registers to the walk.
+// Photon tallies of the forward render: per-thread totals, reduced over the warp at the end.
 struct Tally {
     float esc[6];
     float absorbed, killed, gained, forced, launched;
     unsigned capped, escaped, traced, lost;
+};
+
+// The forward render keeps its tallies in shared memory, one slot per thread (stride kTB
+// words, so a warp's lanes touch consecutive words): no atomics and no registers held across
+// the voxel loop. The replay passes keep none: their NoTally compiles every update away.
+struct LaneTally {
+    float* f;  // 11 float fields at f[q * kTB]
+    unsigned* u;  // 4 counters at u[q * kTB]
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) esc[q] = 0.f;
-        absorbed = killed = gained = forced = launched = 0.f;
-        capped = escaped = traced = lost = 0u;
+        for (int q = 0; q < 11; ++q) f[q * kTB] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[q * kTB] = 0u;
     }
-    __device__ __forceinline__ void add_absorbed(float v) { absorbed += v; }
-    __device__ __forceinline__ void add_forced(float v) { forced += v; }
-    __device__ __forceinline__ void add_gained(float v) { gained += v; }
-    __device__ __forceinline__ void add_killed(float v) { killed += v; }
-    __device__ __forceinline__ void add_capped() { ++capped; }
+    __device__ __forceinline__ void add_absorbed(float v) { f[6 * kTB] += v; }
+    __device__ __forceinline__ void add_killed(float v) { f[7 * kTB] += v; }
+    __device__ __forceinline__ void add_gained(float v) { f[8 * kTB] += v; }
+    __device__ __forceinline__ void add_forced(float v) { f[9 * kTB] += v; }
+    __device__ __forceinline__ void add_capped() { u[0] += 1u; }
     __device__ __forceinline__ void add_launch(float i0) {
-        launched += i0;
-        ++traced;
+        f[10 * kTB] += i0;
+        u[2 * kTB] += 1u;
     }
     __device__ __forceinline__ void add_escape(int face, float v) {
+        if (face < 6) f[face * kTB] += v;
+        if (face == kWalkOverflow) u[3 * kTB] += 1u;
+        else u[1 * kTB] += 1u;
+    }
+    __device__ __forceinline__ Tally load() const {
+        Tally t;
 #pragma unroll
-        for (int q = 0; q < 6; ++q)
-            if (q == face) esc[q] += v;
-        if (face == kWalkOverflow) ++lost;
-        else ++escaped;
+        for (int q = 0; q < 6; ++q) t.esc[q] = f[q * kTB];
+        t.absorbed = f[6 * kTB];
+        t.killed = f[7 * kTB];
+        t.gained = f[8 * kTB];
+        t.forced = f[9 * kTB];
+        t.launched = f[10 * kTB];
+        t.capped = u[0];
+        t.escaped = u[1 * kTB];
+        t.traced = u[2 * kTB];
+        t.lost = u[3 * kTB];
+        return t;
     }
 };
 
@@ -254,6 +273,7 @@ __device__ __forceinline__ void finish_photon(const TransportArgs& A, const Phot
 // launch a warp holds 32 flying + at most 31 queued photons and never more than 63 in total;
 // neither stack can overflow.
 
+constexpr int kScoreTile = 4096;   // photons per block in the list kernels
 constexpr int kEvCap = 64;
 constexpr int kRdCap = 64;
 // Voxels a flying lane advances per loop trip, and minimum resident blocks per SM (register
@@ -261,7 +281,8 @@ constexpr int kRdCap = 64;
 constexpr int kStepsForward = 8;
 constexpr int kStepsPass1 = 8;
 constexpr int kStepsPass2 = 2;
-constexpr int kMinBlocksForward = 1;
+constexpr int kMinBlocksForward = 3;  // voxel estimator; the classic one keeps a 1-block budget
+constexpr int kMinBlocksClassic = 1;
 constexpr int kMinBlocksPass1 = 3;
 constexpr int kMinBlocksPass2 = 3;
 
@@ -334,35 +355,28 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Warp-uniform refill from the photon id pool: lanes without a photon take the next ids of the
-// warp's slice, lane 0 refilling the slice from the chunk's global ticket.
-template <typename LaunchFn, typename SkipFn>
-__device__ __forceinline__ void refill(const TransportArgs& A, bool& fly, bool& dry, uint32_t& wbase, uint32_t& wend,
-                                       unsigned lane, LaunchFn&& on_launch, SkipFn&& on_skip) {
+// Warp-uniform refill from the pool of n work items: lanes without a photon take the next
+// items of the warp's slice, lane 0 refilling the slice from the chunk's global ticket.
+// on_launch(j) starts item j and returns whether the lane now has a photon.
+template <typename LaunchFn>
+__device__ __forceinline__ void refill(const TransportArgs& A, uint32_t n, bool& fly, bool& dry, uint32_t& wbase,
+                                       uint32_t& wend, unsigned lane, LaunchFn&& on_launch) {
     unsigned need = __ballot_sync(kFull, !fly);
     while (need != 0u && !dry) {
         if (wbase >= wend) {
             unsigned t0 = 0u;
             if (lane == 0u) t0 = atomicAdd(A.ticket, (unsigned)kTicketBatch);
             t0 = __shfl_sync(kFull, t0, 0);
-            if (t0 >= A.n) {
+            if (t0 >= n) {
                 dry = true;
                 break;
             }
             wbase = t0;
-            wend = min(t0 + (unsigned)kTicketBatch, A.n);
+            wend = min(t0 + (unsigned)kTicketBatch, n);
         }
         const unsigned rank = __popc(need & lanemask_lt());
         const unsigned avail = wend - wbase;
-        if (!fly && rank < avail) {
-            const uint32_t pid = wbase + rank;
-            if (A.skip && A.skip[A.out_base + pid]) {
-                if (A.hash) A.hash[A.out_base + pid] = 0u;
-                on_skip(pid);
-            } else {
-                fly = on_launch(pid);
-            }
-        }
+        if (!fly && rank < avail) fly = on_launch(wbase + rank);
         wbase += min((unsigned)__popc(need), avail);
         need = __ballot_sync(kFull, !fly);
     }
@@ -408,13 +422,15 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
 // photons that go on are pushed onto the ready stack.
 //
 // Replay adjoint, two launches per chunk. Pass 1 (MODE 3) walks every photon and stores
-// W = sum_s w_s, w_s = sum_c a_c(k_s) albedo I_s P_c(s), and its event count per photon. Pass 2
-// (MODE 2) walks again only the photons with W != 0, with S_j = W - sum_{s<j} w_s (FP64), and
+// W = sum_s w_s, w_s = sum_c a_c(k_s) albedo I_s P_c(s), and its event count per photon; the
+// photons with W != 0 are then gathered into a list, longest first. Pass 2 (MODE 2) walks the
+// listed photons again, with S_j = W - sum_{s<j} w_s (FP64), and
 // scatters the score of every flight that ends in an event; it stops at pass 1's last event.
 // Both passes run the same flight and event arithmetic, so they see the same path.
 template <int DT, int MODE>
 __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
-                                                       : (MODE == kPass1 ? kMinBlocksPass1 : kMinBlocksForward))
+                                                       : (MODE == kPass1 ? kMinBlocksPass1
+                                                          : (MODE == kFwdClassic ? kMinBlocksClassic : kMinBlocksForward)))
     k_transport(const TransportArgs A) {
     constexpr bool REPLAY = MODE == kPass1 || MODE == kPass2;
     constexpr bool PASS1 = MODE == kPass1, PASS2 = MODE == kPass2;
@@ -427,7 +443,13 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
     const Stack<NW> rdq{smem + warp * NW * (kEvCap + kRdCap) + NW * kEvCap, kRdCap};
     int ev_n = 0, rd_n = 0;  // warp-uniform stack heights
 
-    typename std::conditional<REPLAY, NoTally, Tally>::type t;  // photon tallies: forward render only
+    // photon tallies: forward render only, one shared-memory slot per thread after the stacks
+    typename std::conditional<REPLAY, NoTally, LaneTally>::type t;
+    if constexpr (!REPLAY) {
+        float* tb = reinterpret_cast<float*>(smem + (kTB / 32) * NW * (kEvCap + kRdCap));
+        t.f = tb + threadIdx.x;
+        t.u = reinterpret_cast<unsigned*>(tb + 11 * kTB) + threadIdx.x;
+    }
     t.zero();
 
     Photon ph;
@@ -438,6 +460,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
     bool fly = false, dry = false;
     uint32_t wbase = 0u, wend = 0u;
     unsigned segments = 0u, scatters = 0u, events = 0u;
+    const uint32_t pool_n = PASS2 ? *A.plist_n : A.n;  // pass 2 walks the list built from pass 1
 
     for (;;) {
         // (1) fill: ready photons first, new photons only when the ready stack is empty
@@ -454,28 +477,29 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
             rd_n -= take;
             __syncwarp();
         }
-        refill(
-            A, fly, dry, wbase, wend, lane,
-            [&](uint32_t pid) -> bool {
-                nev = 0u;
-                acc = 0.0;
-                if (PASS2) {
-                    acc = A.wbuf[pid];
-                    nev = A.nevbuf[pid];
-                    if (acc == 0.0 || nev == 0u) return false;
-                }
-                launch_photon(A, ph, pid);
-                walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
-                tau = ph.tau;
-                t.add_launch(A.I0);
-                return true;
-            },
-            [&](uint32_t pid) {
+        refill(A, pool_n, fly, dry, wbase, wend, lane, [&](uint32_t j) -> bool {
+            uint32_t pid = j;
+            nev = 0u;
+            acc = 0.0;
+            if (PASS2) {  // item j of the pass-1 list
+                const ScoreRec r = A.plist[j];
+                pid = r.pid;
+                nev = r.nev;
+                acc = r.W;
+            } else if (A.skip && A.skip[A.out_base + j]) {
+                if (A.hash) A.hash[A.out_base + j] = 0u;
                 if (PASS1) {
-                    A.wbuf[pid] = 0.0;
-                    A.nevbuf[pid] = 0u;
+                    A.wbuf[j] = 0.0;
+                    A.nevbuf[j] = 0u;
                 }
-            });
+                return false;
+            }
+            launch_photon(A, ph, pid);
+            walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+            tau = ph.tau;
+            t.add_launch(A.I0);
+            return true;
+        });
         const bool any_fly = __any_sync(kFull, fly);
         if (!any_fly && ev_n == 0 && rd_n == 0 && dry) break;
 
@@ -560,7 +584,74 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
             atomicAdd(A.stats + MST_ST_REPLAY_SCATTERS, (double)sc);
         }
     } else {
-        flush_tally(A, t, segments, events, lane);
+        flush_tally(A, t.load(), segments, events, lane);
+    }
+}
+
+// Pass-2 work list. Photons with W != 0 are binned by their pass-1 event count (the last bin
+// takes every count >= kScoreBins - 1) and listed from the highest bin down, so the longest
+// replays start first and the launch does not end on a tail of long photons.
+__device__ __forceinline__ int score_bin(uint32_t nev) { return (int)min(nev, (uint32_t)(kScoreBins - 1)); }
+
+// Step 1: bin counts cnt[b] over the chunk.
+__global__ void __launch_bounds__(kTB) k_score_hist(const double* __restrict__ W, const uint32_t* __restrict__ nev,
+                                                    uint32_t n, unsigned* __restrict__ cnt) {
+    __shared__ unsigned h[kScoreBins];
+    for (int b = threadIdx.x; b < kScoreBins; b += kTB) h[b] = 0u;
+    __syncthreads();
+    const uint32_t lo = blockIdx.x * kScoreTile, hi = min(lo + (uint32_t)kScoreTile, n);
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += kTB) {
+        const uint32_t e = nev[i];
+        if (e != 0u && W[i] != 0.0) atomicAdd(&h[score_bin(e)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kScoreBins; b += kTB)
+        if (h[b]) atomicAdd(&cnt[b], h[b]);
+}
+
+// Step 2: each tile reserves its slots in every bin (fill[b]) and writes its records there;
+// the list length goes to *total.
+__global__ void __launch_bounds__(kTB) k_score_scatter(const double* __restrict__ W, const uint32_t* __restrict__ nev,
+                                                       uint32_t n, const unsigned* __restrict__ cnt,
+                                                       unsigned* __restrict__ fill, unsigned* __restrict__ total,
+                                                       ScoreRec* __restrict__ list) {
+    __shared__ unsigned h[kScoreBins], pos[kScoreBins];
+    for (int b = threadIdx.x; b < kScoreBins; b += kTB) h[b] = 0u;
+    __syncthreads();
+    const uint32_t lo = blockIdx.x * kScoreTile, hi = min(lo + (uint32_t)kScoreTile, n);
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += kTB) {
+        const uint32_t e = nev[i];
+        if (e != 0u && W[i] != 0.0) atomicAdd(&h[score_bin(e)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // bin starts, highest bin first: start[b] = sum_{b' > b} cnt[b']
+        unsigned run = 0u;
+        for (int b0 = kScoreBins - 32; b0 >= 0; b0 -= 32) {
+            const int b = b0 + (int)threadIdx.x;
+            const unsigned c = cnt[b];
+            unsigned incl = c;  // suffix sum within the 32 bins b0 .. b0+31
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_down_sync(kFull, incl, o);
+                if ((int)threadIdx.x + o < 32) incl += v;
+            }
+            const unsigned start = run + incl - c;
+            pos[b] = h[b] ? start + atomicAdd(&fill[b], h[b]) : 0u;
+            run += __shfl_sync(kFull, incl, 0);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) *total = run;
+    }
+    __syncthreads();
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += kTB) {
+        const uint32_t e = nev[i];
+        const double w = W[i];
+        if (e != 0u && w != 0.0) {
+            ScoreRec r;
+            r.pid = i;
+            r.nev = e;
+            r.W = w;
+            list[atomicAdd(&pos[score_bin(e)], 1u)] = r;
+        }
     }
 }
 
@@ -590,7 +681,8 @@ __global__ void k_fold_grad(float* __restrict__ gacc, double* __restrict__ g64, 
 
 template <bool REPLAY>
 constexpr size_t smem_bytes() {
-    return (size_t)(kTB / 32) * Rec<REPLAY>::NW * (kEvCap + kRdCap) * sizeof(uint32_t);
+    return (size_t)(kTB / 32) * Rec<REPLAY>::NW * (kEvCap + kRdCap) * sizeof(uint32_t) +
+           (REPLAY ? 0 : (size_t)kTB * 15 * sizeof(uint32_t));
 }
 
 template <typename K>
@@ -642,6 +734,17 @@ cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtyp
     (void)g;
     return dtype == 0 ? launch_dt<0>(a, mode, blocks, st)
                       : (dtype == 1 ? launch_dt<1>(a, mode, blocks, st) : launch_dt<2>(a, mode, blocks, st));
+}
+
+cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(g->score_cnt, 0, sizeof(unsigned) * (2 * kScoreBins + 1), st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (n + kScoreTile - 1) / kScoreTile;
+    if (blocks == 0u) return cudaSuccess;
+    k_score_hist<<<blocks, kTB, 0, st>>>(g->wbuf, g->nevbuf, n, g->score_cnt);
+    k_score_scatter<<<blocks, kTB, 0, st>>>(g->wbuf, g->nevbuf, n, g->score_cnt, g->score_cnt + kScoreBins,
+                                            g->score_cnt + 2 * kScoreBins, g->plist);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st) {
