@@ -91,7 +91,7 @@ int check_params(mst_grid* g, const mst_params* p, bool photons) {
     if (!std::isfinite(p->reg_eta)) return fail(g, MST_ERR_INVALID_ARG, "reg_eta must be finite");
     if (photons) {
         if (p->n_photons == 0) return fail(g, MST_ERR_INVALID_ARG, "n_photons must be >= 1");
-        if (p->n_photons > kChunk * (uint64_t)kMaxChunks)
+        if (p->n_photons > kMaxPhotons)
             return fail(g, MST_ERR_INVALID_ARG, "n_photons above the per-call limit (split the call)");
         if (p->max_events < 1) return fail(g, MST_ERR_INVALID_ARG, "max_events must be >= 1");
         if (p->max_order < 0) return fail(g, MST_ERR_INVALID_ARG, "max_order must be >= 0");
@@ -139,37 +139,55 @@ TransportArgs transport_args(mst_grid* g, const mst_params* p) {
     a.nevbuf = g->nevbuf;
     a.plist = g->plist;
     a.plist_n = g->score_cnt + 2 * kScoreBins;
+    a.L64 = g->L64;
+    a.g64 = g->g64;
     a.stats = g->stats;
     a.hash = g->dbg_hash;
     a.skip = g->dbg_skip;
     return a;
 }
 
-// Runs the photon transport (forward or replay) in chunks; after each chunk the FP32 tiles
-// are folded into the FP64 results.
+// Rolling-fold slicing of a tile of `bins` bins (see kFoldSweep): slices of a multiple of 32
+// bins, at least 128, such that one sweep takes at most about kFoldSweep photons.
+void set_fold(TransportArgs& a, uint64_t bins) {
+    const uint64_t batches = kFoldSweep / kTicketBatch;
+    uint64_t slice = (bins + batches - 1) / batches;
+    slice = std::max<uint64_t>(128, (slice + 31) / 32 * 32);
+    a.fold_bins = bins;
+    a.fold_slice = (uint32_t)slice;
+    a.fold_nslices = (uint32_t)((bins + slice - 1) / slice);
+}
+
+// Runs the photon transport. The forward render is one launch per kLaunchPhotons photons; the
+// replay runs pass 1, the pass-2 list and pass 2 per kReplayChunk photons (the size of its
+// per-photon buffers). The launches fold their FP32 tiles while they run; a last fold after each
+// launch takes what is left.
 int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cudaStream_t st) {
     TransportArgs a = transport_args(g, p);
     a.cimg = cimg;
     const uint64_t n = p->n_photons;
-    const int nchunks = (int)((n + kChunk - 1) / kChunk);
-    MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * nchunks * (replay ? 2 : 1), st));
+    const uint64_t span = replay ? kReplayChunk : kLaunchPhotons;
+    const int nl = (int)((n + span - 1) / span);
+    MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * nl * (replay ? 2 : 1), st));
     const int est = replay ? 0 : p->estimator;
     const int b_fwd = g->sm_count * transport_blocks_per_sm(p->grid_dtype, est);
     const int b_p1 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, 3);
     const int b_p2 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, 2);
-    for (int c = 0; c < nchunks; ++c) {
-        const uint64_t base = (uint64_t)c * kChunk;
+    if (replay) set_fold(a, (uint64_t)g->geo.nvox);
+    else if (est == MST_EST_VOXEL) set_fold(a, (uint64_t)g->geo.nvox * g->cp);
+    for (int l = 0; l < nl; ++l) {
+        const uint64_t base = (uint64_t)l * span;
         a.first_id = p->photon_offset + base;
         a.out_base = (uint32_t)base;
-        a.n = (uint32_t)((n - base) < kChunk ? (n - base) : kChunk);
+        a.n = (uint32_t)((n - base) < span ? (n - base) : span);
         if (replay) {
-            a.ticket = g->tickets + 2 * c;
+            a.ticket = g->tickets + 2 * l;
             {
                 Phase ph(g, MST_PH_REPLAY, st);
                 MST_CK(launch_transport(g, a, p->grid_dtype, 3, b_p1, st));
                 MST_CK(launch_score_list(g, a.n, st));
             }
-            a.ticket = g->tickets + 2 * c + 1;
+            a.ticket = g->tickets + 2 * l + 1;
             {
                 Phase ph(g, MST_PH_REPLAY2, st);
                 MST_CK(launch_transport(g, a, p->grid_dtype, 2, b_p2, st));
@@ -177,7 +195,7 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
             Phase ph(g, MST_PH_FOLD, st);
             MST_CK(launch_fold_grad(g, st));
         } else {
-            a.ticket = g->tickets + c;
+            a.ticket = g->tickets + l;
             {
                 Phase ph(g, MST_PH_TRANSPORT, st);
                 MST_CK(launch_transport(g, a, p->grid_dtype, est, b_fwd, st));
@@ -187,6 +205,24 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
                 MST_CK(launch_fold_L(g, st));
             }
         }
+    }
+    return MST_OK;
+}
+
+// Per-photon buffers of the replay, allocated by the first full-gradient call.
+int ensure_replay(mst_grid* g) {
+    if (g->wbuf) return MST_OK;
+    if (cudaMalloc(&g->wbuf, kReplayChunk * 8) != cudaSuccess ||
+        cudaMalloc(&g->nevbuf, kReplayChunk * 4) != cudaSuccess ||
+        cudaMalloc(&g->plist, kReplayChunk * sizeof(ScoreRec)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(g->wbuf);
+        cudaFree(g->nevbuf);
+        cudaFree(g->plist);
+        g->wbuf = nullptr;
+        g->nevbuf = nullptr;
+        g->plist = nullptr;
+        return fail(g, MST_ERR_OOM, "replay buffers: out of device memory");
     }
     return MST_OK;
 }
@@ -366,16 +402,13 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
         {(void**)&g->gT, C * nvox * 4},
         {(void**)&g->adj, nvox * g->cp * 4},
         {(void**)&g->gacc, nvox * 4},
-        {(void**)&g->wbuf, kChunk * 8},
-        {(void**)&g->nevbuf, kChunk * 4},
-        {(void**)&g->plist, kChunk * sizeof(ScoreRec)},
         {(void**)&g->score_cnt, (2 * kScoreBins + 1) * 4},
         {(void**)&g->g64, nvox * 8},
         {(void**)&g->resid, (size_t)off * 8},
         {(void**)&g->lap, nvox * 8},
         {(void**)&g->omega, (size_t)off * 4},
         {(void**)&g->stats, MST_NSTATS * 8 + 64},
-        {(void**)&g->tickets, (size_t)kMaxChunks * 8},
+        {(void**)&g->tickets, (size_t)kMaxTickets * 4},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -521,6 +554,8 @@ int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const 
                                             p->conditioning ? g->Qw : nullptr, grad, st));
         }
     } else {
+        rc = ensure_replay(g);
+        if (rc) return rc;
         {
             Phase ph(g, MST_PH_COMBINE, st);
             MST_CK(launch_adjoint_tiles(g, g->T, g->bacc, g->adj, st));
@@ -825,7 +860,8 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
             mst_grid* g = b->grids[i];
             g->prof = false;
             prof_reset(g);
-            const int rc = ensure_q(g, params[i].grad_mode == MST_GRAD_SURROGATE ? params[i].conditioning : 0, st);
+            int rc = ensure_q(g, params[i].grad_mode == MST_GRAD_SURROGATE ? params[i].conditioning : 0, st);
+            if (rc == MST_OK && params[i].grad_mode == MST_GRAD_FULL) rc = ensure_replay(g);  // no allocation in capture
             if (rc) {
                 b->err = g->err;
                 return rc;

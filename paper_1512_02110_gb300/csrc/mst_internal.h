@@ -12,11 +12,16 @@
 
 namespace mst {
 
-// Photons per transport launch. Each launch accumulates into FP32 tiles that are then folded
-// into the FP64 results and cleared, which bounds the number of FP32 additions per bin.
-constexpr uint64_t kChunk = 1ull << 22;
+// The transport accumulates into FP32 tiles. While a launch runs, every new ticket batch of a
+// warp also folds one slice of the tile into the FP64 result (swap to zero, add in FP64), the
+// slices sized so that a sweep over the whole tile takes at most about kFoldSweep photons:
+// no FP32 bin sums more than a sweep's contributions, however many photons a launch traces.
+constexpr uint64_t kMaxPhotons = 1ull << 34;    // photons per call
+constexpr uint64_t kLaunchPhotons = 1ull << 30;  // photons per forward launch (32-bit ticket)
+constexpr uint64_t kReplayChunk = 1ull << 24;    // photons per replay pass-1 / pass-2 pair
+constexpr uint64_t kFoldSweep = 1ull << 21;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
-constexpr int kMaxChunks = 4096;
+constexpr int kMaxTickets = (int)(2 * (kMaxPhotons / kReplayChunk));
 constexpr int kScoreBins = 64;  // replay pass-2 list bins over the pass-1 event count (multiple of 32)
 
 // A photon that replay pass 2 must walk: index in the chunk, event count and W of pass 1.
@@ -44,10 +49,15 @@ struct TransportArgs {
     const float* omega;        // [total pix] pixel solid angles (classic estimator)
     const float* adj;          // [nvox][cp] a_c(k) = T_c(k) b_c(k) (replay)
     float* gacc;               // [nvox] FP32 gradient accumulator (replay)
-    double* wbuf;              // [kChunk] W per photon of the chunk (replay pass 1)
-    uint32_t* nevbuf;          // [kChunk] events per photon of the chunk (replay pass 1)
-    const ScoreRec* plist;     // [kChunk] photons with W != 0 (replay pass 2)
+    double* wbuf;              // [kReplayChunk] W per photon of the chunk (replay pass 1)
+    uint32_t* nevbuf;          // [kReplayChunk] events per photon of the chunk (replay pass 1)
+    const ScoreRec* plist;     // [kReplayChunk] photons with W != 0 (replay pass 2)
     const unsigned int* plist_n;  // entries in plist
+    double* L64;               // [C][nvox] FP64 result the L tile folds into
+    double* g64;               // [nvox] FP64 result the gradient tile folds into
+    uint64_t fold_bins;        // bins of the tile this launch folds while it runs (0: none)
+    uint32_t fold_slice;       // bins per slice (one slice per ticket batch)
+    uint32_t fold_nslices;     // slices per sweep
     double* stats;             // [MST_NSTATS]
     uint32_t* hash;            // per-photon checksum or NULL
     const uint8_t* skip;       // per-photon skip mask or NULL
@@ -76,9 +86,9 @@ struct mst_grid {
     float* gT = nullptr;          // [C][nvox]  W_c^T (L T b)
     float* adj = nullptr;         // [nvox][cp] T_c b_c
     float* gacc = nullptr;        // [nvox]
-    double* wbuf = nullptr;       // [kChunk]
-    uint32_t* nevbuf = nullptr;   // [kChunk]
-    mst::ScoreRec* plist = nullptr;     // [kChunk]
+    double* wbuf = nullptr;       // [kReplayChunk], allocated by the first full-gradient call
+    uint32_t* nevbuf = nullptr;   // [kReplayChunk]
+    mst::ScoreRec* plist = nullptr;     // [kReplayChunk]
     unsigned int* score_cnt = nullptr;  // [2 kScoreBins + 1] list bin counts, bin fill, list length
     double* g64 = nullptr;        // [nvox]
     double* resid = nullptr;      // [total_pix] 2 M (i - i_meas)
@@ -87,7 +97,7 @@ struct mst_grid {
     float* Qw = nullptr;          // [C][nvox] conditioning weights for qw_mode
     int qw_mode = -1;
     double* stats = nullptr;      // [MST_NSTATS]
-    unsigned int* tickets = nullptr;  // [kMaxChunks]
+    unsigned int* tickets = nullptr;  // [kMaxTickets]
 
     // phase profiler: event pairs recorded on the call's stream
     struct ProfRec {

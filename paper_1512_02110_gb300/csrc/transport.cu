@@ -355,12 +355,38 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// One slice of the rolling fold (see kFoldSweep): the warp swaps the slice's FP32 bins to zero
+// and adds what it took to the FP64 result. Transport lanes keep adding to the same bins with
+// 32-bit atomics, so nothing added is lost; each bin's FP32 partial covers at most one sweep.
+template <int MODE>
+__device__ __forceinline__ void fold_slice(const TransportArgs& A, uint32_t batch, unsigned lane) {
+    if constexpr (MODE == kFwdVoxel || MODE == kPass2) {
+        if (A.fold_bins == 0u) return;
+        const uint64_t i0 = (uint64_t)(batch % A.fold_nslices) * A.fold_slice;
+        const uint64_t i1 = min(i0 + A.fold_slice, A.fold_bins);
+        for (uint64_t i = i0 + lane; i < i1; i += 32) {
+            if (MODE == kFwdVoxel) {  // L tile [nvox][cp] -> L64 [C][nvox]
+                const uint64_t k = i / (uint32_t)A.cp;
+                const int c = (int)(i - k * (uint32_t)A.cp);
+                if (c < A.cams.n) {
+                    const float v = atomicExch(A.Lacc + i, 0.f);
+                    if (v != 0.f) atomicAdd(A.L64 + (size_t)c * A.g.nvox + k, (double)v);
+                }
+            } else {  // gradient tile [nvox] -> g64 [nvox]
+                const float v = atomicExch(A.gacc + i, 0.f);
+                if (v != 0.f) atomicAdd(A.g64 + i, (double)v);
+            }
+        }
+    }
+}
+
 // Warp-uniform refill from the pool of n work items: lanes without a photon take the next
-// items of the warp's slice, lane 0 refilling the slice from the chunk's global ticket.
-// on_launch(j) starts item j and returns whether the lane now has a photon.
-template <typename LaunchFn>
+// items of the warp's slice, lane 0 refilling the slice from the launch's global ticket.
+// on_launch(j) starts item j and returns whether the lane now has a photon; on_batch(t0) runs
+// on the whole warp after each new batch.
+template <typename LaunchFn, typename BatchFn>
 __device__ __forceinline__ void refill(const TransportArgs& A, uint32_t n, bool& fly, bool& dry, uint32_t& wbase,
-                                       uint32_t& wend, unsigned lane, LaunchFn&& on_launch) {
+                                       uint32_t& wend, unsigned lane, LaunchFn&& on_launch, BatchFn&& on_batch) {
     unsigned need = __ballot_sync(kFull, !fly);
     while (need != 0u && !dry) {
         if (wbase >= wend) {
@@ -373,6 +399,7 @@ __device__ __forceinline__ void refill(const TransportArgs& A, uint32_t n, bool&
             }
             wbase = t0;
             wend = min(t0 + (unsigned)kTicketBatch, n);
+            on_batch(t0);
         }
         const unsigned rank = __popc(need & lanemask_lt());
         const unsigned avail = wend - wbase;
@@ -499,7 +526,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
             tau = ph.tau;
             t.add_launch(A.I0);
             return true;
-        });
+        }, [&](uint32_t t0) { fold_slice<MODE>(A, t0 / (uint32_t)kTicketBatch, lane); });
         const bool any_fly = __any_sync(kFull, fly);
         if (!any_fly && ev_n == 0 && rd_n == 0 && dry) break;
 

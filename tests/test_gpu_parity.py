@@ -196,13 +196,41 @@ def test_zero_albedo_and_single_photon(m, torch):
     assert h[0] == oracle.render(sc, p1, want_L=False, hashes=True)["hash"][0]
 
 
-def test_chunk_boundary_and_ragged_count(m, torch):
-    """More photons than one transport launch takes (2^22), with a ragged tail."""
+def _tiny_scene():
     shape, h = (4, 4, 4), (60.0, 60.0, 60.0)
     beta = synth.blob_field(shape, h, 1, (60.0, 90.0), 8 * synth.KM, 0.1 * synth.KM, seed=2)
-    sc = f32_scene(synth.make_scene(shape, h, beta, synth.make_cameras([(121.0, 117.0, 1.0)], 8, 8, 70.0)))
+    return f32_scene(synth.make_scene(shape, h, beta, synth.make_cameras([(121.0, 117.0, 1.0)], 8, 8, 70.0)))
+
+
+def test_chunk_boundary_and_ragged_count(m, torch):
+    """4M photons with a ragged count into a 256-bin tile: the rolling fold sweeps the tile
+    (2 slices of 128 bins) every 128 photons while the transport keeps adding to it."""
     p = synth.Params(albedo=0.99, g=0.85, sun_zenith=0.5, n_photons=(1 << 22) + 1003, seed=17)
-    _forward_parity(m, torch, sc, p, name="forward[4^3,chunk+ragged]")
+    _forward_parity(m, torch, _tiny_scene(), p, name="forward[4^3,chunk+ragged]")
+
+
+@pytest.mark.slow
+def test_full_gradient_across_replay_chunks(m, torch):
+    """More photons than one replay chunk (2^24): two pass-1 / list / pass-2 rounds, the
+    second ragged, against the oracle's full gradient."""
+    sc = _tiny_scene()
+    p = synth.Params(albedo=0.99, g=0.85, sun_zenith=0.5, n_photons=(1 << 24) + 1003, seed=23)
+    rng = np.random.default_rng(4)
+    meas = rng.uniform(0.0, 2e-3, sc.n_pix)
+    mask = np.ones(sc.n_pix, np.uint8)
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    skip, _, _ = _diverged(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render_grad(beta, m.make_params(p, grad_mode="full"), dev(meas, np.float64), dev(mask, np.uint8))
+    st = grid.stats()
+    grid.set_debug(None, None)
+    ref = oracle.full_grad(sc, p, meas, mask, skip=skip)
+    el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
+    eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    record("full_gradient_replay_chunks", diverged_frac=skip.mean(), loss_rel=el, grad_rel_l2=eg)
+    assert st["traced"] == p.n_photons - int(skip.sum())
+    assert el < 1e-4 and eg < 1e-3, (el, eg)
 
 
 def test_photon_offset_split(m, torch):
