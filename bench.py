@@ -265,28 +265,43 @@ def run_ours(args):
         ms_job, segs_job = ms_step, segs
     value = segs_job / (ms_job * 1e-3)
 
-    # roofline of the dominant kernel (algorithmic bytes per launch / average launch time). Pass 1
-    # of the replay walks the forward paths again (same segments and events); pass 2 the rest.
+    # Roofline of the dominant kernel. The transport kernels are issue-bound integer / FP32 work
+    # (ncu: DRAM < 1 % and L2 < 20 % of peak, issue slots ~65 % busy, ALU pipe the busiest), so
+    # the binding roof is the lane issue rate: SMs x 4 schedulers x 32 lanes x max SM clock.
+    # Achieved = algorithmic operations per launch / average launch time, with per-unit counts:
+    # 15 per transport segment, 27 per event and camera (local estimate: direction, cosine,
+    # Henyey-Greenstein phase, two MUFU), 35 per event (scattering sample, roulette), 2 per replay
+    # score scatter. Pass 1 walks the forward paths again (same segments and events); pass 2 the
+    # rest. The HBM form (4 B per segment, 8 B per camera per event) is kept beside it.
     C = sc.n_cams
     seg1, ev1 = st["segments"], st["events"]
     seg2, ev2 = st["replay_segments"] - seg1, st["replay_events"] - ev1
+    ops_ev = 27 * C + 35
     kernels = {
-        "k_transport": (phase_acc["transport"], 4 * seg1 + 8 * C * ev1),
-        "k_replay_pass1": (phase_acc["replay"], 4 * seg1 + 4 * C * ev1),
-        "k_replay_pass2": (phase_acc["replay2"], 4 * seg2 + 4 * C * ev2 + 8 * st["replay_scatters"]),
+        "k_transport": (phase_acc["transport"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 8 * C * ev1),
+        "k_replay_pass1": (phase_acc["replay"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 4 * C * ev1),
+        "k_replay_pass2": (phase_acc["replay2"], 15 * seg2 + ops_ev * ev2 + 2 * st["replay_scatters"],
+                           4 * seg2 + 4 * C * ev2 + 8 * st["replay_scatters"]),
     }
     kern = max(kernels, key=lambda k: kernels[k][0][0])
-    (kms, kn), abytes = kernels[kern]
+    (kms, kn), aops, abytes = kernels[kern]
     calls_per_step = kn / args.steps
-    per_launch_bytes = abytes / calls_per_step
     per_launch_s = (kms / kn) * 1e-3
-    achieved = per_launch_bytes / per_launch_s / 1e9
-    peak, peak_kind = peaks()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_ops = props.multi_processor_count * 128 * sm_max * 1e6
+    achieved_ops = aops / calls_per_step / per_launch_s
+    hbm_peak, peak_kind = peaks()
+    hbm_achieved = abytes / calls_per_step / per_launch_s / 1e9
     traffic = traffic_record(kern)
-    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": kms / kn,
+    roofline = {"bound": "alu", "kernel": kern, "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                "unit": "TOP/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz",
+                "algorithmic_ops_per_launch": aops / calls_per_step,
+                "algorithmic_bytes_per_launch": abytes / calls_per_step, "ms_per_launch": kms / kn,
                 "launches_per_step": calls_per_step,
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                        "peak_source": peak_kind},
                 "phase_ms_per_step": {k: v[0] / args.steps for k, v in phase_acc.items()}}
     launches = int(sum(v[1] for v in phase_acc.values()))
 

@@ -71,7 +71,9 @@ enum {
 enum {
     MST_PH_STAGE = 0, MST_PH_TRANSPORT = 1, MST_PH_FOLD = 2, MST_PH_LOS = 3, MST_PH_IMAGES = 4,
     MST_PH_BACKPROJECT = 5, MST_PH_LOS_ADJOINT = 6, MST_PH_REPLAY = 7, MST_PH_COMBINE = 8, MST_PH_REPLAY2 = 9,
-    MST_NPHASES = 10 /* MST_PH_REPLAY: replay pass 1 (W per photon); MST_PH_REPLAY2: pass 2 (scatter) */
+    MST_PH_REPLAY_LIST = 10,
+    MST_NPHASES = 11 /* MST_PH_REPLAY: replay pass 1 (W per photon); MST_PH_REPLAY_LIST: the list of photons
+                        with W != 0 that pass 2 walks; MST_PH_REPLAY2: pass 2 (scatter) */
 };
 
 typedef struct mst_grid mst_grid; /* opaque; owned by the library */

@@ -39,7 +39,8 @@ EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy"
            "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
            "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
            "mst_batch_last_error", "mst_batch_destroy"]
-PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine", "replay2"]
+PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine", "replay2",
+          "replay_list"]
 
 
 class MSTError(RuntimeError):

@@ -185,6 +185,9 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
             {
                 Phase ph(g, MST_PH_REPLAY, st);
                 MST_CK(launch_transport(g, a, p->grid_dtype, 3, b_p1, st));
+            }
+            {
+                Phase ph(g, MST_PH_REPLAY_LIST, st);
                 MST_CK(launch_score_list(g, a.n, st));
             }
             a.ticket = g->tickets + 2 * l + 1;
