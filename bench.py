@@ -393,7 +393,7 @@ def _timed(fn, steps, warmup, flush):
 
 
 def run_batch(args):
-    """Config 5: 16 scenes of uneven size (24^3-96^3, 3-12 cameras, 1e7-1e8 photons log-uniform),
+    """Batched workload: 16 scenes of uneven size (24^3-96^3, 3-12 cameras, 1e7-1e8 photons log-uniform),
     forward + full gradient, as one graph launch vs. 16 sequential calls."""
     import torch
 

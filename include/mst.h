@@ -45,7 +45,7 @@ extern "C" {
 #define MST_MAX_CAMERAS 16
 #define MST_MAX_SUBPIXEL_RAYS 64
 #define MST_NSTATS 32
-#define MST_NOALLOC_MAX_BRICK_VOXELS (1 << 21) /* 8^3-brick slots of mst_transmittance_noalloc */
+#define MST_NOALLOC_MAX_VOXELS (1 << 21) /* largest grid (nx ny nz) of mst_transmittance_noalloc */
 
 /* local estimate used by the forward render */
 enum { MST_EST_VOXEL = 0, MST_EST_CLASSIC = 1 };
@@ -223,10 +223,10 @@ const char *mst_last_error(mst_grid *g);
  * own arena, plugins that may not allocate after start-up). The paper has no counterpart: it
  * computes the same T_c(k) as mst_transmittance (FP32 grid) for the grid and cameras given.
  *   beta_dev [nvox] float, T_dev [C][nvox] float: the caller's buffers.
- * Scratch: a fixed device array of MST_NOALLOC_MAX_BRICK_VOXELS floats (8 MiB) inside the
- * library, held by every GPU that loads it until the process exits. Grids whose 8^3-brick
- * rounding (ceil(nx/8) ceil(ny/8) ceil(nz/8) * 512) exceeds it are rejected with
- * MST_ERR_TOO_LARGE before anything is enqueued (e.g. 128^3 fits, 136 x 128 x 128 does not).
+ * Scratch: a fixed device array of MST_NOALLOC_MAX_VOXELS floats (8 MiB) inside the library,
+ * held by every GPU that loads it until the process exits. Grids of more voxels (nx ny nz) are
+ * rejected with MST_ERR_TOO_LARGE before anything is enqueued (e.g. 128^3 fits, 136 x 128 x 128
+ * does not).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call outside any stream capture. Every call shares the one array and
  * overwrites it; calls whose work overlaps on the GPU (other streams, other threads) race,
@@ -235,7 +235,7 @@ const char *mst_last_error(mst_grid *g);
 int mst_transmittance_noalloc(const mst_grid_desc *grid, int n_cams, const mst_camera *cams, const float *beta_dev,
                               float *T_dev, void *stream);
 
-/* Batched scenes (BASELINE config 5; Sec. 1 photon parallelism across independent scenes).
+/* Batched scenes (many independent scenes of uneven size; Sec. 1 photon parallelism across them).
  * A batch owns one CUDA graph holding the mst_render_grad sequences of n distinct handles, each
  * on its own branch, so scenes of uneven size overlap on the GPU and the whole batch is one
  * graph launch. The graph is captured on the first call (work is enqueued on internal

@@ -116,7 +116,7 @@ TransportArgs transport_args(mst_grid* g, const mst_params* p) {
     a.hg.opg = (float)(1.0 + gg);
     a.hg.tg = (float)(2.0 * gg);
     a.hg.iso = std::fabs(gg) < 1e-6;
-    a.beta = g->bricks;
+    a.beta = g->ext;
     const double th = p->sun_zenith_rad, ph = p->sun_azimuth_rad;
     a.sun = make_float3((float)(-std::sin(th) * std::cos(ph)), (float)(-std::sin(th) * std::sin(ph)),
                         (float)(-std::cos(th)));
@@ -256,7 +256,7 @@ double radical_inverse(int base, int i) {
 }
 
 void free_all(mst_grid* g) {
-    void* ptrs[] = {g->bricks, g->Lacc, g->L64, g->T, g->R, g->bacc, g->gT, g->adj, g->gacc, g->g64,
+    void* ptrs[] = {g->ext, g->Lacc, g->L64, g->T, g->R, g->bacc, g->gT, g->adj, g->gacc, g->g64,
                     g->resid, g->lap, g->omega, g->Qw, g->stats, g->tickets, g->wbuf, g->nevbuf, g->plist, g->score_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -333,13 +333,10 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
     if (g->sm_count < 1) g->sm_count = 1;
     Geo& geo = g->geo;
     geo.nx = d->nx; geo.ny = d->ny; geo.nz = d->nz;
-    geo.nbx = (d->nx + 7) / 8; geo.nby = (d->ny + 7) / 8; geo.nbz = (d->nz + 7) / 8;
     geo.hx = (float)d->dx; geo.hy = (float)d->dy; geo.hz = (float)d->dz;
     geo.ex = (float)(d->nx * d->dx); geo.ey = (float)(d->ny * d->dy); geo.ez = (float)(d->nz * d->dz);
     geo.nvox = d->nx * d->ny * d->nz;
     geo.max_steps = d->nx + d->ny + d->nz + 8;
-    geo.wrap_y = 512 * geo.nbx - 56;
-    geo.wrap_z = 512 * geo.nbx * geo.nby - 448;
     for (int a = 0; a < 3; ++a) g->origin[a] = d->origin[a];
     g->voxel_volume = d->dx * d->dy * d->dz;
     g->n_cams = n_cams;
@@ -391,12 +388,11 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
     }
 
     const size_t nvox = (size_t)geo.nvox, C = (size_t)n_cams;
-    const size_t nbrick_vox = (size_t)geo.nbx * geo.nby * geo.nbz * kBrickVox;
     struct A {
         void** p;
         size_t bytes;
     } allocs[] = {
-        {&g->bricks, nbrick_vox * 4},
+        {&g->ext, nvox * 4},
         {(void**)&g->Lacc, nvox * g->cp * 4},
         {(void**)&g->L64, C * nvox * 8},
         {(void**)&g->T, C * nvox * 4},

@@ -1,7 +1,7 @@
 // Device-side building blocks of the sm_103a path: counter-based random numbers, the
-// Henyey-Greenstein phase function and sampler, direction rotation, the bricked extinction
-// fetch and the FP32 voxel walk (Amanatides-Woo). Positions are in grid-local metres
-// (origin subtracted) so FP32 keeps ~1e-4 m resolution across a 2 km domain.
+// Henyey-Greenstein phase function and sampler, direction rotation, the staged extinction
+// fetch and the FP32 voxel walk (Amanatides-Woo), whose positions are voxel index + offset
+// inside the voxel.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -14,17 +14,13 @@ namespace mst {
 
 constexpr int kMaxCams = 16;
 constexpr int kMaxRays = 64;
-constexpr int kBrickShift = 3;  // 8^3 bricks
-constexpr int kBrickVox = 512;
 
 struct Geo {
     int nx, ny, nz;     // voxels per axis
-    int nbx, nby, nbz;  // 8^3 bricks per axis
     float hx, hy, hz;   // voxel size (m)
     float ex, ey, ez;   // grid extent (m)
     int nvox;
     int max_steps;      // nx + ny + nz + 8: no straight walk crosses more voxels
-    int wrap_y, wrap_z; // brick-address step when a y / z step crosses into the next brick
 };
 
 struct Cam {
@@ -130,14 +126,10 @@ __device__ __forceinline__ float3 rotate_dir(float3 d, float ct, float st, float
 }
 
 // ------------------------------------------------------------------------------------------
-// Extinction storage: 8^3 bricks (2 KB in FP32), x fastest inside a brick, bricks x fastest.
-// A voxel step changes the address by +-1, +-8 or +-64 inside a brick and by a fixed stride
-// when it crosses into the next brick, so walks update it with one add.
-
-__device__ __forceinline__ int brick_addr(const Geo& g, int ix, int iy, int iz) {
-    const int b = (ix >> kBrickShift) + g.nbx * ((iy >> kBrickShift) + g.nby * (iz >> kBrickShift));
-    return (b << 9) | (ix & 7) | ((iy & 7) << 3) | ((iz & 7) << 6);
-}
+// Extinction storage: the grid staged in the compute dtype, x fastest ([nz][ny][nx], the
+// linear voxel index). A voxel step changes the index by +-1, +-nx or +-nx ny, one multiply-add;
+// the whole 64^3 grid is 1 MB and stays in L2, where 8^3 bricks bought no measurable locality
+// but cost the walk a wrap test and two selects per step.
 
 __device__ __forceinline__ int lin_index(const Geo& g, int ix, int iy, int iz) { return ix + g.nx * (iy + g.ny * iz); }
 
@@ -180,8 +172,7 @@ struct Walk {
     float p0x, p0y, p0z;  // offset at the start (kept on axes the ray does not move along)
     int ix, iy, iz;       // current voxel
     int sx, sy, sz;       // step per axis (0 when the direction component is 0)
-    int addr;             // brick address of the current voxel
-    int lin;              // linear index ix + nx (iy + ny iz) of the current voxel
+    int lin;              // linear index ix + nx (iy + ny iz) of the current voxel (its extinction's address)
     int left;             // face crossings left before the walk is abandoned
 };
 
@@ -213,7 +204,6 @@ __device__ __forceinline__ void walk_init(Walk& w, const Geo& g, float3 p, float
     axis_init(fminf(fmaxf(p.z, 0.f), g.hz), d.z, g.hz, w.tz, w.qz, w.az, w.sz);
     w.p0x = p.x; w.p0y = p.y; w.p0z = p.z;
     w.ix = ix; w.iy = iy; w.iz = iz;
-    w.addr = brick_addr(g, ix, iy, iz);
     w.lin = lin_index(g, ix, iy, iz);
     w.left = g.max_steps;
 }
@@ -243,11 +233,6 @@ __device__ __forceinline__ int walk_step(Walk& w, const Geo& g, int a, float seg
     w.ix += bx ? s : 0;
     w.iy += by ? s : 0;
     w.iz += bz ? s : 0;
-    const int i = bx ? w.ix : (by ? w.iy : w.iz);
-    const bool wrap = (i & 7) == (s > 0 ? 0 : 7);
-    const int small = bx ? 1 : (by ? 8 : 64);
-    const int big = bx ? 505 : (by ? g.wrap_y : g.wrap_z);
-    w.addr += s * (wrap ? big : small);
     w.lin += s * (bx ? 1 : (by ? g.nx : g.nx * g.ny));
     const bool out = ((unsigned)w.ix >= (unsigned)g.nx) | ((unsigned)w.iy >= (unsigned)g.ny) |
                      ((unsigned)w.iz >= (unsigned)g.nz);
@@ -329,7 +314,7 @@ __device__ __forceinline__ int cam_of_pixel(const CamSet& cs, int gp) {
 }
 
 // Walks the segment from the point (voxel i, offset p) to the centre of projection of camera c,
-// calling fn(walk, length) for every voxel it crosses (walk.addr / walk.lin name the voxel). The walk ends in the
+// calling fn(walk, length) for every voxel it crosses (walk.lin names the voxel). The walk ends in the
 // camera's voxel (last length = distance to the camera inside it) or, for a camera outside the
 // grid, at the grid face; the remaining distance guards both ends against rounding.
 template <typename F>

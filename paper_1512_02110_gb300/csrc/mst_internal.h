@@ -35,7 +35,7 @@ struct TransportArgs {
     Geo g;
     CamSet cams;
     HG hg;
-    const void* beta;          // staged bricks
+    const void* beta;          // staged extinction [nvox] in the compute dtype
     float3 sun;                // photon direction at launch
     float albedo, I0, rr_below, rr_survival, inv_rr_survival;
     uint2 key;
@@ -77,7 +77,7 @@ struct mst_grid {
     double voxel_volume = 0;
 
     // device buffers owned by the handle
-    void* bricks = nullptr;       // nbricks * 512 * 4 bytes
+    void* ext = nullptr;          // staged extinction [nvox], up to 4 bytes per voxel
     float* Lacc = nullptr;        // [nvox][cp]
     double* L64 = nullptr;        // [C][nvox]
     float* T = nullptr;           // [C][nvox]

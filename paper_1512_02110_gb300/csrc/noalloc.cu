@@ -3,7 +3,7 @@
 // Some callers cannot call cudaMalloc at all: code running inside a CUDA graph capture, a
 // host that hands out device memory only through its own arena, or a plugin whose process
 // forbids allocation after start-up. mst_transmittance_noalloc serves them: it takes no
-// handle, and the only scratch it needs (the extinction grid staged into 8^3 bricks) lives in
+// handle, and the only scratch it needs (the staged extinction grid) lives in
 // a file-scope device array that every GPU loading this library holds until the process ends.
 // The caller passes beta and T; nothing is allocated or freed here.
 #include <cmath>
@@ -14,24 +14,24 @@
 
 namespace {
 
-// 2^21 brick voxel slots (8 MiB of FP32): grids up to 128 x 128 x 128 voxels.
-constexpr int kNoAllocMaxBrickVoxels = 1 << 21;
-static_assert(kNoAllocMaxBrickVoxels == MST_NOALLOC_MAX_BRICK_VOXELS, "header and library disagree");
+// 2^21 voxels (8 MiB of FP32): grids up to 128 x 128 x 128 voxels.
+constexpr int kNoAllocMaxVoxels = 1 << 21;
+static_assert(kNoAllocMaxVoxels == MST_NOALLOC_MAX_VOXELS, "header and library disagree");
 
-static __device__ __align__(256) float g_noalloc_bricks[kNoAllocMaxBrickVoxels];
+static __device__ __align__(256) float g_noalloc_ext[kNoAllocMaxVoxels];
 
-// Device address of g_noalloc_bricks, resolved once per device. In host code the symbol name
+// Device address of g_noalloc_ext, resolved once per device. In host code the symbol name
 // is only a host-side stand-in for the array, so the address must come from the runtime.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
-int bricks_address(int dev, void** out) {
+int ext_address(int dev, void** out) {
     if (dev < 0 || dev >= kMaxDevices) return MST_ERR_NO_DEVICE;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_addr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_bricks) != cudaSuccess || !p) {
+        if (cudaGetSymbolAddress(&p, g_noalloc_ext) != cudaSuccess || !p) {
             cudaGetLastError();
             return MST_ERR_CUDA;
         }
@@ -53,8 +53,7 @@ extern "C" int mst_transmittance_noalloc(const mst_grid_desc* d, int n_cams, con
     if (!(d->dx > 0 && d->dy > 0 && d->dz > 0) || !std::isfinite(d->dx + d->dy + d->dz) || !finite3(d->origin))
         return MST_ERR_INVALID_ARG;
     if (n_cams < 1 || n_cams > MST_MAX_CAMERAS) return MST_ERR_INVALID_ARG;
-    const long long nbx = (d->nx + 7) / 8, nby = (d->ny + 7) / 8, nbz = (d->nz + 7) / 8;
-    if (nbx * nby * nbz * 512 > kNoAllocMaxBrickVoxels) return MST_ERR_TOO_LARGE;
+    if ((long long)d->nx * d->ny * d->nz > kNoAllocMaxVoxels) return MST_ERR_TOO_LARGE;
     const double hh[3] = {d->dx, d->dy, d->dz};
     const int nn[3] = {d->nx, d->ny, d->nz};
     for (int c = 0; c < n_cams; ++c) {
@@ -67,22 +66,19 @@ extern "C" int mst_transmittance_noalloc(const mst_grid_desc* d, int n_cams, con
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MST_ERR_NO_DEVICE;
     void* scratch = nullptr;
-    const int rc = bricks_address(dev, &scratch);
+    const int rc = ext_address(dev, &scratch);
     if (rc != MST_OK) return rc;
 
     // A descriptor on the host stack for the existing launchers: grid geometry, cameras and the
-    // static brick array; no statistics are kept.
+    // static extinction array; no statistics are kept.
     mst_grid g;
     g.device = dev;
     mst::Geo& geo = g.geo;
     geo.nx = d->nx; geo.ny = d->ny; geo.nz = d->nz;
-    geo.nbx = (int)nbx; geo.nby = (int)nby; geo.nbz = (int)nbz;
     geo.hx = (float)d->dx; geo.hy = (float)d->dy; geo.hz = (float)d->dz;
     geo.ex = (float)(d->nx * d->dx); geo.ey = (float)(d->ny * d->dy); geo.ez = (float)(d->nz * d->dz);
     geo.nvox = d->nx * d->ny * d->nz;
     geo.max_steps = d->nx + d->ny + d->nz + 8;
-    geo.wrap_y = 512 * geo.nbx - 56;
-    geo.wrap_z = 512 * geo.nbx * geo.nby - 448;
     g.n_cams = n_cams;
     g.cams.n = n_cams;
     for (int c = 0; c < n_cams; ++c) {
@@ -108,14 +104,14 @@ extern "C" int mst_transmittance_noalloc(const mst_grid_desc* d, int n_cams, con
         t.lx = lv[0]; t.ly = lv[1]; t.lz = lv[2];
         t.inside = inside ? 1 : 0;
     }
-    g.bricks = scratch;
+    g.ext = scratch;
     g.stats = nullptr;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // staging writes every brick slot of this grid (padding included), so no clearing is needed
+    // staging writes every voxel of this grid, so no clearing is needed
     if (mst::launch_stage(&g, beta_dev, MST_GRID_F32, st) != cudaSuccess) return MST_ERR_CUDA;
     if (mst::launch_los(&g, MST_GRID_F32, nullptr, nullptr, nullptr, beta_dev, T_dev, nullptr, st) != cudaSuccess)
         return MST_ERR_CUDA;
-    g.bricks = nullptr;  // not owned
+    g.ext = nullptr;  // not owned
     return MST_OK;
 }

@@ -13,18 +13,13 @@ namespace {
 
 constexpr int kTB = 256;
 
+// The extinction grid in the compute dtype, in the linear voxel order of the input.
 template <int DT>
-__global__ void k_stage(const float* __restrict__ beta, void* __restrict__ bricks, const Geo g, int total) {
+__global__ void k_stage(const float* __restrict__ beta, void* __restrict__ ext, int nvox) {
     typedef typename BetaFetch<DT>::T T;
-    T* out = static_cast<T*>(bricks);
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < total; a += gridDim.x * blockDim.x) {
-        const int b = a >> 9, m = a & 511;
-        const int bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / (g.nbx * g.nby);
-        const int ix = bx * 8 + (m & 7), iy = by * 8 + ((m >> 3) & 7), iz = bz * 8 + (m >> 6);
-        float v = 0.f;
-        if (ix < g.nx && iy < g.ny && iz < g.nz) v = beta[lin_index(g, ix, iy, iz)];
-        out[a] = BetaFetch<DT>::make(v);
-    }
+    T* out = static_cast<T*>(ext);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nvox; k += gridDim.x * blockDim.x)
+        out[k] = BetaFetch<DT>::make(beta[k]);
 }
 
 __device__ __forceinline__ void flush_count(double* stats, int slot, unsigned long long n) {
@@ -36,7 +31,7 @@ __device__ __forceinline__ void flush_count(double* stats, int slot, unsigned lo
 // also R_c(k) = L_c(k) T_c(k) (Eq. Rck), where L = Lsrc * beta / beta_ref when beta_ref is
 // given (the j-fixed surrogate, L = j beta with j = L_ref / beta_ref).
 template <int DT>
-__global__ void __launch_bounds__(kTB) k_los(const Geo g, const CamSet cs, const void* __restrict__ bricks,
+__global__ void __launch_bounds__(kTB) k_los(const Geo g, const CamSet cs, const void* __restrict__ ext,
                                              const double* __restrict__ Lsrc, const float* __restrict__ beta_ref,
                                              const float* __restrict__ beta, float* __restrict__ T_out,
                                              float* __restrict__ R_out, double* stats) {
@@ -48,7 +43,7 @@ __global__ void __launch_bounds__(kTB) k_los(const Geo g, const CamSet cs, const
         const int ix = k % g.nx, iy = (k / g.nx) % g.ny, iz = k / (g.nx * g.ny);
         double tau = 0.0;  // FP64 sum: ~1e-7 relative for optical depths up to ~100
         walk_to_camera(g, cs.c[c], ix, iy, iz, make_float3(0.5f * g.hx, 0.5f * g.hy, 0.5f * g.hz),
-                       [&](const Walk& w, float len) { tau += (double)(BetaFetch<DT>::get(bricks, w.addr) * len); },
+                       [&](const Walk& w, float len) { tau += (double)(BetaFetch<DT>::get(ext, w.lin) * len); },
                        nseg);
         const float T = (float)exp(-tau);
         if (T_out) T_out[idx] = T;
@@ -252,11 +247,11 @@ inline int nblocks(long long n, int tb = kTB, int cap = 1 << 20) {
 }  // namespace
 
 cudaError_t launch_stage(const mst_grid* g, const float* beta, int dtype, cudaStream_t st) {
-    const int total = g->geo.nbx * g->geo.nby * g->geo.nbz * kBrickVox;
-    const int nb = nblocks(total, kTB, 8192);
-    if (dtype == 0) k_stage<0><<<nb, kTB, 0, st>>>(beta, g->bricks, g->geo, total);
-    else if (dtype == 1) k_stage<1><<<nb, kTB, 0, st>>>(beta, g->bricks, g->geo, total);
-    else k_stage<2><<<nb, kTB, 0, st>>>(beta, g->bricks, g->geo, total);
+    const int nvox = g->geo.nvox;
+    const int nb = nblocks(nvox, kTB, 8192);
+    if (dtype == 0) k_stage<0><<<nb, kTB, 0, st>>>(beta, g->ext, nvox);
+    else if (dtype == 1) k_stage<1><<<nb, kTB, 0, st>>>(beta, g->ext, nvox);
+    else k_stage<2><<<nb, kTB, 0, st>>>(beta, g->ext, nvox);
     return cudaGetLastError();
 }
 
@@ -264,9 +259,9 @@ cudaError_t launch_los(const mst_grid* g, int dtype, const double* L, const doub
                        const float* beta, float* T_out, float* R_out, cudaStream_t st) {
     const long long total = (long long)g->n_cams * g->geo.nvox;
     const int nb = nblocks(total);
-    if (dtype == 0) k_los<0><<<nb, kTB, 0, st>>>(g->geo, g->cams, g->bricks, L, beta_ref, beta, T_out, R_out, g->stats);
-    else if (dtype == 1) k_los<1><<<nb, kTB, 0, st>>>(g->geo, g->cams, g->bricks, L, beta_ref, beta, T_out, R_out, g->stats);
-    else k_los<2><<<nb, kTB, 0, st>>>(g->geo, g->cams, g->bricks, L, beta_ref, beta, T_out, R_out, g->stats);
+    if (dtype == 0) k_los<0><<<nb, kTB, 0, st>>>(g->geo, g->cams, g->ext, L, beta_ref, beta, T_out, R_out, g->stats);
+    else if (dtype == 1) k_los<1><<<nb, kTB, 0, st>>>(g->geo, g->cams, g->ext, L, beta_ref, beta, T_out, R_out, g->stats);
+    else k_los<2><<<nb, kTB, 0, st>>>(g->geo, g->cams, g->ext, L, beta_ref, beta, T_out, R_out, g->stats);
     return cudaGetLastError();
 }
 

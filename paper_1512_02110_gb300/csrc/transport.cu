@@ -125,7 +125,7 @@ constexpr int kCollided = -2;
 template <int DT>
 __device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, Walk& w, float& tau, float S,
                                            unsigned& nsc) {
-    const float b = BetaFetch<DT>::get(A.beta, w.addr);
+    const float b = BetaFetch<DT>::get(A.beta, w.lin);
     float seg;
     const int a = walk_axis(w, seg);
     const float bs = b * seg;
@@ -220,7 +220,7 @@ __device__ __forceinline__ void le_classic(const TransportArgs& A, const Photon&
         float tau = 0.f;
         unsigned long long ns = 0;
         walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p,
-                       [&](const Walk& wk, float len) { tau += BetaFetch<DT>::get(A.beta, wk.addr) * len; }, ns);
+                       [&](const Walk& wk, float len) { tau += BetaFetch<DT>::get(A.beta, wk.lin) * len; }, ns);
         const float val = w * hg_phase(A.hg, mu) * expf(-tau) / (r2 * A.omega[gp]);
         atomicAdd(A.cimg + gp, (double)val);
     }
