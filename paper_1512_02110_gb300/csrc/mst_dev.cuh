@@ -176,16 +176,19 @@ struct Walk {
     int left;             // face crossings left before the walk is abandoned
 };
 
+// kFastRcp: 1/|d| by the hardware reciprocal (__fdividef, within 2 ulp) instead of the
+// correctly rounded division; photon flights use it, camera and LOS rays keep the division.
+template <bool kFastRcp>
 __device__ __forceinline__ void axis_init(float p, float d, float h, float& t, float& q, float& a, int& s) {
     if (d > 0.f) {
         a = d;
-        const float inv = 1.f / d;
+        const float inv = kFastRcp ? __fdividef(1.f, d) : 1.f / d;
         t = (h - p) * inv;
         q = h * inv;
         s = 1;
     } else if (d < 0.f) {
         a = -d;
-        const float inv = 1.f / a;
+        const float inv = kFastRcp ? __fdividef(1.f, a) : 1.f / a;
         t = p * inv;
         q = h * inv;
         s = -1;
@@ -198,10 +201,11 @@ __device__ __forceinline__ void axis_init(float p, float d, float h, float& t, f
 }
 
 // p: offset of the start point inside voxel (ix, iy, iz), each in [0, h]
+template <bool kFastRcp = false>
 __device__ __forceinline__ void walk_init(Walk& w, const Geo& g, float3 p, float3 d, int ix, int iy, int iz) {
-    axis_init(fminf(fmaxf(p.x, 0.f), g.hx), d.x, g.hx, w.tx, w.qx, w.ax, w.sx);
-    axis_init(fminf(fmaxf(p.y, 0.f), g.hy), d.y, g.hy, w.ty, w.qy, w.ay, w.sy);
-    axis_init(fminf(fmaxf(p.z, 0.f), g.hz), d.z, g.hz, w.tz, w.qz, w.az, w.sz);
+    axis_init<kFastRcp>(fminf(fmaxf(p.x, 0.f), g.hx), d.x, g.hx, w.tx, w.qx, w.ax, w.sx);
+    axis_init<kFastRcp>(fminf(fmaxf(p.y, 0.f), g.hy), d.y, g.hy, w.ty, w.qy, w.ay, w.sy);
+    axis_init<kFastRcp>(fminf(fmaxf(p.z, 0.f), g.hz), d.z, g.hz, w.tz, w.qz, w.az, w.sz);
     w.p0x = p.x; w.p0y = p.y; w.p0z = p.z;
     w.ix = ix; w.iy = iy; w.iz = iz;
     w.lin = lin_index(g, ix, iy, iz);
@@ -223,7 +227,9 @@ constexpr int kWalkOverflow = 6;
 // Moves seg along the ray and crosses the face on axis a. Returns the exit face (0..5: x-, x+,
 // y-, y+, z-, z+) if the walk left the grid, kWalkOverflow if it made more crossings than any
 // straight line through the grid can (only possible with a non-finite direction), else -1.
-// Branch-free in the axis, so lanes that cross different faces do not diverge.
+// Branch-free in the axis, so lanes that cross different faces do not diverge. Callers that
+// bound the crossings themselves (the transport, once per trip) pass kGuard = false.
+template <bool kGuard = true>
 __device__ __forceinline__ int walk_step(Walk& w, const Geo& g, int a, float seg) {
     const bool bx = a == 0, by = a == 1, bz = a == 2;
     w.tx = bx ? w.qx : w.tx - seg;
@@ -236,7 +242,7 @@ __device__ __forceinline__ int walk_step(Walk& w, const Geo& g, int a, float seg
     w.lin += s * (bx ? 1 : (by ? g.nx : g.nx * g.ny));
     const bool out = ((unsigned)w.ix >= (unsigned)g.nx) | ((unsigned)w.iy >= (unsigned)g.ny) |
                      ((unsigned)w.iz >= (unsigned)g.nz);
-    if (--w.left < 0) return kWalkOverflow;
+    if (kGuard && --w.left < 0) return kWalkOverflow;
     return out ? 2 * a + (s > 0) : -1;
 }
 

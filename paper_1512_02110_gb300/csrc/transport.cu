@@ -146,7 +146,7 @@ __device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, W
         ++nsc;
     }
     tau -= bs;
-    return walk_step(w, A.g, a, seg);
+    return walk_step<false>(w, A.g, a, seg);  // the kernel bounds the crossings once per trip
 }
 
 // cosine between the photon direction and the direction from the photon to camera c, and the
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
             const int take = min(__popc(empty), rd_n);
             if (!fly && rank < take) {
                 get(rdq, rd_n - 1 - rank, A, ph, nev, acc);
-                walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+                walk_init<true>(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
                 tau = ph.tau;
                 fly = true;
             }
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                 return false;
             }
             launch_photon(A, ph, pid);
-            walk_init(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+            walk_init<true>(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
             tau = ph.tau;
             t.add_launch(A.I0);
             return true;
@@ -540,6 +540,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
         int r = -1;
         constexpr int kTripMinActive =
             PASS2 ? kTripMinActivePass2 : (PASS1 ? kTripMinActivePass1 : kTripMinActiveForward);
+        int nstep = 0;
         if constexpr (kTripMinActive > 0) {
             const float S = PASS2 ? (float)acc : 0.f;
 #pragma unroll 1
@@ -547,17 +548,19 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                 const bool go = fly && r == -1;
                 if (q > 0 && __popc(__ballot_sync(kFull, go)) < kTripMinActive) break;
                 if (go) {
-                    ++segments;
+                    ++nstep;
                     r = flight_step<DT>(A, ph, w, tau, S, scatters);
                 }
             }
         } else if (fly) {
             const float S = PASS2 ? (float)acc : 0.f;
 #pragma unroll 1
-            for (int q = 0; q < kStepsPerTrip && r == -1; ++q) {
-                ++segments;
-                r = flight_step<DT>(A, ph, w, tau, S, scatters);
-            }
+            for (; nstep < kStepsPerTrip && r == -1; ++nstep) r = flight_step<DT>(A, ph, w, tau, S, scatters);
+        }
+        if (fly) {  // a flight longer than any straight walk through the grid is abandoned
+            segments += nstep;
+            w.left -= nstep;
+            if (r == -1 && w.left < 0) r = kWalkOverflow;
         }
         const bool collided = fly && r == kCollided;
         const unsigned cmask = __ballot_sync(kFull, collided);
