@@ -47,11 +47,12 @@ def parse():
     ap.add_argument("--grad", default="full", choices=["full", "surrogate"])
     ap.add_argument("--grid-dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--ref-photons", type=float, default=2e4, help="photons per oracle step (bounded sample)")
+    ap.add_argument("--recon-iters", type=int, default=50, help="iterations of --study recon")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
     ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
-    ap.add_argument("--study", default=None, choices=["precision"],
+    ap.add_argument("--study", default=None, choices=["precision", "recon"],
                     help="FP16/BF16 brick forms against FP32 at equal photon count (prints one JSON line)")
     return ap.parse_args()
 
@@ -436,6 +437,54 @@ def run_batch(args):
     return 0
 
 
+def run_recon_study(args):
+    """Reconstruction of the cumulus64 field from its seed-4 images, 1e8 photons per render,
+    from beta = 1 1/km everywhere (Sec. 5 loop at the benchmark scale): projected L-BFGS on the
+    full gradient (common random numbers), and the paper's surrogate loop (Eq. GD, N_GD = 5)
+    under each conditioning of the gradient (none, 1/ray count, ray count). Prints one JSON line
+    with the loss, epsilon = |b - b_true|_1 / |b_true|_1 and delta_mass = (|b|_1 - |b_true|_1) /
+    |b_true|_1 (the paper's two error measures) along each run, and its GPU time."""
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(0)
+    n = int(args.photons)
+    sc, p = synth.cfg_cumulus64(n)
+    grid = m.Grid.from_scene(sc)
+    b_true = sc.beta.astype(np.float64)
+    meas = grid.render(torch.from_numpy(sc.beta.astype(np.float32)).cuda(), m.make_params(p, seed=4))["images"]
+    beta0 = np.full(sc.nvox, 1.0 * synth.KM)
+    t1 = np.abs(b_true).sum()
+
+    def errs(b):
+        return {"epsilon": float(np.abs(b - b_true).sum() / t1), "delta_mass": float((np.abs(b).sum() - t1) / t1)}
+
+    out = {"study": "recon", "photons_per_render": n, "start": "beta = 1 1/km", "initial": errs(beta0)}
+    trace = []
+    t0 = time.perf_counter()
+    st = m.reconstruct(grid, meas, beta0, m.make_params(p, grad_mode="full"), iters=args.recon_iters,
+                       method="lbfgs", callback=lambda s: trace.append({"it": s.it, "loss": s.losses[-1], **errs(s.beta)}))
+    torch.cuda.synchronize()
+    out["lbfgs_full"] = {"iterations": st.it, "renders": st.n_renders, "s": time.perf_counter() - t0,
+                         "loss0": st.losses[0], "trace": trace[::5] + trace[-1:]}
+    for cond in ["none", "inv_count", "count"]:
+        prm = m.make_params(p, grad_mode="surrogate", conditioning=cond)
+        b0 = torch.from_numpy(beta0.astype(np.float32)).cuda()
+        L0 = grid.render(b0, prm, images=False, L=True)["L"]
+        g0 = grid.surrogate_grad(b0, L0, b0, prm, meas)["grad"].cpu().numpy()
+        step = 0.5 * beta0.max() / max(np.abs(g0).max(), 1e-300)  # first step moves beta by at most half
+        trace = []
+        t0 = time.perf_counter()
+        st = m.reconstruct(grid, meas, beta0, prm, iters=args.recon_iters, method="gd", step=step, n_gd=5,
+                           callback=lambda s: trace.append({"outer": s.it, "loss": s.losses[-1], **errs(s.beta)}))
+        torch.cuda.synchronize()
+        out[f"gd_{cond}"] = {"outer_iterations": st.it, "n_gd": 5, "step": step, "renders": st.n_renders,
+                             "s": time.perf_counter() - t0, "loss0": st.losses[0], "trace": trace[::5] + trace[-1:]}
+    print(json.dumps(out))
+    return 0
+
+
 def run_precision_study(args):
     """Image and gradient error of the FP32 / FP16 / BF16 brick forms at N photons against a
     10 N-photon FP32 reference (relative L2), and their step times."""
@@ -475,6 +524,8 @@ def main():
         return run_single(args)
     if args.study == "precision":
         return run_precision_study(args)
+    if args.study == "recon":
+        return run_recon_study(args)
     if args.workload == "batch16":
         return run_batch(args)
     return run_ours(args)

@@ -97,7 +97,11 @@ def reconstruct(grid, meas, beta0, params, iters: int = 50, method: str = "lbfgs
                 break
             alpha *= 0.5
         if not ok:
-            break
+            if not st.s_hist:
+                break  # no descent along the projected gradient either
+            st.s_hist.clear()  # stale curvature pairs: retry from the projected gradient
+            st.y_hist.clear()
+            continue
         s, y = xn - x, gn - g
         if np.dot(s, y) > 1e-12 * np.dot(y, y):
             st.s_hist.append(s)

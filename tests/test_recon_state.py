@@ -1,4 +1,5 @@
-"""Checkpoint / resume of the reconstruction driver state (host only)."""
+"""Host logic of the reconstruction drivers: checkpoint / resume of their state, and the projected
+L-BFGS and surrogate GD loops on a CPU stand-in for the grid (a quadratic loss)."""
 import numpy as np
 
 
@@ -21,3 +22,59 @@ def test_recon_state_roundtrip(tmp_path):
     Y = [A @ s for s in S]
     g = rng.random(6)
     assert np.allclose(_two_loop(g, S, Y), np.linalg.solve(A, g), rtol=1e-10)
+
+
+class _QuadGrid:
+    """Stand-in for a Grid on the CPU: E(beta) = |A beta - y|^2, the shape of the paper's loss
+    with a linear image model, so the drivers' host logic runs without a GPU."""
+
+    device = "cpu"
+
+    def __init__(self, A, y):
+        import torch
+        self.A, self.y, self.torch = torch.from_numpy(A), torch.from_numpy(y), torch
+
+    def _f(self, beta):
+        r = self.A @ beta.double() - self.y
+        return (r @ r).reshape(1), 2.0 * (self.A.T @ r)
+
+    def render_grad(self, beta, params, meas, mask=None, images=False):
+        loss, grad = self._f(beta)
+        return {"loss": loss, "grad": grad}
+
+    def render(self, beta, params, images=False, L=False):
+        return {"L": beta.double().clone()}
+
+    def surrogate_grad(self, beta, L_ref, beta_ref, params, meas, mask=None):
+        loss, grad = self._f(beta)
+        return {"loss": loss, "grad": grad}
+
+
+def _nnls_case(seed=3, m=40, n=25):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(m, n))
+    x_true = np.maximum(rng.normal(size=n), 0.0)
+    y = A @ x_true + 0.3 * rng.normal(size=m)  # noisy: some bounds are active at the optimum
+    return A, y
+
+
+def test_projected_lbfgs_reaches_the_nonnegative_least_squares_optimum():
+    scipy_opt = __import__("pytest").importorskip("scipy.optimize")
+    from paper_1512_02110_gb300.autograd import reconstruct
+    A, y = _nnls_case()
+    x_ref, _ = scipy_opt.nnls(A, y)
+    st = reconstruct(_QuadGrid(A, y), None, np.full(A.shape[1], 0.5), None, iters=300, method="lbfgs")
+    f_ref = float(np.sum((A @ x_ref - y) ** 2))
+    assert st.losses[-1] <= f_ref * (1 + 1e-6)
+    assert np.all(st.beta >= 0.0)
+    assert np.allclose(st.beta, x_ref, atol=1e-4)
+
+
+def test_surrogate_gd_loop_descends_with_a_safe_step():
+    from paper_1512_02110_gb300.autograd import reconstruct
+    A, y = _nnls_case(seed=5)
+    step = 0.5 / np.linalg.norm(A, 2) ** 2  # below 1 / Lipschitz constant of the gradient
+    st = reconstruct(_QuadGrid(A, y), None, np.full(A.shape[1], 0.5), None, iters=20, method="gd", step=step, n_gd=5)
+    assert st.it == 20 and st.n_renders == 20 and len(st.losses) == 100
+    assert all(b <= a + 1e-12 for a, b in zip(st.losses, st.losses[1:]))
+    assert np.all(st.beta >= 0.0)
