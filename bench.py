@@ -272,18 +272,25 @@ def run_ours(args):
     # Achieved = algorithmic operations per launch / average launch time, with per-unit counts:
     # 15 per transport segment, 27 per event and camera (local estimate: direction, cosine,
     # Henyey-Greenstein phase, two MUFU), 35 per event (scattering sample, roulette), 2 per replay
-    # score scatter. Pass 1 walks the forward paths again (same segments and events); pass 2 the
-    # rest. The HBM form (4 B per segment, 8 B per camera per event) is kept beside it.
+    # score scatter; the stored-event adjoint 27 per event and camera, 36 B record + 4 B per camera
+    # + 8 B of W per event. The HBM form (4 B per segment, 8 B per camera per event) is kept beside it.
     C = sc.n_cams
     seg1, ev1 = st["segments"], st["events"]
-    seg2, ev2 = st["replay_segments"] - seg1, st["replay_events"] - ev1
+    stored = st.get("events_stored", 0.0)
+    if stored > 0:  # W came from the forward's stored events: the replay counters hold pass 2 alone
+        seg2, ev2 = st["replay_segments"], st["replay_events"]
+    else:           # pass 1 walked the forward paths again (same segments and events)
+        seg2, ev2 = st["replay_segments"] - seg1, st["replay_events"] - ev1
     ops_ev = 27 * C + 35
     kernels = {
         "k_transport": (phase_acc["transport"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 8 * C * ev1),
         "k_replay_pass1": (phase_acc["replay"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 4 * C * ev1),
         "k_replay_pass2": (phase_acc["replay2"], 15 * seg2 + ops_ev * ev2 + 2 * st["replay_scatters"],
                            4 * seg2 + 4 * C * ev2 + 8 * st["replay_scatters"]),
+        "k_event_adjoint": (phase_acc.get("event_adjoint", [0.0, 0]), 27 * C * stored,
+                            (36 + 4 * C + 8) * stored),
     }
+    kernels = {k: v for k, v in kernels.items() if v[0][1] > 0 and v[1] > 0}
     kern = max(kernels, key=lambda k: kernels[k][0][0])
     (kms, kn), aops, abytes = kernels[kern]
     calls_per_step = kn / args.steps

@@ -64,16 +64,18 @@ enum {
     MST_ST_LAUNCHED = 14, MST_ST_TRACED = 15,
     MST_ST_REPLAY_SEGMENTS = 16, MST_ST_REPLAY_EVENTS = 17, MST_ST_LOS_SEGMENTS = 18,
     MST_ST_PIXEL_SEGMENTS = 19, MST_ST_BACKPROJ_SEGMENTS = 20, MST_ST_LOSADJ_SEGMENTS = 21,
-    MST_ST_REPLAY_SCATTERS = 22, MST_ST_LOST = 23 /* walks abandoned (non-finite direction); 0 in valid use */
+    MST_ST_REPLAY_SCATTERS = 22, MST_ST_LOST = 23, /* walks abandoned (non-finite direction); 0 in valid use */
+    MST_ST_EVENTS_STORED = 24 /* full gradient: events the forward stored for the adjoint (0: replayed instead) */
 };
 
 /* phases timed by the profiler (mst_get_phase_times) */
 enum {
     MST_PH_STAGE = 0, MST_PH_TRANSPORT = 1, MST_PH_FOLD = 2, MST_PH_LOS = 3, MST_PH_IMAGES = 4,
     MST_PH_BACKPROJECT = 5, MST_PH_LOS_ADJOINT = 6, MST_PH_REPLAY = 7, MST_PH_COMBINE = 8, MST_PH_REPLAY2 = 9,
-    MST_PH_REPLAY_LIST = 10,
-    MST_NPHASES = 11 /* MST_PH_REPLAY: replay pass 1 (W per photon); MST_PH_REPLAY_LIST: the list of photons
-                        with W != 0 that pass 2 walks; MST_PH_REPLAY2: pass 2 (scatter) */
+    MST_PH_REPLAY_LIST = 10, MST_PH_EVENT_ADJOINT = 11,
+    MST_NPHASES = 12 /* MST_PH_REPLAY: replay pass 1 (W per photon); MST_PH_EVENT_ADJOINT: W per photon from
+                        the events the forward stored (instead of pass 1); MST_PH_REPLAY_LIST: the list of
+                        photons with W != 0 that pass 2 walks; MST_PH_REPLAY2: pass 2 (scatter) */
 };
 
 typedef struct mst_grid mst_grid; /* opaque; owned by the library */
@@ -157,8 +159,10 @@ int mst_render(mst_grid *g, const float *beta_dev, const mst_params *p, double *
  * Eq. Jaco1, Eq. TcofJaco1, Eq. DivTc) and conditioning Q_c.
  * MST_GRAD_FULL: the full gradient of Eq. DirectJacob applied to the residual, where
  * dL/dbeta is estimated by the score of the free-flight density (Eq. beer-lambert,
- * Eq. MCextinct) over paths replayed from their Philox keys (no paths are stored).
- * Requires the voxel estimator. */
+ * Eq. MCextinct) over paths replayed from their Philox keys. W = sum_s w_s per photon comes
+ * from the events the forward render stored (36 B per event, within the handle's budget, see
+ * mst_set_replay_memory), or, when they do not fit, from a first replay of every path; the
+ * second replay scatters the score. Results agree either way. Requires the voxel estimator. */
 int mst_render_grad(mst_grid *g, const float *beta_dev, const mst_params *p, const double *images_meas_dev,
                     const uint8_t *mask_dev, double *images_dev, double *grad_dev, double *loss_dev, void *stream);
 
@@ -190,6 +194,14 @@ int mst_ray_counts(mst_grid *g, float *Q_dev, void *stream);
  * (Sec. 6). psi_dev [1] double or NULL; grad_dev [nvox] double or NULL, receives += eta dPsi. */
 int mst_regularizer(mst_grid *g, const float *beta_dev, double eta, double *psi_dev, double *grad_dev,
                     void *stream);
+
+/* Device memory the handle may hold for the events a full-gradient forward render stores
+ * (36 B per scattering event: voxel, position, incoming direction, weight, photon index), for
+ * calls of at most 2^27 photons. Default 16 GiB; 0 stores nothing (W by replay). The buffer
+ * is allocated at the first full-gradient call that needs it and grown, within the budget,
+ * when a call stored more events than it held; a call whose events do not fit, or whose
+ * allocation fails, computes W by replay instead. Takes effect at the next call. */
+int mst_set_replay_memory(mst_grid *g, uint64_t bytes);
 
 /* Validation aids for the forward render, kept on the handle until replaced:
  *   photon_hash_dev [n_photons] uint32 or NULL: per-photon path checksum (FNV-1a over the

@@ -161,8 +161,10 @@ void set_fold(TransportArgs& a, uint64_t bins) {
 // Runs the photon transport. The forward render is one launch per kLaunchPhotons photons; the
 // replay runs pass 1, the pass-2 list and pass 2 per kReplayChunk photons (the size of its
 // per-photon buffers). The launches fold their FP32 tiles while they run; a last fold after each
-// launch takes what is left.
-int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cudaStream_t st) {
+// launch takes what is left. store_events (forward of a full gradient, one launch): the forward
+// also stores its events and each photon's event count for the stored-event adjoint.
+int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cudaStream_t st,
+                bool store_events = false) {
     TransportArgs a = transport_args(g, p);
     a.cimg = cimg;
     const uint64_t n = p->n_photons;
@@ -175,6 +177,12 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
     const int b_p2 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, 2);
     if (replay) set_fold(a, (uint64_t)g->geo.nvox);
     else if (est == MST_EST_VOXEL) set_fold(a, (uint64_t)g->geo.nvox * g->cp);
+    if (store_events) {
+        a.evrec = g->evrec;
+        a.ev_cap = g->ev_cap;
+        a.ev_count = g->ev_count;
+        MST_CK(cudaMemsetAsync(g->ev_count, 0, sizeof(unsigned long long), st));
+    }
     for (int l = 0; l < nl; ++l) {
         const uint64_t base = (uint64_t)l * span;
         a.first_id = p->photon_offset + base;
@@ -209,15 +217,66 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
             }
         }
     }
+    if (store_events) {  // the count reaches the host for the next call's sizing, without a wait
+        MST_CK(cudaMemcpyAsync(g->ev_seen, g->ev_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        MST_CK(cudaEventRecord(g->ev_seen_ready, st));
+        g->ev_seen_pending = true;
+    }
     return MST_OK;
 }
 
-// Per-photon buffers of the replay, allocated by the first full-gradient call.
-int ensure_replay(mst_grid* g) {
-    if (g->wbuf) return MST_OK;
-    if (cudaMalloc(&g->wbuf, kReplayChunk * 8) != cudaSuccess ||
-        cudaMalloc(&g->nevbuf, kReplayChunk * 4) != cudaSuccess ||
-        cudaMalloc(&g->plist, kReplayChunk * sizeof(ScoreRec)) != cudaSuccess) {
+// The replay of a call whose forward stored its events: W per photon from the stored events
+// (replay pass 1 over all photons instead, on the device, when they did not fit), the list of
+// photons with W != 0 over the whole call, and one pass-2 launch over it.
+int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
+    TransportArgs a = transport_args(g, p);
+    const uint64_t n = p->n_photons;
+    set_fold(a, (uint64_t)g->geo.nvox);
+    a.evrec = g->evrec;
+    a.ev_cap = g->ev_cap;
+    a.ev_count = g->ev_count;
+    a.first_id = p->photon_offset;
+    a.out_base = 0;
+    a.n = (uint32_t)n;
+    MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * 2, st));
+    MST_CK(cudaMemsetAsync(g->wbuf, 0, sizeof(double) * n, st));
+    {
+        Phase ph(g, MST_PH_EVENT_ADJOINT, st);
+        MST_CK(launch_event_adjoint(g, a, p->grid_dtype, st));
+    }
+    a.ticket = g->tickets;
+    {
+        Phase ph(g, MST_PH_REPLAY, st);  // returns at once when the events fitted
+        MST_CK(launch_transport(g, a, p->grid_dtype, 3, g->sm_count * transport_blocks_per_sm(p->grid_dtype, 3), st));
+    }
+    {
+        Phase ph(g, MST_PH_REPLAY_LIST, st);
+        MST_CK(launch_score_list(g, a.n, st));
+    }
+    a.ticket = g->tickets + 1;
+    {
+        Phase ph(g, MST_PH_REPLAY2, st);
+        MST_CK(launch_transport(g, a, p->grid_dtype, 2, g->sm_count * transport_blocks_per_sm(p->grid_dtype, 2), st));
+    }
+    Phase ph(g, MST_PH_FOLD, st);
+    MST_CK(launch_fold_grad(g, st));
+    return MST_OK;
+}
+
+// Per-photon buffers of the replay for n photons (at least kReplayChunk), allocated by the
+// first full-gradient call that needs them and grown when a call needs more.
+int ensure_replay(mst_grid* g, uint64_t n) {
+    n = std::max<uint64_t>(n, kReplayChunk);
+    if (g->wbuf && g->replay_cap >= n) return MST_OK;
+    cudaFree(g->wbuf);
+    cudaFree(g->nevbuf);
+    cudaFree(g->plist);
+    g->wbuf = nullptr;
+    g->nevbuf = nullptr;
+    g->plist = nullptr;
+    g->replay_cap = 0;
+    if (cudaMalloc(&g->wbuf, n * 8) != cudaSuccess || cudaMalloc(&g->nevbuf, n * 4) != cudaSuccess ||
+        cudaMalloc(&g->plist, n * sizeof(ScoreRec)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(g->wbuf);
         cudaFree(g->nevbuf);
@@ -227,7 +286,50 @@ int ensure_replay(mst_grid* g) {
         g->plist = nullptr;
         return fail(g, MST_ERR_OOM, "replay buffers: out of device memory");
     }
+    g->replay_cap = n;
     return MST_OK;
+}
+
+// Whether the forward of a full-gradient call of n photons stores its events, with the buffer
+// sized for them: room for 6 events per photon at first, then 1.25 x the events the last
+// storing call offered (read without a wait once its copy has landed), within the budget. Never
+// fails the call: too many photons, no budget, a failed allocation or a call inside a stream
+// capture (no allocation there) all mean W by replay.
+bool ensure_records(mst_grid* g, uint64_t n) {
+    const uint64_t rec_bytes = (uint64_t)kEventWords * 4;
+    if (g->capturing || n > kRecordMaxPhotons || g->rec_budget < rec_bytes * 1024) return false;
+    if (!g->ev_count) {
+        if (cudaMalloc(&g->ev_count, sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMallocHost(&g->ev_seen, sizeof(unsigned long long)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g->ev_seen_ready, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    unsigned long long seen = 0;
+    if (g->ev_seen_pending) {
+        if (cudaEventQuery(g->ev_seen_ready) == cudaSuccess) {
+            seen = *g->ev_seen;
+            g->ev_seen_pending = false;
+            g->ev_last = seen;
+        } else {
+            cudaGetLastError();  // not ready yet: size from the last count that arrived
+        }
+    }
+    const uint64_t max_ev = g->rec_budget / rec_bytes;
+    uint64_t want = g->ev_last ? g->ev_last + g->ev_last / 4 : 6 * n;
+    want = std::min<uint64_t>(std::max<uint64_t>(want, 1024), max_ev);
+    if (g->evrec && g->ev_cap >= want) return true;
+    cudaFree(g->evrec);
+    g->evrec = nullptr;
+    g->ev_cap = 0;
+    if (cudaMalloc(&g->evrec, want * rec_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        g->evrec = nullptr;
+        return false;
+    }
+    g->ev_cap = want;
+    return true;
 }
 
 int ensure_q(mst_grid* g, int mode, cudaStream_t st) {
@@ -260,6 +362,10 @@ void free_all(mst_grid* g) {
                     g->resid, g->lap, g->omega, g->Qw, g->stats, g->tickets, g->wbuf, g->nevbuf, g->plist, g->score_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    cudaFree(g->evrec);
+    cudaFree(g->ev_count);
+    if (g->ev_seen) cudaFreeHost(g->ev_seen);
+    if (g->ev_seen_ready) cudaEventDestroy(g->ev_seen_ready);
 }
 
 int check_render_grad(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const double* grad);
@@ -523,7 +629,16 @@ int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const 
     }
     MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
     MST_CK(cudaMemsetAsync(g->L64, 0, sizeof(double) * nL, st));
-    rc = run_photons(g, p, false, nullptr, st);
+    // full gradient: the forward stores its events when they can be held (W without pass 1)
+    bool stored = false;
+    if (p->grad_mode == MST_GRAD_FULL) {
+        stored = ensure_records(g, p->n_photons);
+        if (stored && ensure_replay(g, p->n_photons) != MST_OK) {
+            stored = false;
+            g->err.clear();
+        }
+    }
+    rc = run_photons(g, p, false, nullptr, st, stored);
     if (rc) return rc;
     {
         Phase ph(g, MST_PH_LOS, st);
@@ -553,14 +668,14 @@ int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const 
                                             p->conditioning ? g->Qw : nullptr, grad, st));
         }
     } else {
-        rc = ensure_replay(g);
+        rc = ensure_replay(g, stored ? p->n_photons : kReplayChunk);
         if (rc) return rc;
         {
             Phase ph(g, MST_PH_COMBINE, st);
             MST_CK(launch_adjoint_tiles(g, g->T, g->bacc, g->adj, st));
         }
         MST_CK(cudaMemsetAsync(g->g64, 0, sizeof(double) * g->geo.nvox, st));
-        rc = run_photons(g, p, true, nullptr, st);
+        rc = stored ? run_replay_stored(g, p, st) : run_photons(g, p, true, nullptr, st);
         if (rc) return rc;
         {
             Phase ph(g, MST_PH_COMBINE, st);
@@ -726,6 +841,19 @@ int mst_get_phase_times(mst_grid* g, double* ms, int* launches) {
     return MST_OK;
 }
 
+int mst_set_replay_memory(mst_grid* g, uint64_t bytes) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    g->rec_budget = bytes;
+    if (g->evrec && g->ev_cap * (uint64_t)kEventWords * 4 > bytes) {  // shrink to the new budget at the next call
+        DeviceGuard dg(g->device);
+        MST_CK(cudaDeviceSynchronize());
+        cudaFree(g->evrec);
+        g->evrec = nullptr;
+        g->ev_cap = 0;
+    }
+    return MST_OK;
+}
+
 int mst_sync(mst_grid* g) {
     if (!g) return MST_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
@@ -860,7 +988,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
             g->prof = false;
             prof_reset(g);
             int rc = ensure_q(g, params[i].grad_mode == MST_GRAD_SURROGATE ? params[i].conditioning : 0, st);
-            if (rc == MST_OK && params[i].grad_mode == MST_GRAD_FULL) rc = ensure_replay(g);  // no allocation in capture
+            if (rc == MST_OK && params[i].grad_mode == MST_GRAD_FULL) rc = ensure_replay(g, kReplayChunk);  // no allocation in capture
             if (rc) {
                 b->err = g->err;
                 return rc;
@@ -877,6 +1005,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
             return MST_ERR_CUDA;
         }
         int rc = MST_OK;
+        for (int i = 0; i < b->n; ++i) b->grids[i]->capturing = true;  // graph branches replay W
         cudaEventRecord(b->fork, b->cap);
         for (int i = 0; i < b->n && rc == MST_OK; ++i) {
             cudaStreamWaitEvent(b->branch[i], b->fork, 0);
@@ -887,6 +1016,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
             cudaStreamWaitEvent(b->cap, b->join[i], 0);
         }
         const cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
+        for (int i = 0; i < b->n; ++i) b->grids[i]->capturing = false;
         if (rc == MST_OK && (ec != cudaSuccess || !graph)) {
             b->err = std::string("graph capture failed: ") + cudaGetErrorString(ec);
             rc = MST_ERR_CUDA;

@@ -19,6 +19,12 @@ namespace mst {
 constexpr uint64_t kMaxPhotons = 1ull << 34;    // photons per call
 constexpr uint64_t kLaunchPhotons = 1ull << 30;  // photons per forward launch (32-bit ticket)
 constexpr uint64_t kReplayChunk = 1ull << 24;    // photons per replay pass-1 / pass-2 pair
+// Full gradient: the forward stores its events (kEventWords words each, structure of arrays)
+// for calls of at most kRecordMaxPhotons photons; W then comes from the stored events and the
+// replay is one pass-2 launch over the call's photons.
+constexpr uint64_t kRecordMaxPhotons = 1ull << 27;
+constexpr int kEventWords = 9;  // packed voxel, offset (3), incoming direction (3), albedo * weight, photon
+constexpr uint64_t kDefaultRecordBytes = 16ull << 30;
 constexpr uint64_t kFoldSweep = 1ull << 21;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
 constexpr int kMaxTickets = (int)(2 * (kMaxPhotons / kReplayChunk));
@@ -49,8 +55,12 @@ struct TransportArgs {
     const float* omega;        // [total pix] pixel solid angles (classic estimator)
     const float* adj;          // [nvox][cp] a_c(k) = T_c(k) b_c(k) (replay)
     float* gacc;               // [nvox] FP32 gradient accumulator (replay)
-    double* wbuf;              // [kReplayChunk] W per photon of the chunk (replay pass 1)
-    uint32_t* nevbuf;          // [kReplayChunk] events per photon of the chunk (replay pass 1)
+    double* wbuf;              // [photons of the chunk] W per photon (replay pass 1, stored-event adjoint)
+    uint32_t* nevbuf;          // [photons of the chunk] events per photon (replay pass 1, or the forward
+                               // when it stores events)
+    uint32_t* evrec;           // stored events [kEventWords][ev_cap] (forward), or NULL
+    unsigned long long ev_cap;     // capacity of evrec in events (0: no events stored)
+    unsigned long long* ev_count;  // events offered for storage; > ev_cap: they did not fit
     const ScoreRec* plist;     // [kReplayChunk] photons with W != 0 (replay pass 2)
     const unsigned int* plist_n;  // entries in plist
     double* L64;               // [C][nvox] FP64 result the L tile folds into
@@ -86,9 +96,19 @@ struct mst_grid {
     float* gT = nullptr;          // [C][nvox]  W_c^T (L T b)
     float* adj = nullptr;         // [nvox][cp] T_c b_c
     float* gacc = nullptr;        // [nvox]
-    double* wbuf = nullptr;       // [kReplayChunk], allocated by the first full-gradient call
-    uint32_t* nevbuf = nullptr;   // [kReplayChunk]
-    mst::ScoreRec* plist = nullptr;     // [kReplayChunk]
+    double* wbuf = nullptr;       // [replay_cap], allocated by the first full-gradient call
+    uint32_t* nevbuf = nullptr;   // [replay_cap]
+    mst::ScoreRec* plist = nullptr;     // [replay_cap]
+    uint64_t replay_cap = 0;            // photons the three buffers above hold
+    uint32_t* evrec = nullptr;          // [kEventWords][ev_cap] stored events (full gradient)
+    unsigned long long ev_cap = 0;
+    unsigned long long* ev_count = nullptr;  // device counter of the last recording forward
+    unsigned long long* ev_seen = nullptr;   // pinned host copy of it, read at the next call
+    cudaEvent_t ev_seen_ready = nullptr;     // recorded after that copy
+    bool ev_seen_pending = false;
+    unsigned long long ev_last = 0;          // events offered by the last storing call whose count arrived
+    bool capturing = false;                  // inside a stream capture: no allocation, no event query
+    uint64_t rec_budget = mst::kDefaultRecordBytes;
     unsigned int* score_cnt = nullptr;  // [2 kScoreBins + 1] list bin counts, bin fill, list length
     double* g64 = nullptr;        // [nvox]
     double* resid = nullptr;      // [total_pix] 2 M (i - i_meas)
@@ -124,6 +144,8 @@ cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtyp
 cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st);
 cudaError_t launch_fold_grad(const mst_grid* g, cudaStream_t st);
 cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st);
+// W per photon from the stored events (returns at once when they did not fit)
+cudaError_t launch_event_adjoint(const mst_grid* g, const TransportArgs& a, int dtype, cudaStream_t st);
 cudaError_t launch_los(const mst_grid* g, int dtype, const double* L, const double* jfix, const float* beta_ref,
                        const float* beta, float* T_out, float* R_out, cudaStream_t st);
 cudaError_t launch_images(const mst_grid* g, const float* R, double* images, const double* meas, const uint8_t* mask,

@@ -263,6 +263,22 @@ __device__ __forceinline__ void finish_photon(const TransportArgs& A, const Phot
     uint32_t h = (ph.hash ^ ph.s) * kFnvPrime;
     h = (h ^ (uint32_t)term) * kFnvPrime;
     if (A.hash) A.hash[ph.idx] = h;
+    if (A.ev_cap) A.nevbuf[ph.idx - A.out_base] = ph.s;  // forward storing events: the count pass 2 stops at
+}
+
+// One stored event (forward, full gradient): what w_s = sum_c a_c(k) albedo I_s P_c(s) needs.
+__device__ __forceinline__ void store_event(const TransportArgs& A, unsigned long long i, const Photon& e, float wgt) {
+    const unsigned long long C = A.ev_cap;
+    uint32_t* r = A.evrec + i;
+    r[0] = (uint32_t)e.ix | ((uint32_t)e.iy << 11) | ((uint32_t)e.iz << 22);
+    r[C] = __float_as_uint(e.p.x);
+    r[2 * C] = __float_as_uint(e.p.y);
+    r[3 * C] = __float_as_uint(e.p.z);
+    r[4 * C] = __float_as_uint(e.d.x);
+    r[5 * C] = __float_as_uint(e.d.y);
+    r[6 * C] = __float_as_uint(e.d.z);
+    r[7 * C] = __float_as_uint(wgt);
+    r[8 * C] = e.idx - A.out_base;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -494,6 +510,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
     uint32_t wbase = 0u, wend = 0u;
     unsigned segments = 0u, scatters = 0u, events = 0u;
     const uint32_t pool_n = PASS2 ? *A.plist_n : A.n;  // pass 2 walks the list built from pass 1
+    if (PASS1 && A.ev_cap && *A.ev_count <= A.ev_cap) return;  // the forward's stored events gave W
 
     for (;;) {
         // (1) fill: ready photons first, new photons only when the ready stack is empty
@@ -521,10 +538,8 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                 acc = r.W;
             } else if (A.skip && A.skip[A.out_base + j]) {
                 if (A.hash) A.hash[A.out_base + j] = 0u;
-                if (PASS1) {
-                    A.wbuf[j] = 0.0;
-                    A.nevbuf[j] = 0u;
-                }
+                if (PASS1) A.wbuf[j] = 0.0;
+                if (PASS1 || A.ev_cap) A.nevbuf[j] = 0u;
                 return false;
             }
             launch_photon(A, ph, pid);
@@ -590,6 +605,11 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
             uint32_t enev = 0u;
             double eacc = 0.0;
             int term = -1;  // -1 idle lane, 0 goes on, > 0 ended
+            unsigned long long ev_base = 0ull;  // forward storing events: this round's first slot
+            if (MODE == kFwdVoxel && A.ev_cap) {
+                if (lane == 0u) ev_base = atomicAdd(A.ev_count, (unsigned long long)n);
+                ev_base = __shfl_sync(kFull, ev_base, 0);
+            }
             if ((int)lane < n) {
                 get(evq, ev_n - 1 - (int)lane, A, e, enev, eacc);
                 e.s += 1u;
@@ -598,6 +618,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                 const float wgt = A.albedo * e.I;
                 if (!REPLAY) {
                     e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
+                    if (MODE == kFwdVoxel && A.ev_cap && ev_base + lane < A.ev_cap) store_event(A, ev_base + lane, e, wgt);
                     if (MODE == 0) le_voxel(A, e, wgt, k);
                     else le_classic<DT>(A, e, wgt);
                     term = after_event(A, e, t);
@@ -635,6 +656,29 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
     } else {
         flush_tally(A, t.load(), segments, events, lane);
     }
+}
+
+// W = sum_s w_s per photon from the events the forward stored, instead of replay pass 1: the
+// same w_s arithmetic (le_adjoint) on the same event state, accumulated in FP64. Does nothing
+// when the events did not fit (replay pass 1 then computes W from the paths).
+__global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
+    const unsigned long long cnt = *A.ev_count;
+    if (cnt > A.ev_cap) return;
+    const unsigned long long C = A.ev_cap;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kTB;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * kTB + threadIdx.x; i < cnt; i += stride) {
+        const uint32_t* r = A.evrec + i;
+        const uint32_t v = r[0];
+        Photon e;
+        e.ix = (int)(v & 2047u);
+        e.iy = (int)((v >> 11) & 2047u);
+        e.iz = (int)(v >> 22);
+        e.p = make_float3(__uint_as_float(r[C]), __uint_as_float(r[2 * C]), __uint_as_float(r[3 * C]));
+        e.d = make_float3(__uint_as_float(r[4 * C]), __uint_as_float(r[5 * C]), __uint_as_float(r[6 * C]));
+        const float w = le_adjoint(A, e, __uint_as_float(r[7 * C]), lin_index(A.g, e.ix, e.iy, e.iz));
+        if (w != 0.f) atomicAdd(A.wbuf + r[8 * C], (double)w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.stats + MST_ST_EVENTS_STORED, (double)cnt);
 }
 
 // Pass-2 work list. Photons with W != 0 are binned by their pass-1 event count (the last bin
@@ -793,6 +837,12 @@ cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st) {
     k_score_hist<<<blocks, kTB, 0, st>>>(g->wbuf, g->nevbuf, n, g->score_cnt);
     k_score_scatter<<<blocks, kTB, 0, st>>>(g->wbuf, g->nevbuf, n, g->score_cnt, g->score_cnt + kScoreBins,
                                             g->score_cnt + 2 * kScoreBins, g->plist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_event_adjoint(const mst_grid* g, const TransportArgs& a, int dtype, cudaStream_t st) {
+    (void)dtype;
+    k_event_adjoint<<<g->sm_count * 8, kTB, 0, st>>>(a);
     return cudaGetLastError();
 }
 

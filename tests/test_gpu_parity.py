@@ -211,19 +211,21 @@ def test_chunk_boundary_and_ragged_count(m, torch):
 
 @pytest.mark.slow
 def test_full_gradient_across_replay_chunks(m, torch):
-    """More photons than one replay chunk (2^24): two pass-1 / list / pass-2 rounds, the
-    second ragged, against the oracle's full gradient."""
+    """More photons than one replay chunk (2^24), W by replay: two pass-1 / list / pass-2
+    rounds, the second ragged, against the oracle's full gradient."""
     sc = _tiny_scene()
     p = synth.Params(albedo=0.99, g=0.85, sun_zenith=0.5, n_photons=(1 << 24) + 1003, seed=23)
     rng = np.random.default_rng(4)
     meas = rng.uniform(0.0, 2e-3, sc.n_pix)
     mask = np.ones(sc.n_pix, np.uint8)
     grid = m.Grid.from_scene(sc)
+    grid.set_replay_memory(0)  # W by replay pass 1, chunk by chunk
     beta = dev(sc.beta, np.float32)
     skip, _, _ = _diverged(m, grid, sc, p, beta)
     grid.set_debug(None, dev(skip, np.uint8))
     out = grid.render_grad(beta, m.make_params(p, grad_mode="full"), dev(meas, np.float64), dev(mask, np.uint8))
     st = grid.stats()
+    assert st["events_stored"] == 0
     grid.set_debug(None, None)
     ref = oracle.full_grad(sc, p, meas, mask, skip=skip)
     el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
@@ -294,6 +296,32 @@ def test_full_gradient(m, torch):
     eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
     record("full_gradient", diverged_frac=skip.mean(), images_max_rel=ei, loss_rel=el, grad_rel_l2=eg)
     assert ei < 1e-4 and el < 1e-4 and eg < 1e-3
+
+
+@pytest.mark.parametrize("budget", ["replay", "overflow"])
+def test_full_gradient_stored_events_match_replay(m, torch, budget):
+    """W from the forward's stored events (the default) against W from replay pass 1: same
+    loss and gradient up to the order of floating-point additions. "overflow": a budget of
+    2048 events, far fewer than the call makes, so the device falls back to pass 1."""
+    sc, p, meas, mask = _grad_case()
+    beta = dev(sc.beta, np.float32)
+    args = (beta, m.make_params(p, grad_mode="full", reg_eta=0.05), dev(meas, np.float64), dev(mask, np.uint8))
+    g_st = m.Grid.from_scene(sc)
+    a = g_st.render_grad(*args)
+    st_a = g_st.stats()
+    g_rp = m.Grid.from_scene(sc)
+    g_rp.set_replay_memory(0 if budget == "replay" else 2048 * 36)
+    b = g_rp.render_grad(*args)
+    st_b = g_rp.stats()
+    assert st_a["events_stored"] == st_a["events"] > 2048
+    assert st_b["events_stored"] == 0
+    el = abs(a["loss"].item() - b["loss"].item()) / abs(b["loss"].item())
+    eg = rel_l2(a["grad"].cpu().numpy(), b["grad"].cpu().numpy())
+    record(f"stored_events_vs_{budget}", loss_rel=el, grad_rel_l2=eg, replay_segments_stored=st_a["replay_segments"],
+           replay_segments_replay=st_b["replay_segments"])
+    assert el < 1e-6 and eg < 1e-5, (el, eg)  # the forward L sums in FP32 atomics in any order
+    # pass 2 walks the same photons either way; the replay also walks every path in pass 1
+    assert st_b["replay_segments"] > st_a["replay_segments"]
 
 
 def test_surrogate_mode_of_render_grad(m, torch):
