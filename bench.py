@@ -273,7 +273,8 @@ def run_ours(args):
     # 15 per transport segment, 27 per event and camera (local estimate: direction, cosine,
     # Henyey-Greenstein phase, two MUFU), 35 per event (scattering sample, roulette), 2 per replay
     # score scatter; the stored-event adjoint 27 per event and camera, 36 B record + 4 B per camera
-    # + 8 B of W per event. The HBM form (4 B per segment, 8 B per camera per event) is kept beside it.
+    # + 8 B of W per event. The HBM form (4 B per segment, 8 B per camera per event, plus the stored
+    # events and event counts the forward writes) is kept beside it.
     C = sc.n_cams
     seg1, ev1 = st["segments"], st["events"]
     stored = st.get("events_stored", 0.0)
@@ -283,7 +284,8 @@ def run_ours(args):
         seg2, ev2 = st["replay_segments"] - seg1, st["replay_events"] - ev1
     ops_ev = 27 * C + 35
     kernels = {
-        "k_transport": (phase_acc["transport"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 8 * C * ev1),
+        "k_transport": (phase_acc["transport"], 15 * seg1 + ops_ev * ev1,
+                        4 * seg1 + 8 * C * ev1 + (36 * stored + 4 * st["traced"] if stored > 0 else 0)),
         "k_replay_pass1": (phase_acc["replay"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 4 * C * ev1),
         "k_replay_pass2": (phase_acc["replay2"], 15 * seg2 + ops_ev * ev2 + 2 * st["replay_scatters"],
                            4 * seg2 + 4 * C * ev2 + 8 * st["replay_scatters"]),
