@@ -296,13 +296,7 @@ constexpr int kRdCap = 64;
 // budget), per kernel mode; set from sweeps on the 64^3 cumulus workload.
 constexpr int kStepsForward = 8;
 constexpr int kStepsPass1 = 8;
-constexpr int kStepsPass2 = 4;
-// A trip ends early, after its first step, once fewer than this many lanes are still in flight
-// (0: every lane runs up to the trip's steps), so lanes whose flight ended get work sooner. It
-// pays only in replay pass 2, whose steps also scatter the score.
-constexpr int kTripMinActiveForward = 0;
-constexpr int kTripMinActivePass1 = 0;
-constexpr int kTripMinActivePass2 = 16;
+constexpr int kStepsPass2 = 5;
 constexpr int kMinBlocksForward = 3;  // voxel estimator; the classic one keeps a 1-block budget
 constexpr int kMinBlocksClassic = 1;
 constexpr int kMinBlocksPass1 = 3;
@@ -553,21 +547,8 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
 
         // (2) one voxel for every flying photon
         int r = -1;
-        constexpr int kTripMinActive =
-            PASS2 ? kTripMinActivePass2 : (PASS1 ? kTripMinActivePass1 : kTripMinActiveForward);
         int nstep = 0;
-        if constexpr (kTripMinActive > 0) {
-            const float S = PASS2 ? (float)acc : 0.f;
-#pragma unroll 1
-            for (int q = 0; q < kStepsPerTrip; ++q) {
-                const bool go = fly && r == -1;
-                if (q > 0 && __popc(__ballot_sync(kFull, go)) < kTripMinActive) break;
-                if (go) {
-                    ++nstep;
-                    r = flight_step<DT>(A, ph, w, tau, S, scatters);
-                }
-            }
-        } else if (fly) {
+        if (fly) {
             const float S = PASS2 ? (float)acc : 0.f;
 #pragma unroll 1
             for (; nstep < kStepsPerTrip && r == -1; ++nstep) r = flight_step<DT>(A, ph, w, tau, S, scatters);
