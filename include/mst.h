@@ -159,10 +159,11 @@ int mst_render(mst_grid *g, const float *beta_dev, const mst_params *p, double *
  * Eq. Jaco1, Eq. TcofJaco1, Eq. DivTc) and conditioning Q_c.
  * MST_GRAD_FULL: the full gradient of Eq. DirectJacob applied to the residual, where
  * dL/dbeta is estimated by the score of the free-flight density (Eq. beer-lambert,
- * Eq. MCextinct) over paths replayed from their Philox keys. W = sum_s w_s per photon comes
- * from the events the forward render stored (36 B per event, within the handle's budget, see
- * mst_set_replay_memory), or, when they do not fit, from a first replay of every path; the
- * second replay scatters the score. Results agree either way. Requires the voxel estimator. */
+ * Eq. MCextinct) over paths replayed from their Philox keys. W = sum_s w_s per photon and the
+ * w_s come from the events the forward render stored (44 B per event, within the handle's
+ * budget, see mst_set_replay_memory), or, when they do not fit, from a first replay of every
+ * path; a last replay scatters the score. Results agree either way. Requires the voxel
+ * estimator. */
 int mst_render_grad(mst_grid *g, const float *beta_dev, const mst_params *p, const double *images_meas_dev,
                     const uint8_t *mask_dev, double *images_dev, double *grad_dev, double *loss_dev, void *stream);
 
@@ -196,7 +197,8 @@ int mst_regularizer(mst_grid *g, const float *beta_dev, double eta, double *psi_
                     void *stream);
 
 /* Device memory the handle may hold for the events a full-gradient forward render stores
- * (36 B per scattering event: voxel, position, incoming direction, weight, photon index), for
+ * (44 B per scattering event: voxel, position, incoming direction, weight, photon index, event
+ * number, and its w_s), for
  * calls of at most 2^27 photons. Default 16 GiB; 0 stores nothing (W by replay). The buffer
  * is allocated at the first full-gradient call that needs it and grown, within the budget,
  * when a call stored more events than it held; a call whose events do not fit, or whose

@@ -235,6 +235,8 @@ int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
     a.evrec = g->evrec;
     a.ev_cap = g->ev_cap;
     a.ev_count = g->ev_count;
+    a.wseq = g->wseq;
+    a.evoff = g->evoff;
     a.first_id = p->photon_offset;
     a.out_base = 0;
     a.n = (uint32_t)n;
@@ -242,6 +244,7 @@ int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
     MST_CK(cudaMemsetAsync(g->wbuf, 0, sizeof(double) * n, st));
     {
         Phase ph(g, MST_PH_EVENT_ADJOINT, st);
+        MST_CK(launch_event_offsets(g, a.n, st));
         MST_CK(launch_event_adjoint(g, a, p->grid_dtype, st));
     }
     a.ticket = g->tickets;
@@ -255,7 +258,8 @@ int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
     }
     a.ticket = g->tickets + 1;
     {
-        Phase ph(g, MST_PH_REPLAY2, st);
+        Phase ph(g, MST_PH_REPLAY2, st);  // on the stored w_s (mode 4), or recomputing them when they did not fit
+        MST_CK(launch_transport(g, a, p->grid_dtype, 4, g->sm_count * transport_blocks_per_sm(p->grid_dtype, 4), st));
         MST_CK(launch_transport(g, a, p->grid_dtype, 2, g->sm_count * transport_blocks_per_sm(p->grid_dtype, 2), st));
     }
     Phase ph(g, MST_PH_FOLD, st);
@@ -271,19 +275,23 @@ int ensure_replay(mst_grid* g, uint64_t n) {
     cudaFree(g->wbuf);
     cudaFree(g->nevbuf);
     cudaFree(g->plist);
+    cudaFree(g->evoff);
     g->wbuf = nullptr;
     g->nevbuf = nullptr;
     g->plist = nullptr;
+    g->evoff = nullptr;
     g->replay_cap = 0;
     if (cudaMalloc(&g->wbuf, n * 8) != cudaSuccess || cudaMalloc(&g->nevbuf, n * 4) != cudaSuccess ||
-        cudaMalloc(&g->plist, n * sizeof(ScoreRec)) != cudaSuccess) {
+        cudaMalloc(&g->plist, n * sizeof(ScoreRec)) != cudaSuccess || cudaMalloc(&g->evoff, n * 4) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(g->wbuf);
         cudaFree(g->nevbuf);
         cudaFree(g->plist);
+        cudaFree(g->evoff);
         g->wbuf = nullptr;
         g->nevbuf = nullptr;
         g->plist = nullptr;
+        g->evoff = nullptr;
         return fail(g, MST_ERR_OOM, "replay buffers: out of device memory");
     }
     g->replay_cap = n;
@@ -296,7 +304,7 @@ int ensure_replay(mst_grid* g, uint64_t n) {
 // fails the call: too many photons, no budget, a failed allocation or a call inside a stream
 // capture (no allocation there) all mean W by replay.
 bool ensure_records(mst_grid* g, uint64_t n) {
-    const uint64_t rec_bytes = (uint64_t)kEventWords * 4;
+    const uint64_t rec_bytes = (uint64_t)kEventBytes;
     if (g->capturing || n > kRecordMaxPhotons || g->rec_budget < rec_bytes * 1024) return false;
     if (!g->ev_count) {
         if (cudaMalloc(&g->ev_count, sizeof(unsigned long long)) != cudaSuccess ||
@@ -316,16 +324,20 @@ bool ensure_records(mst_grid* g, uint64_t n) {
             cudaGetLastError();  // not ready yet: size from the last count that arrived
         }
     }
-    const uint64_t max_ev = g->rec_budget / rec_bytes;
+    const uint64_t max_ev = std::min<uint64_t>(g->rec_budget / rec_bytes, 0xFFFFFFFFull);  // 32-bit w_s slots
     uint64_t want = g->ev_last ? g->ev_last + g->ev_last / 4 : 6 * n;
     want = std::min<uint64_t>(std::max<uint64_t>(want, 1024), max_ev);
     if (g->evrec && g->ev_cap >= want) return true;
     cudaFree(g->evrec);
+    cudaFree(g->wseq);
     g->evrec = nullptr;
+    g->wseq = nullptr;
     g->ev_cap = 0;
-    if (cudaMalloc(&g->evrec, want * rec_bytes) != cudaSuccess) {
+    if (cudaMalloc(&g->evrec, want * kEventWords * 4) != cudaSuccess || cudaMalloc(&g->wseq, want * 4) != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(g->evrec);
         g->evrec = nullptr;
+        g->wseq = nullptr;
         return false;
     }
     g->ev_cap = want;
@@ -363,6 +375,8 @@ void free_all(mst_grid* g) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     cudaFree(g->evrec);
+    cudaFree(g->wseq);
+    cudaFree(g->evoff);
     cudaFree(g->ev_count);
     if (g->ev_seen) cudaFreeHost(g->ev_seen);
     if (g->ev_seen_ready) cudaEventDestroy(g->ev_seen_ready);
@@ -844,11 +858,13 @@ int mst_get_phase_times(mst_grid* g, double* ms, int* launches) {
 int mst_set_replay_memory(mst_grid* g, uint64_t bytes) {
     if (!g) return MST_ERR_INVALID_ARG;
     g->rec_budget = bytes;
-    if (g->evrec && g->ev_cap * (uint64_t)kEventWords * 4 > bytes) {  // shrink to the new budget at the next call
+    if (g->evrec && g->ev_cap * (uint64_t)kEventBytes > bytes) {  // shrink to the new budget at the next call
         DeviceGuard dg(g->device);
         MST_CK(cudaDeviceSynchronize());
         cudaFree(g->evrec);
+        cudaFree(g->wseq);
         g->evrec = nullptr;
+        g->wseq = nullptr;
         g->ev_cap = 0;
     }
     return MST_OK;
@@ -993,7 +1009,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
                 b->err = g->err;
                 return rc;
             }
-            for (int mode = 0; mode < 4; ++mode) transport_blocks_per_sm(params[i].grid_dtype, mode);
+            for (int mode = 0; mode < 5; ++mode) transport_blocks_per_sm(params[i].grid_dtype, mode);
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             b->err = "stream error before capture";

@@ -23,7 +23,8 @@ constexpr uint64_t kReplayChunk = 1ull << 24;    // photons per replay pass-1 / 
 // for calls of at most kRecordMaxPhotons photons; W then comes from the stored events and the
 // replay is one pass-2 launch over the call's photons.
 constexpr uint64_t kRecordMaxPhotons = 1ull << 27;
-constexpr int kEventWords = 9;  // packed voxel, offset (3), incoming direction (3), albedo * weight, photon
+constexpr int kEventWords = 10;  // packed voxel, offset (3), incoming direction (3), albedo * weight, photon, event number
+constexpr int kEventBytes = kEventWords * 4 + 4;  // the record and its w_s
 constexpr uint64_t kDefaultRecordBytes = 16ull << 30;
 constexpr uint64_t kFoldSweep = 1ull << 21;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
@@ -61,6 +62,8 @@ struct TransportArgs {
     uint32_t* evrec;           // stored events [kEventWords][ev_cap] (forward), or NULL
     unsigned long long ev_cap;     // capacity of evrec in events (0: no events stored)
     unsigned long long* ev_count;  // events offered for storage; > ev_cap: they did not fit
+    float* wseq;               // [ev_cap] w_s of the stored events, photon after photon (event order)
+    const uint32_t* evoff;     // [photons of the call] each photon's first slot in wseq
     const ScoreRec* plist;     // [kReplayChunk] photons with W != 0 (replay pass 2)
     const unsigned int* plist_n;  // entries in plist
     double* L64;               // [C][nvox] FP64 result the L tile folds into
@@ -99,8 +102,10 @@ struct mst_grid {
     double* wbuf = nullptr;       // [replay_cap], allocated by the first full-gradient call
     uint32_t* nevbuf = nullptr;   // [replay_cap]
     mst::ScoreRec* plist = nullptr;     // [replay_cap]
-    uint64_t replay_cap = 0;            // photons the three buffers above hold
+    uint32_t* evoff = nullptr;          // [replay_cap] first w_s slot of each photon (stored events)
+    uint64_t replay_cap = 0;            // photons the four buffers above hold
     uint32_t* evrec = nullptr;          // [kEventWords][ev_cap] stored events (full gradient)
+    float* wseq = nullptr;              // [ev_cap] their w_s, grouped by photon
     unsigned long long ev_cap = 0;
     unsigned long long* ev_count = nullptr;  // device counter of the last recording forward
     unsigned long long* ev_seen = nullptr;   // pinned host copy of it, read at the next call
@@ -138,7 +143,8 @@ namespace mst {
 
 // launchers (all enqueue on `st`; return cudaGetLastError())
 cudaError_t launch_stage(const mst_grid* g, const float* beta, int dtype, cudaStream_t st);
-// transport kernel modes: 0 forward voxel LE, 1 forward classic LE, 3 replay pass 1, 2 replay pass 2
+// transport kernel modes: 0 forward voxel LE, 1 forward classic LE, 3 replay pass 1, 2 replay pass 2,
+// 4 replay pass 2 reading w_s from the stored events
 cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int mode, int blocks,
                              cudaStream_t st);
 cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st);
@@ -146,6 +152,8 @@ cudaError_t launch_fold_grad(const mst_grid* g, cudaStream_t st);
 cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st);
 // W per photon from the stored events (returns at once when they did not fit)
 cudaError_t launch_event_adjoint(const mst_grid* g, const TransportArgs& a, int dtype, cudaStream_t st);
+// evoff = exclusive prefix sum of the n photons' event counts (nevbuf)
+cudaError_t launch_event_offsets(const mst_grid* g, uint32_t n, cudaStream_t st);
 cudaError_t launch_los(const mst_grid* g, int dtype, const double* L, const double* jfix, const float* beta_ref,
                        const float* beta, float* T_out, float* R_out, cudaStream_t st);
 cudaError_t launch_images(const mst_grid* g, const float* R, double* images, const double* meas, const uint8_t* mask,

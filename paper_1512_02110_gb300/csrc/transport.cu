@@ -24,7 +24,7 @@ struct Photon {
     int ix, iy, iz;
     float I, tau;
     uint32_t s;      // scattering events so far
-    uint32_t hash;
+    uint32_t hash;   // forward: path checksum; replay pass 2 on stored w_s: the photon's first w_s slot
     uint64_t id;     // global photon id (Philox counter)
     uint32_t idx;    // call-relative index (hash / skip arrays)
 };
@@ -279,6 +279,7 @@ __device__ __forceinline__ void store_event(const TransportArgs& A, unsigned lon
     r[6 * C] = __float_as_uint(e.d.z);
     r[7 * C] = __float_as_uint(wgt);
     r[8 * C] = e.idx - A.out_base;
+    r[9 * C] = e.s;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -303,7 +304,8 @@ constexpr int kMinBlocksPass1 = 3;
 constexpr int kMinBlocksPass2 = 3;
 
 // kernel modes
-constexpr int kFwdVoxel = 0, kFwdClassic = 1, kPass2 = 2, kPass1 = 3;
+// kPass2W: replay pass 2 reading w_s from the stored events instead of recomputing them
+constexpr int kFwdVoxel = 0, kFwdClassic = 1, kPass2 = 2, kPass1 = 3, kPass2W = 4;
 
 template <int NW>
 struct Stack {
@@ -376,7 +378,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // 32-bit atomics, so nothing added is lost; each bin's FP32 partial covers at most one sweep.
 template <int MODE>
 __device__ __forceinline__ void fold_slice(const TransportArgs& A, uint32_t batch, unsigned lane) {
-    if constexpr (MODE == kFwdVoxel || MODE == kPass2) {
+    if constexpr (MODE == kFwdVoxel || MODE == kPass2 || MODE == kPass2W) {
         if (A.fold_bins == 0u) return;
         const uint64_t i0 = (uint64_t)(batch % A.fold_nslices) * A.fold_slice;
         const uint64_t i1 = min(i0 + A.fold_slice, A.fold_bins);
@@ -471,12 +473,12 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
 // scatters the score of every flight that ends in an event; it stops at pass 1's last event.
 // Both passes run the same flight and event arithmetic, so they see the same path.
 template <int DT, int MODE>
-__global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
+__global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMinBlocksPass2
                                                        : (MODE == kPass1 ? kMinBlocksPass1
                                                           : (MODE == kFwdClassic ? kMinBlocksClassic : kMinBlocksForward)))
     k_transport(const TransportArgs A) {
-    constexpr bool REPLAY = MODE == kPass1 || MODE == kPass2;
-    constexpr bool PASS1 = MODE == kPass1, PASS2 = MODE == kPass2;
+    constexpr bool PASS1 = MODE == kPass1, PASS2 = MODE == kPass2 || MODE == kPass2W;
+    constexpr bool REPLAY = PASS1 || PASS2;
     constexpr int kStepsPerTrip = PASS2 ? kStepsPass2 : (PASS1 ? kStepsPass1 : kStepsForward);
     constexpr int NW = Rec<REPLAY>::NW;
     extern __shared__ uint32_t smem[];
@@ -504,7 +506,11 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
     uint32_t wbase = 0u, wend = 0u;
     unsigned segments = 0u, scatters = 0u, events = 0u;
     const uint32_t pool_n = PASS2 ? *A.plist_n : A.n;  // pass 2 walks the list built from pass 1
-    if (PASS1 && A.ev_cap && *A.ev_count <= A.ev_cap) return;  // the forward's stored events gave W
+    if (A.ev_cap) {  // a call whose forward stored its events: one of each pair of kernels works
+        const bool fit = *A.ev_count <= A.ev_cap;
+        if ((PASS1 || MODE == kPass2) && fit) return;  // W and w_s come from the stored events
+        if (MODE == kPass2W && !fit) return;           // they did not fit: pass 1 and kPass2 run
+    }
 
     for (;;) {
         // (1) fill: ready photons first, new photons only when the ready stack is empty
@@ -537,6 +543,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                 return false;
             }
             launch_photon(A, ph, pid);
+            if (MODE == kPass2W) ph.hash = A.evoff[pid];
             walk_init<true>(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
             tau = ph.tau;
             t.add_launch(A.I0);
@@ -605,7 +612,7 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
                     term = after_event(A, e, t);
                     if (term) finish_photon(A, e, term);
                 } else {
-                    const float we = le_adjoint(A, e, wgt, k);
+                    const float we = MODE == kPass2W ? A.wseq[e.hash + e.s - 1u] : le_adjoint(A, e, wgt, k);
                     if (PASS1) {
                         eacc += (double)we;
                         term = after_event(A, e, t);
@@ -639,9 +646,9 @@ __global__ void __launch_bounds__(kTB, MODE == kPass2 ? kMinBlocksPass2
     }
 }
 
-// W = sum_s w_s per photon from the events the forward stored, instead of replay pass 1: the
-// same w_s arithmetic (le_adjoint) on the same event state, accumulated in FP64. Does nothing
-// when the events did not fit (replay pass 1 then computes W from the paths).
+// w_s of every event the forward stored, instead of replay pass 1: the same arithmetic
+// (le_adjoint) on the same event state, written to the photon's slot in wseq for pass 2 and
+// added to W in FP64. Does nothing when the events did not fit (pass 1 then walks the paths).
 __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
     const unsigned long long cnt = *A.ev_count;
     if (cnt > A.ev_cap) return;
@@ -657,9 +664,108 @@ __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
         e.p = make_float3(__uint_as_float(r[C]), __uint_as_float(r[2 * C]), __uint_as_float(r[3 * C]));
         e.d = make_float3(__uint_as_float(r[4 * C]), __uint_as_float(r[5 * C]), __uint_as_float(r[6 * C]));
         const float w = le_adjoint(A, e, __uint_as_float(r[7 * C]), lin_index(A.g, e.ix, e.iy, e.iz));
-        if (w != 0.f) atomicAdd(A.wbuf + r[8 * C], (double)w);
+        const uint32_t j = r[8 * C];
+        A.wseq[A.evoff[j] + r[9 * C] - 1u] = w;  // event s of photon j: slot evoff[j] + s - 1
+        if (w != 0.f) atomicAdd(A.wbuf + j, (double)w);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.stats + MST_ST_EVENTS_STORED, (double)cnt);
+}
+
+// Exclusive prefix sum of the photons' event counts (three passes over tiles of kScanTile):
+// photon j's w_s go to wseq[evoff[j] + s - 1], so pass 2 reads each photon's in event order.
+constexpr int kScanPer = 16;                 // consecutive counts per thread
+constexpr int kScanTile = kTB * kScanPer;    // counts per block
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total) {
+    __shared__ uint32_t wsum[kTB / 32 + 1];
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (unsigned)o) incl += u;
+    }
+    if (lane == 31u) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t x = lane < kTB / 32 ? wsum[lane] : 0u;
+        uint32_t xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(kFull, xi, o);
+            if (lane >= (unsigned)o) xi += u;
+        }
+        if (lane < kTB / 32) wsum[lane] = xi - x;  // exclusive offset of each warp
+        if (lane == 31u) wsum[kTB / 32] = xi;      // block total
+    }
+    __syncthreads();
+    total = wsum[kTB / 32];
+    return wsum[warp] + incl - v;
+}
+
+__global__ void __launch_bounds__(kTB) k_scan_tiles(const uint32_t* __restrict__ x, uint32_t n,
+                                                    uint32_t* __restrict__ tsum) {
+    const uint32_t lo = blockIdx.x * (uint32_t)kScanTile + threadIdx.x * kScanPer;
+    uint32_t v = 0u;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q)
+        if (lo + q < n) v += x[lo + q];
+    uint32_t total = 0u;
+    block_exclusive_scan(v, total);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ tsum, uint32_t nt) {
+    // one block: exclusive scan of the tile sums in place, ceil(nt / 1024) consecutive per thread
+    __shared__ uint32_t wsum[32];
+    const uint32_t per = (nt + 1023u) / 1024u, lo = threadIdx.x * per;
+    uint32_t v = 0u;
+    for (uint32_t q = 0; q < per; ++q)
+        if (lo + q < nt) v += tsum[lo + q];
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (unsigned)o) incl += u;
+    }
+    if (lane == 31u) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t x = wsum[lane];
+        uint32_t xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(kFull, xi, o);
+            if (lane >= (unsigned)o) xi += u;
+        }
+        wsum[lane] = xi - x;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + incl - v;
+    for (uint32_t q = 0; q < per; ++q)
+        if (lo + q < nt) {
+            const uint32_t t = tsum[lo + q];
+            tsum[lo + q] = run;
+            run += t;
+        }
+}
+
+__global__ void __launch_bounds__(kTB) k_scan_apply(const uint32_t* __restrict__ x, uint32_t n,
+                                                    const uint32_t* __restrict__ tsum, uint32_t* __restrict__ out) {
+    const uint32_t lo = blockIdx.x * (uint32_t)kScanTile + threadIdx.x * kScanPer;
+    uint32_t v[kScanPer], sum = 0u;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        v[q] = lo + q < n ? x[lo + q] : 0u;
+        sum += v[q];
+    }
+    uint32_t total = 0u;
+    uint32_t run = tsum[blockIdx.x] + block_exclusive_scan(sum, total);
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q)
+        if (lo + q < n) {
+            out[lo + q] = run;
+            run += v[q];
+        }
 }
 
 // Pass-2 work list. Photons with W != 0 are binned by their pass-1 event count (the last bin
@@ -779,6 +885,7 @@ int occupancy_mode(int mode) {
         case kFwdVoxel: return occupancy(k_transport<DT, kFwdVoxel>, smem_bytes<false>());
         case kFwdClassic: return occupancy(k_transport<DT, kFwdClassic>, smem_bytes<false>());
         case kPass2: return occupancy(k_transport<DT, kPass2>, smem_bytes<true>());
+        case kPass2W: return occupancy(k_transport<DT, kPass2W>, smem_bytes<true>());
         default: return occupancy(k_transport<DT, kPass1>, smem_bytes<true>());
     }
 }
@@ -789,6 +896,7 @@ cudaError_t launch_dt(const TransportArgs& a, int mode, int blocks, cudaStream_t
         case kFwdVoxel: return launch_mode<DT, kFwdVoxel>(a, blocks, st);
         case kFwdClassic: return launch_mode<DT, kFwdClassic>(a, blocks, st);
         case kPass2: return launch_mode<DT, kPass2>(a, blocks, st);
+        case kPass2W: return launch_mode<DT, kPass2W>(a, blocks, st);
         default: return launch_mode<DT, kPass1>(a, blocks, st);
     }
 }
@@ -796,7 +904,7 @@ cudaError_t launch_dt(const TransportArgs& a, int mode, int blocks, cudaStream_t
 }  // namespace
 
 int transport_blocks_per_sm(int dtype, int mode) {
-    static int cache[3][4] = {{0}};
+    static int cache[3][5] = {{0}};
     if (cache[dtype][mode]) return cache[dtype][mode];
     const int n = dtype == 0 ? occupancy_mode<0>(mode) : (dtype == 1 ? occupancy_mode<1>(mode) : occupancy_mode<2>(mode));
     cache[dtype][mode] = n;
@@ -824,6 +932,17 @@ cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st) {
 cudaError_t launch_event_adjoint(const mst_grid* g, const TransportArgs& a, int dtype, cudaStream_t st) {
     (void)dtype;
     k_event_adjoint<<<g->sm_count * 8, kTB, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_event_offsets(const mst_grid* g, uint32_t n, cudaStream_t st) {
+    const uint32_t nt = (n + kScanTile - 1) / kScanTile;
+    if (nt == 0u) return cudaSuccess;
+    if (nt > 1024u * 64u) return cudaErrorInvalidValue;  // 2^28 photons; calls that store events hold 2^27
+    uint32_t* tsum = reinterpret_cast<uint32_t*>(g->plist);  // the list is built after the offsets are used
+    k_scan_tiles<<<nt, kTB, 0, st>>>(g->nevbuf, n, tsum);
+    k_scan_top<<<1, 1024, 0, st>>>(tsum, nt);
+    k_scan_apply<<<nt, kTB, 0, st>>>(g->nevbuf, n, tsum, g->evoff);
     return cudaGetLastError();
 }
 

@@ -310,7 +310,7 @@ def test_full_gradient_stored_events_match_replay(m, torch, budget):
     a = g_st.render_grad(*args)
     st_a = g_st.stats()
     g_rp = m.Grid.from_scene(sc)
-    g_rp.set_replay_memory(0 if budget == "replay" else 2048 * 36)
+    g_rp.set_replay_memory(0 if budget == "replay" else 2048 * 44)
     b = g_rp.render_grad(*args)
     st_b = g_rp.stats()
     assert st_a["events_stored"] == st_a["events"] > 2048
