@@ -25,7 +25,7 @@ constexpr uint64_t kReplayChunk = 1ull << 24;    // photons per replay pass-1 / 
 constexpr uint64_t kRecordMaxPhotons = 1ull << 27;
 constexpr int kEventWords = 10;  // packed voxel, offset (3), incoming direction (3), albedo * weight, photon, event number
 constexpr int kEventBytes = kEventWords * 4 + 4;  // the record and its w_s
-constexpr uint64_t kDefaultRecordBytes = 16ull << 30;
+constexpr uint64_t kDefaultRecordBytes = 24ull << 30;
 constexpr uint64_t kFoldSweep = 1ull << 21;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
 constexpr int kMaxTickets = (int)(2 * (kMaxPhotons / kReplayChunk));

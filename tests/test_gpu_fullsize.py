@@ -59,7 +59,7 @@ def test_energy_balance_full_size(case):
     record("fullsize_energy", launched_rel=abs(st["launched"] - incident) / incident,
            balance_rel=abs(out - incident) / incident)
     assert abs(out - incident) < 1e-4 * incident
-    # the forward stored every event (14 GB within the default budget), so W came from them and
+    # the forward stored every event (17 GB within the default budget), so W came from them and
     # the replay is pass 2 alone: it walks the scoring photons up to their last event
     assert st["events_stored"] == st["events"]
     assert 0 < st["replay_segments"] < st["segments"]
