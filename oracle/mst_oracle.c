@@ -924,11 +924,13 @@ void or_full_grad(const or_scene *s, const or_params *P, const double *meas, con
 }
 
 /* ----------------------------------------------------------------------------------------- */
-/* backward MC with the sun local estimate (Eq. ble), one pixel: used only to check          */
-/* Helmholtz reciprocity against the forward estimates. The pixel is sampled uniformly on    */
-/* the image plane and weighted by cos^3 * A_pix / Omega_p, so the mean is the pixel's       */
-/* solid-angle average radiance. A point is sunlit only if its sun-ward ray leaves through   */
-/* the top face, matching top-face illumination in the forward model.                        */
+/* backward MC with the sun local estimate (Eq. ble), one pixel: checks Helmholtz            */
+/* reciprocity against the forward estimates and is the reference of the GPU BMC. The pixel  */
+/* is sampled uniformly on the image plane and weighted by cos^3 * A_pix / Omega_p, so the   */
+/* mean is the pixel's solid-angle average radiance. A point is sunlit only if its sun-ward  */
+/* ray leaves through the top face, matching top-face illumination in the forward model.     */
+/* Sample q of global pixel p draws Philox counters (q, event, 1 + p): every pixel has its   */
+/* own stream (the forward transport uses stream word 0).                                    */
 
 void or_bmc_pixel(const or_scene *s, const or_params *P, int c, int i, int j, uint64_t n, double *mean, double *var) {
     double sun[3] = {-sin(P->sun_zenith) * cos(P->sun_azimuth), -sin(P->sun_zenith) * sin(P->sun_azimuth),
@@ -942,6 +944,7 @@ void or_bmc_pixel(const or_scene *s, const or_params *P, int c, int i, int j, ui
     double omega = rect_solid_angle(x1, x2, y1, y2);
     double apix = (x2 - x1) * (y2 - y1);
     const double *Pc = s->cam_pos + 3 * c;
+    const uint32_t stream = (uint32_t)(1 + pix_offset(s, c) + (long)j * W + i);
     double sum = 0.0, sum2 = 0.0;
     double st[ST_N];
     tctx cx;
@@ -949,7 +952,7 @@ void or_bmc_pixel(const or_scene *s, const or_params *P, int c, int i, int j, ui
     cx.stats = st;
     for (uint64_t q = 0; q < n; ++q) {
         double u[4];
-        draws4(P->seed, q, 0, 1, u);
+        draws4(P->seed, q, 0, stream, u);
         double px = i + u[0], py = j + u[1];
         double xx = (2.0 * px / W - 1.0) * tx, yy = (2.0 * py / H - 1.0) * ty;
         double cosv = 1.0 / sqrt(1.0 + xx * xx + yy * yy);
@@ -974,7 +977,7 @@ void or_bmc_pixel(const or_scene *s, const or_params *P, int c, int i, int j, ui
                 if (I == 0.0) break;
                 if (P->max_order > 0 && (int)ev >= P->max_order) break;
                 if ((int)ev >= P->max_events) break;
-                draws4(P->seed, q, ev, 1, u);
+                draws4(P->seed, q, ev, stream, u);
                 if (I < P->rr_threshold) {
                     if (u[2] < P->rr_survival) I /= P->rr_survival;
                     else break;
