@@ -65,15 +65,16 @@ enum {
     MST_ST_REPLAY_SEGMENTS = 16, MST_ST_REPLAY_EVENTS = 17, MST_ST_LOS_SEGMENTS = 18,
     MST_ST_PIXEL_SEGMENTS = 19, MST_ST_BACKPROJ_SEGMENTS = 20, MST_ST_LOSADJ_SEGMENTS = 21,
     MST_ST_REPLAY_SCATTERS = 22, MST_ST_LOST = 23, /* walks abandoned (non-finite direction); 0 in valid use */
-    MST_ST_EVENTS_STORED = 24 /* full gradient: events the forward stored for the adjoint (0: replayed instead) */
+    MST_ST_EVENTS_STORED = 24, /* full gradient: events the forward stored for the adjoint (0: replayed instead) */
+    MST_ST_BMC_PATHS = 25, MST_ST_BMC_EVENTS = 26, MST_ST_BMC_SEGMENTS = 27 /* mst_render_bmc: flight + sun-ray voxels */
 };
 
 /* phases timed by the profiler (mst_get_phase_times) */
 enum {
     MST_PH_STAGE = 0, MST_PH_TRANSPORT = 1, MST_PH_FOLD = 2, MST_PH_LOS = 3, MST_PH_IMAGES = 4,
     MST_PH_BACKPROJECT = 5, MST_PH_LOS_ADJOINT = 6, MST_PH_REPLAY = 7, MST_PH_COMBINE = 8, MST_PH_REPLAY2 = 9,
-    MST_PH_REPLAY_LIST = 10, MST_PH_EVENT_ADJOINT = 11,
-    MST_NPHASES = 12 /* MST_PH_REPLAY: replay pass 1 (W per photon); MST_PH_EVENT_ADJOINT: W per photon from
+    MST_PH_REPLAY_LIST = 10, MST_PH_EVENT_ADJOINT = 11, MST_PH_BMC = 12,
+    MST_NPHASES = 13 /* MST_PH_REPLAY: replay pass 1 (W per photon); MST_PH_EVENT_ADJOINT: W per photon from
                         the events the forward stored (instead of pass 1); MST_PH_REPLAY_LIST: the list of
                         photons with W != 0 that pass 2 walks; MST_PH_REPLAY2: pass 2 (scatter) */
 };
@@ -195,6 +196,22 @@ int mst_ray_counts(mst_grid *g, float *Q_dev, void *stream);
  * (Sec. 6). psi_dev [1] double or NULL; grad_dev [nvox] double or NULL, receives += eta dPsi. */
 int mst_regularizer(mst_grid *g, const float *beta_dev, double eta, double *psi_dev, double *grad_dev,
                     void *stream);
+
+/* Backward Monte Carlo with the sun local estimate (Eq. ble; Sec. 3, the paper's check of the
+ * in-situ forward model): for every pixel, n_per_pixel paths start at the camera through uniform
+ * points of the pixel (weight cos^3 A_pix / Omega_p, so the mean is the pixel's solid-angle
+ * average radiance), fly by the same voxel walk as the forward transport, and at each
+ * scattering event add albedo I P_HG(d . s_sun) exp(-tau) F, where tau is the optical depth
+ * along the sun-ward ray and the event counts as sunlit only if that ray leaves through the top
+ * face (the forward model's illumination); then albedo, roulette and HG sampling as in
+ * mst_render. Sample q of global pixel p draws Philox counters (q, event, 1 + p) under p->seed.
+ *   images_dev [sum W*H] double: pixel means, in the units of mst_render's images.
+ *   var_dev    [sum W*H] double or NULL: variance of each pixel's mean (n_per_pixel >= 2).
+ * Reads albedo, g, the sun angles and irradiance, rr_threshold (absolute: a path starts with
+ * weight 1), rr_survival, max_order, max_events, seed and grid_dtype. n_per_pixel >= 1; the
+ * handle's per-pixel FP64 scratch is reused. */
+int mst_render_bmc(mst_grid *g, const float *beta_dev, const mst_params *p, uint32_t n_per_pixel, double *images_dev,
+                   double *var_dev, void *stream);
 
 /* Device memory the handle may hold for the events a full-gradient forward render stores
  * (44 B per scattering event: voxel, position, incoming direction, weight, photon index, event

@@ -33,14 +33,14 @@ NSTATS = 32
 STAT_NAMES = ["esc_xm", "esc_xp", "esc_ym", "esc_yp", "esc_zm", "esc_zp", "absorbed", "rr_killed", "rr_gained",
               "forced", "events", "segments", "capped", "escaped_n", "launched", "traced", "replay_segments",
               "replay_events", "los_segments", "pixel_segments", "backproj_segments", "losadj_segments",
-              "replay_scatters", "lost", "events_stored"]
+              "replay_scatters", "lost", "events_stored", "bmc_paths", "bmc_events", "bmc_segments"]
 EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy", "mst_render", "mst_render_grad",
            "mst_transmittance", "mst_form_images", "mst_surrogate_grad", "mst_ray_counts", "mst_regularizer",
            "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
            "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
-           "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory"]
+           "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory", "mst_render_bmc"]
 PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine", "replay2",
-          "replay_list", "event_adjoint"]
+          "replay_list", "event_adjoint", "bmc"]
 
 
 class MSTError(RuntimeError):
@@ -87,6 +87,7 @@ def _load():
     L.mst_regularizer.argtypes = [P, P, D, P, P, P]
     L.mst_set_debug.argtypes = [P, P, P]
     L.mst_set_replay_memory.argtypes = [P, ctypes.c_uint64]
+    L.mst_render_bmc.argtypes = [P, P, P, ctypes.c_uint32, P, P, P]
     L.mst_get_stats.argtypes = [P, P]
     L.mst_set_profiling.argtypes = [P, I]
     L.mst_get_phase_times.argtypes = [P, P, P]
@@ -273,6 +274,15 @@ class Grid:
         out = np.zeros(NSTATS)
         self._check(lib.mst_get_stats(self._h, out.ctypes.data_as(ctypes.c_void_p)), "mst_get_stats")
         return dict(zip(STAT_NAMES, out.tolist()))
+
+    def render_bmc(self, beta, params: Params, n_per_pixel: int, var=True, stream=None):
+        """Backward MC images (Eq. ble): dict(images=[total pix] means, var=variance of each mean)."""
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        img = self._new(self.n_pix)
+        v = self._new(self.n_pix) if var else None
+        self._check(lib.mst_render_bmc(self._h, _ptr(beta), ctypes.byref(params), int(n_per_pixel), _ptr(img), _ptr(v),
+                                       _stream(stream)), "mst_render_bmc")
+        return dict(images=img, var=v)
 
     def set_replay_memory(self, nbytes: int):
         """Budget for the events a full-gradient forward render stores (0: W by replay)."""

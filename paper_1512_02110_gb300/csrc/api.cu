@@ -609,6 +609,30 @@ int mst_render(mst_grid* g, const float* beta, const mst_params* p, double* imag
     return MST_OK;
 }
 
+int mst_render_bmc(mst_grid* g, const float* beta, const mst_params* p, uint32_t n_per_pixel, double* images,
+                   double* var, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta || !images) return fail(g, MST_ERR_INVALID_ARG, "beta and images are required");
+    int rc = check_params(g, p, false);
+    if (rc) return rc;
+    if (n_per_pixel < 1) return fail(g, MST_ERR_INVALID_ARG, "n_per_pixel must be >= 1");
+    if (p->max_events < 1) return fail(g, MST_ERR_INVALID_ARG, "max_events must be >= 1");
+    if (p->max_order < 0) return fail(g, MST_ERR_INVALID_ARG, "max_order must be >= 0");
+    DeviceGuard dg(g->device);
+    cudaStream_t st = as_stream(stream);
+    prof_reset(g);
+    {
+        Phase ph(g, MST_PH_STAGE, st);
+        MST_CK(launch_stage(g, beta, p->grid_dtype, st));
+    }
+    MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
+    MST_CK(cudaMemsetAsync(images, 0, sizeof(double) * g->total_pix, st));
+    MST_CK(cudaMemsetAsync(g->resid, 0, sizeof(double) * g->total_pix, st));  // sum of squares
+    Phase ph(g, MST_PH_BMC, st);
+    MST_CK(launch_bmc(g, p, n_per_pixel, images, g->resid, var, st));
+    return MST_OK;
+}
+
 int mst_render_grad(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const uint8_t* mask,
                     double* images, double* grad, double* loss, void* stream) {
     if (!g) return MST_ERR_INVALID_ARG;

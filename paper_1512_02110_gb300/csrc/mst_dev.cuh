@@ -65,8 +65,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // (2 (x >> 9) + 1) / 2^24: 24 significant bits, exact in FP32, strictly inside (0, 1).
 __device__ __forceinline__ float u01(uint32_t x) { return __uint2float_rn(2u * (x >> 9) + 1u) * 5.9604644775390625e-08f; }
 
-__device__ __forceinline__ float4 draws(uint2 key, uint64_t photon, uint32_t event) {
-    const uint4 x = philox4x32_10(make_uint4((uint32_t)photon, (uint32_t)(photon >> 32), event, 0u), key);
+// stream 0: the forward transport and its replays; 1 + p: backward paths of global pixel p
+__device__ __forceinline__ float4 draws(uint2 key, uint64_t photon, uint32_t event, uint32_t stream = 0u) {
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)photon, (uint32_t)(photon >> 32), event, stream), key);
     return make_float4(u01(x.x), u01(x.y), u01(x.z), u01(x.w));
 }
 

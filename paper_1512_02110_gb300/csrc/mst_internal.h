@@ -152,6 +152,10 @@ cudaError_t launch_fold_grad(const mst_grid* g, cudaStream_t st);
 cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st);
 // W per photon from the stored events (returns at once when they did not fit)
 cudaError_t launch_event_adjoint(const mst_grid* g, const TransportArgs& a, int dtype, cudaStream_t st);
+// backward MC images (Eq. ble): n paths per pixel, sums into sum / sum2, then sum <- means and
+// var <- variances of the means (var may be NULL)
+cudaError_t launch_bmc(const mst_grid* g, const mst_params* p, uint32_t n, double* sum, double* sum2, double* var,
+                       cudaStream_t st);
 // evoff = exclusive prefix sum of the n photons' event counts (nevbuf)
 cudaError_t launch_event_offsets(const mst_grid* g, uint32_t n, cudaStream_t st);
 cudaError_t launch_los(const mst_grid* g, int dtype, const double* L, const double* jfix, const float* beta_ref,
