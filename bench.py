@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
     ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
-    ap.add_argument("--study", default=None, choices=["precision", "recon"],
+    ap.add_argument("--study", default=None, choices=["precision", "recon", "bmc"],
                     help="FP16/BF16 brick forms against FP32 at equal photon count (prints one JSON line)")
     return ap.parse_args()
 
@@ -446,6 +446,48 @@ def run_batch(args):
     return 0
 
 
+def run_bmc_study(args):
+    """Backward MC (Eq. ble) on the benchmark scene: throughput (paths and voxel segments per
+    second), the pixels' relative standard errors, and the images against the forward render
+    with the voxelised local estimate at 1e8 photons (the paper's in-situ check, Sec. 3), for
+    256 and 1024 paths per pixel. Prints one JSON line."""
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(0)
+    sc, p = synth.cfg_cumulus64(int(args.photons))
+    grid = m.Grid.from_scene(sc)
+    beta = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
+    prm = m.make_params(p)
+    grid.render(beta, prm)  # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    fwd = grid.render(beta, prm)["images"]
+    b.record()
+    torch.cuda.synchronize()
+    out = {"study": "bmc", "workload": "cumulus64, 9 in-situ 128x128 cameras",
+           "forward_voxel_le": {"photons": int(args.photons), "ms": a.elapsed_time(b)}}
+    f = fwd.cpu().numpy()
+    lit = f > 1e-3 * f.max()
+    for n in (256, 1024):
+        grid.render_bmc(beta, prm, 32)  # warm-up
+        a.record()
+        r = grid.render_bmc(beta, prm, n)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        st = grid.stats()
+        img, var = r["images"].cpu().numpy(), r["var"].cpu().numpy()
+        rse = np.sqrt(var[lit]) / np.maximum(img[lit], 1e-300)
+        out[f"bmc_{n}"] = {"ms": ms, "paths_per_s": st["bmc_paths"] / (ms * 1e-3),
+                           "segments_per_s": st["bmc_segments"] / (ms * 1e-3), "events_per_path":
+                           st["bmc_events"] / st["bmc_paths"], "median_rel_std_err": float(np.median(rse)),
+                           "image_rel_l2_vs_forward": float(np.linalg.norm(img - f) / np.linalg.norm(f))}
+    print(json.dumps(out))
+    return 0
+
+
 def run_recon_study(args):
     """Reconstruction of the cumulus64 field from its seed-4 images, 1e8 photons per render,
     from beta = 1 1/km everywhere (Sec. 5 loop at the benchmark scale): projected L-BFGS on the
@@ -535,6 +577,8 @@ def main():
         return run_precision_study(args)
     if args.study == "recon":
         return run_recon_study(args)
+    if args.study == "bmc":
+        return run_bmc_study(args)
     if args.workload == "batch16":
         return run_batch(args)
     return run_ours(args)
