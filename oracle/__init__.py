@@ -37,7 +37,8 @@ class _Scene(ctypes.Structure):
                 ("n_rays", ctypes.c_int), ("pad_", ctypes.c_int),
                 ("h", ctypes.c_double * 3), ("o", ctypes.c_double * 3),
                 ("beta", ctypes.c_void_p), ("cam_pos", ctypes.c_void_p), ("cam_rot", ctypes.c_void_p),
-                ("cam_w", ctypes.c_void_p), ("cam_h", ctypes.c_void_p), ("cam_fov", ctypes.c_void_p)]
+                ("cam_w", ctypes.c_void_p), ("cam_h", ctypes.c_void_p), ("cam_fov", ctypes.c_void_p),
+                ("reg_wz", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -104,6 +105,9 @@ class _Bound:
         s.o = (ctypes.c_double * 3)(*scene.origin)
         s.beta, s.cam_pos, s.cam_rot = _ptr(self.beta), _ptr(self.pos), _ptr(self.rot)
         s.cam_w, s.cam_h, s.cam_fov = _ptr(self.w), _ptr(self.h), _ptr(self.fov)
+        wz = getattr(scene, "reg_wz", None)
+        self.wz = None if wz is None else np.ascontiguousarray(wz, dtype=np.float64)
+        s.reg_wz = None if self.wz is None else _ptr(self.wz)
         self.s = s
 
     @property

@@ -58,6 +58,7 @@ typedef struct {
     const int *cam_w;        /* [C] */
     const int *cam_h;        /* [C] */
     const double *cam_fov;   /* [C] horizontal field of view, rad */
+    const double *reg_wz;    /* [nz] altitude weights W of the regulariser (Sec. 6), NULL: W = I */
 } or_scene;
 
 typedef struct {
@@ -724,9 +725,12 @@ void or_ray_counts(const or_scene *s, double *Q) {
 }
 
 /* ----------------------------------------------------------------------------------------- */
-/* regulariser: Psi = || Lap beta ||^2 with the 6-neighbour graph Laplacian, W = identity    */
+/* regulariser: Psi = || W Lap beta ||^2 with the 6-neighbour graph Laplacian and W diagonal */
+/* in altitude (the scene's reg_wz per layer; identity when it is NULL)                      */
 
 void or_laplacian(const or_scene *s, const double *beta, double *psi, double *grad) {
+    /* Psi = |W Lap beta|^2 with the 6-neighbour graph Laplacian and W diagonal, W_kk = the    */
+    /* altitude weight of voxel k's layer (Sec. 6); dPsi = 2 Lap^T W^T W Lap beta.             */
     const long nvox = nvox_of(s);
     double *lb = (double *)calloc((size_t)nvox, sizeof(double));
     const int n[3] = {s->nx, s->ny, s->nz};
@@ -740,13 +744,17 @@ void or_laplacian(const or_scene *s, const double *beta, double *psi, double *gr
                 if (w[a] < 0 || w[a] >= n[a]) continue;
                 acc += beta[lin(s, w)] - beta[k];
             }
-        lb[k] = acc;
+        lb[k] = acc;                      /* (Lap beta)_k */
     }
     double ps = 0.0;
-    for (long k = 0; k < nvox; ++k) ps += lb[k] * lb[k];
+    for (long k = 0; k < nvox; ++k) {
+        const double wk = s->reg_wz ? s->reg_wz[k / ((long)s->nx * s->ny)] : 1.0;
+        ps += (wk * lb[k]) * (wk * lb[k]);
+        lb[k] *= wk * wk;                 /* now (W^T W Lap beta)_k */
+    }
     *psi = ps;
     if (grad) {
-        /* the graph Laplacian is symmetric: dPsi = 2 Lap (Lap beta) */
+        /* the graph Laplacian is symmetric: Lap^T = Lap */
         for (long k = 0; k < nvox; ++k) {
             int v[3] = {(int)(k % s->nx), (int)((k / s->nx) % s->ny), (int)(k / ((long)s->nx * s->ny))};
             double acc = 0.0;

@@ -42,6 +42,7 @@ class Scene:
     cam_h: np.ndarray       # [C] int32
     cam_fov: np.ndarray     # [C] float64, horizontal field of view, radians
     n_rays: int = 10        # sub-pixel rays per pixel (N_rays, Sec. 3.1)
+    reg_wz: Optional[np.ndarray] = None  # [nz] altitude weights of the regulariser, None: all 1
 
     @property
     def nvox(self) -> int:

@@ -524,6 +524,35 @@ def test_laplacian_regulariser(orc):
         assert abs(fd - g[k]) < 1e-9 * max(1.0, abs(g[k]))
 
 
+def test_altitude_weighted_laplacian(orc):
+    """Psi = |W Lap beta|^2 with W diagonal by altitude (Sec. 6): the delta pin with a weight on
+    the delta's layer and on its neighbours' layers, zero weights removing layers, and the
+    gradient 2 Lap^T W^T W Lap beta against central differences."""
+    import dataclasses
+    base = synth.make_scene((5, 4, 3), (10.0, 10.0, 10.0), synth.homogeneous((5, 4, 3), 0.0),
+                            synth.make_cameras([(1.0, 1.0, -1.0)], 2, 2, 40.0))
+    b = np.zeros(base.nvox)
+    b[2 + 5 * (1 + 4 * 1)] = 1.0  # interior voxel of layer 1: Lap = -6 there, +1 at its 6 neighbours
+    wz = np.array([0.5, 3.0, 2.0])
+    sc = dataclasses.replace(base, reg_wz=wz)
+    psi, _ = orc.laplacian(sc, b)
+    # layer 1 holds the voxel (-6) and its 4 in-layer neighbours; layers 0 and 2 one neighbour each
+    assert abs(psi - (3.0 ** 2 * (36 + 4) + 0.5 ** 2 + 2.0 ** 2)) < 1e-12
+    psi0, _ = orc.laplacian(dataclasses.replace(base, reg_wz=np.array([0.0, 1.0, 0.0])), b)
+    assert psi0 == 36 + 4
+    rng = np.random.default_rng(1)
+    b = rng.random(base.nvox)
+    psi1, g1 = orc.laplacian(dataclasses.replace(base, reg_wz=np.full(3, 2.0)), b)
+    psi_u, g_u = orc.laplacian(base, b)
+    assert abs(psi1 - 4.0 * psi_u) < 1e-9 * psi1 and np.allclose(g1, 4.0 * g_u, rtol=1e-12)
+    psi, g = orc.laplacian(sc, b)
+    for k in range(0, sc.nvox, 5):
+        e = np.zeros(sc.nvox)
+        e[k] = 1e-3
+        fd = (orc.laplacian(sc, b + e)[0] - orc.laplacian(sc, b - e)[0]) / 2e-3
+        assert abs(fd - g[k]) < 1e-9 * max(1.0, abs(g[k]))
+
+
 # ------------------------------------------------------------------------------------------
 # full gradient by the score of the free-flight density, against central differences with
 # common random numbers (FD-CRN)
