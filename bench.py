@@ -491,7 +491,8 @@ def run_bmc_study(args):
 def run_recon_study(args):
     """Reconstruction of the cumulus64 field from its seed-4 images, 1e8 photons per render,
     from beta = 1 1/km everywhere (Sec. 5 loop at the benchmark scale): projected L-BFGS on the
-    full gradient (common random numbers), and the paper's surrogate loop (Eq. GD, N_GD = 5)
+    full gradient (common random numbers), also over 2^3- and 4^3-voxel blocks (Sec. 5), and the
+    paper's surrogate loop (Eq. GD, N_GD = 5)
     under each conditioning of the gradient (none, 1/ray count, ray count). Prints one JSON line
     with the loss, epsilon = |b - b_true|_1 / |b_true|_1 and delta_mass = (|b|_1 - |b_true|_1) /
     |b_true|_1 (the paper's two error measures) along each run, and its GPU time."""
@@ -519,6 +520,16 @@ def run_recon_study(args):
     torch.cuda.synchronize()
     out["lbfgs_full"] = {"iterations": st.it, "renders": st.n_renders, "s": time.perf_counter() - t0,
                          "loss0": st.losses[0], "trace": trace[::5] + trace[-1:]}
+    for blk in ((2, 2, 2), (4, 4, 4)):  # the paper's piecewise-constant blocks (Sec. 5): fewer unknowns
+        trace = []
+        t0 = time.perf_counter()
+        st = m.reconstruct(grid, meas, beta0, m.make_params(p, grad_mode="full"), iters=args.recon_iters,
+                           method="lbfgs", block=blk,
+                           callback=lambda s: trace.append({"it": s.it, "loss": s.losses[-1], **errs(s.beta)}))
+        torch.cuda.synchronize()
+        out["lbfgs_full_block%d" % blk[0]] = {"block": blk, "unknowns": int(st.x.size), "iterations": st.it,
+                                              "renders": st.n_renders, "s": time.perf_counter() - t0,
+                                              "loss0": st.losses[0], "trace": trace[::5] + trace[-1:]}
     for cond in ["none", "inv_count", "count"]:
         prm = m.make_params(p, grad_mode="surrogate", conditioning=cond)
         b0 = torch.from_numpy(beta0.astype(np.float32)).cuda()

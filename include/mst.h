@@ -192,10 +192,17 @@ int mst_surrogate_grad(mst_grid *g, const float *beta_dev, const double *L_ref_d
  * Q_dev [C][nvox] float. */
 int mst_ray_counts(mst_grid *g, float *Q_dev, void *stream);
 
-/* Laplacian regulariser Psi = ||Lap beta||^2 with the 6-neighbour graph Laplacian and W = I
- * (Sec. 6). psi_dev [1] double or NULL; grad_dev [nvox] double or NULL, receives += eta dPsi. */
+/* Laplacian regulariser Psi = ||W Lap beta||^2 with the 6-neighbour graph Laplacian and W
+ * diagonal by altitude (Sec. 6; W = I unless mst_set_reg_weights gave weights), gradient
+ * 2 Lap^T W^T W Lap beta. psi_dev [1] double or NULL; grad_dev [nvox] double or NULL,
+ * receives += eta dPsi. */
 int mst_regularizer(mst_grid *g, const float *beta_dev, double eta, double *psi_dev, double *grad_dev,
                     void *stream);
+
+/* Altitude weights of the regulariser (Sec. 6): W_kk = wz_host[iz] for voxel k in layer iz.
+ * wz_host [nz] double, copied; NULL restores W = I. Used by mst_regularizer and by the eta
+ * term of mst_render_grad and mst_surrogate_grad. Synchronises the device. */
+int mst_set_reg_weights(mst_grid *g, const double *wz_host);
 
 /* Backward Monte Carlo with the sun local estimate (Eq. ble; Sec. 3, the paper's check of the
  * in-situ forward model): for every pixel, n_per_pixel paths start at the camera through uniform

@@ -38,7 +38,8 @@ EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy"
            "mst_transmittance", "mst_form_images", "mst_surrogate_grad", "mst_ray_counts", "mst_regularizer",
            "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
            "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
-           "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory", "mst_render_bmc"]
+           "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory", "mst_render_bmc",
+           "mst_set_reg_weights"]
 PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine", "replay2",
           "replay_list", "event_adjoint", "bmc"]
 
@@ -87,6 +88,7 @@ def _load():
     L.mst_regularizer.argtypes = [P, P, D, P, P, P]
     L.mst_set_debug.argtypes = [P, P, P]
     L.mst_set_replay_memory.argtypes = [P, ctypes.c_uint64]
+    L.mst_set_reg_weights.argtypes = [P, P]
     L.mst_render_bmc.argtypes = [P, P, P, ctypes.c_uint32, P, P, P]
     L.mst_get_stats.argtypes = [P, P]
     L.mst_set_profiling.argtypes = [P, I]
@@ -284,6 +286,16 @@ class Grid:
                                        _stream(stream)), "mst_render_bmc")
         return dict(images=img, var=v)
 
+    def set_reg_weights(self, wz=None):
+        """Altitude weights W of the regulariser, one per layer ([nz]); None restores W = I."""
+        if wz is None:
+            self._check(lib.mst_set_reg_weights(self._h, None), "mst_set_reg_weights")
+            return
+        w = np.ascontiguousarray(wz, dtype=np.float64)
+        if w.shape != (self.shape[2],):
+            raise ValueError(f"need {self.shape[2]} weights, one per layer")
+        self._check(lib.mst_set_reg_weights(self._h, w.ctypes.data_as(ctypes.c_void_p)), "mst_set_reg_weights")
+
     def set_replay_memory(self, nbytes: int):
         """Budget for the events a full-gradient forward render stores (0: W by replay)."""
         self._check(lib.mst_set_replay_memory(self._h, int(nbytes)), "mst_set_replay_memory")
@@ -388,4 +400,4 @@ def transmittance_noalloc(shape, h, origin, cam_pos, cam_rot, cam_w, cam_h, cam_
     return T
 
 
-from .autograd import RenderLoss, reconstruct  # noqa: E402  (needs `lib` above)
+from .autograd import Blocks, RenderLoss, reconstruct  # noqa: E402  (needs `lib` above)

@@ -39,44 +39,89 @@ class ReconState:
     y_hist: List[np.ndarray] = dataclasses.field(default_factory=list)
     losses: List[float] = dataclasses.field(default_factory=list)
     n_renders: int = 0
+    x: Optional[np.ndarray] = None  # block values when the field is block-parametrised
 
     def save(self, path: str):
+        n = self.beta.size if self.x is None else self.x.size
         np.savez(path, beta=self.beta, it=self.it, losses=np.array(self.losses), n_renders=self.n_renders,
-                 s=np.array(self.s_hist) if self.s_hist else np.zeros((0, self.beta.size)),
-                 y=np.array(self.y_hist) if self.y_hist else np.zeros((0, self.beta.size)))
+                 s=np.array(self.s_hist) if self.s_hist else np.zeros((0, n)),
+                 y=np.array(self.y_hist) if self.y_hist else np.zeros((0, n)),
+                 x=self.x if self.x is not None else np.zeros(0))
 
     @classmethod
     def load(cls, path: str) -> "ReconState":
         z = np.load(path)
+        x = z["x"] if "x" in z.files and z["x"].size else None
         return cls(beta=z["beta"], it=int(z["it"]), s_hist=list(z["s"]), y_hist=list(z["y"]),
-                   losses=z["losses"].tolist(), n_renders=int(z["n_renders"]))
+                   losses=z["losses"].tolist(), n_renders=int(z["n_renders"]), x=x)
 
 
-def _eval(grid, params, meas, mask, beta_np):
+class Blocks:
+    """beta = B theta: beta piecewise constant over 3-D blocks of bx x by x bz voxels (Sec. 5,
+    the paper's dimensionality reduction; blocks at the far faces may be smaller). expand
+    gives beta from the block values, reduce applies B^T (sums a voxel field over each
+    block: the gradient with respect to theta), restrict gives the block means."""
+
+    def __init__(self, shape, block):
+        nx, ny, nz = (int(v) for v in shape)
+        bx, by, bz = (int(v) for v in block)
+        if min(bx, by, bz) < 1:
+            raise ValueError("block sizes must be >= 1")
+        nbx, nby, nbz = -(-nx // bx), -(-ny // by), -(-nz // bz)
+        ix = np.arange(nx) // bx
+        iy = np.arange(ny) // by
+        iz = np.arange(nz) // bz
+        self.bid = (ix[None, None, :] + nbx * (iy[None, :, None] + nby * iz[:, None, None])).ravel()
+        self.n = nbx * nby * nbz
+        self.count = np.bincount(self.bid, minlength=self.n).astype(np.float64)
+
+    def expand(self, theta):
+        return np.asarray(theta, dtype=np.float64)[self.bid]
+
+    def reduce(self, g):
+        return np.bincount(self.bid, weights=np.asarray(g, dtype=np.float64), minlength=self.n)
+
+    def restrict(self, beta):
+        return self.reduce(beta) / self.count
+
+
+def _eval(grid, params, meas, mask, x, P=None):
+    """Loss and gradient at parameter vector x (beta itself, or block values under P)."""
+    beta_np = x if P is None else P.expand(x)
     beta = torch.from_numpy(beta_np.astype(np.float32)).to(grid.device)
     out = grid.render_grad(beta, params, meas, mask, images=False)
-    return float(out["loss"].item()), out["grad"].cpu().numpy()
+    g = out["grad"].cpu().numpy()
+    return float(out["loss"].item()), (g if P is None else P.reduce(g))
 
 
 def reconstruct(grid, meas, beta0, params, iters: int = 50, method: str = "lbfgs", mask=None, history: int = 10,
                 step: float = 1e-3, n_gd: int = 5, state: Optional[ReconState] = None,
-                callback: Optional[Callable[[ReconState], None]] = None) -> ReconState:
+                callback: Optional[Callable[[ReconState], None]] = None, block=None) -> ReconState:
     """Recovers beta >= 0 from measured images.
 
     method="lbfgs": projected L-BFGS. The photon seed is held fixed across iterations (common
     random numbers), so the objective is one deterministic function of beta.
     method="gd": the paper's loop (Eq. GD): a forward render gives L and j = L/beta; then n_gd
     projected steps beta <- max(0, beta - step * dE/dbeta) with j fixed; repeat.
+    block=(bx, by, bz): optimise one value per block of voxels (Blocks); the state's x holds the
+    block values and its beta the expanded field.
     """
-    st = state or ReconState(beta=np.maximum(np.asarray(beta0, dtype=np.float64), 0.0))
+    P = Blocks(grid.shape, block) if block is not None else None
+    b0 = np.maximum(np.asarray(beta0, dtype=np.float64), 0.0)
+    if state is None:
+        x0 = b0 if P is None else P.restrict(b0)
+        st = ReconState(beta=x0 if P is None else P.expand(x0), x=None if P is None else x0)
+    else:
+        st = state
     if method == "gd":
-        return _run_gd(grid, meas, params, mask, iters, step, n_gd, st, callback)
-    f, g = _eval(grid, params, meas, mask, st.beta)
+        return _run_gd(grid, meas, params, mask, iters, step, n_gd, st, callback, P)
+    cur = lambda: st.beta if P is None else st.x  # noqa: E731
+    f, g = _eval(grid, params, meas, mask, cur(), P)
     st.n_renders += 1
     if not st.losses:
         st.losses.append(f)
     while st.it < iters:
-        x = st.beta
+        x = cur()
         free = (x > 0) | (g < 0)
         gf = np.where(free, g, 0.0)
         d = -_two_loop(gf, st.s_hist, st.y_hist)
@@ -90,7 +135,7 @@ def reconstruct(grid, meas, beta0, params, iters: int = 50, method: str = "lbfgs
         alpha, ok = 1.0, False
         for _ in range(20):
             xn = np.maximum(x + alpha * d, 0.0)
-            fn, gn = _eval(grid, params, meas, mask, xn)
+            fn, gn = _eval(grid, params, meas, mask, xn, P)
             st.n_renders += 1
             if fn <= f + 1e-4 * np.dot(gf, xn - x):
                 ok = True
@@ -109,7 +154,11 @@ def reconstruct(grid, meas, beta0, params, iters: int = 50, method: str = "lbfgs
             if len(st.s_hist) > history:
                 st.s_hist.pop(0)
                 st.y_hist.pop(0)
-        st.beta, f, g = xn, fn, gn
+        if P is None:
+            st.beta = xn
+        else:
+            st.x, st.beta = xn, P.expand(xn)
+        f, g = fn, gn
         st.it += 1
         st.losses.append(f)
         if callback:
@@ -133,7 +182,7 @@ def _two_loop(g, S, Y):
     return q
 
 
-def _run_gd(grid, meas, params, mask, iters, step, n_gd, st, callback):
+def _run_gd(grid, meas, params, mask, iters, step, n_gd, st, callback, P=None):
     while st.it < iters:
         beta_ref = torch.from_numpy(st.beta.astype(np.float32)).to(grid.device)
         L_ref = grid.render(beta_ref, params, images=False, L=True)["L"]
@@ -142,7 +191,12 @@ def _run_gd(grid, meas, params, mask, iters, step, n_gd, st, callback):
             beta = torch.from_numpy(st.beta.astype(np.float32)).to(grid.device)
             out = grid.surrogate_grad(beta, L_ref, beta_ref, params, meas, mask)
             st.losses.append(float(out["loss"].item()))
-            st.beta = np.maximum(st.beta - step * out["grad"].cpu().numpy(), 0.0)
+            g = out["grad"].cpu().numpy()
+            if P is None:
+                st.beta = np.maximum(st.beta - step * g, 0.0)
+            else:
+                st.x = np.maximum(st.x - step * P.reduce(g), 0.0)
+                st.beta = P.expand(st.x)
         st.it += 1
         if callback:
             callback(st)

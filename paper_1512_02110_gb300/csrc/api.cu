@@ -377,6 +377,7 @@ void free_all(mst_grid* g) {
     cudaFree(g->evrec);
     cudaFree(g->wseq);
     cudaFree(g->evoff);
+    cudaFree(g->reg_wz);
     cudaFree(g->ev_count);
     if (g->ev_seen) cudaFreeHost(g->ev_seen);
     if (g->ev_seen_ready) cudaEventDestroy(g->ev_seen_ready);
@@ -876,6 +877,24 @@ int mst_get_phase_times(mst_grid* g, double* ms, int* launches) {
         ms[r.phase] += (double)t;
         if (launches) launches[r.phase] += 1;
     }
+    return MST_OK;
+}
+
+int mst_set_reg_weights(mst_grid* g, const double* wz) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (!wz) {
+        if (g->reg_wz) {
+            MST_CK(cudaDeviceSynchronize());
+            cudaFree(g->reg_wz);
+            g->reg_wz = nullptr;
+        }
+        return MST_OK;
+    }
+    for (int z = 0; z < g->geo.nz; ++z)
+        if (!std::isfinite(wz[z])) return fail(g, MST_ERR_INVALID_ARG, "altitude weights must be finite");
+    if (!g->reg_wz) MST_CK(cudaMalloc(&g->reg_wz, sizeof(double) * g->geo.nz));
+    MST_CK(cudaMemcpy(g->reg_wz, wz, sizeof(double) * g->geo.nz, cudaMemcpyHostToDevice));
     return MST_OK;
 }
 

@@ -117,7 +117,8 @@ struct mst_grid {
     unsigned int* score_cnt = nullptr;  // [2 kScoreBins + 1] list bin counts, bin fill, list length
     double* g64 = nullptr;        // [nvox]
     double* resid = nullptr;      // [total_pix] 2 M (i - i_meas)
-    double* lap = nullptr;        // [nvox] Lap beta
+    double* lap = nullptr;        // [nvox] W^T W Lap beta
+    double* reg_wz = nullptr;     // [nz] altitude weights W of the regulariser, NULL: W = I
     float* omega = nullptr;       // [total_pix]
     float* Qw = nullptr;          // [C][nvox] conditioning weights for qw_mode
     int qw_mode = -1;

@@ -219,11 +219,14 @@ __device__ __forceinline__ double lap_at(const Geo& g, const TIn* x, int k) {
     return acc;
 }
 
-__global__ void k_lap1(const Geo g, const float* __restrict__ beta, double* __restrict__ lap, double* psi) {
+// Psi = |W Lap beta|^2 (W diagonal by altitude: wz[iz], or 1 when wz is NULL); lap <- W^T W Lap beta
+__global__ void k_lap1(const Geo g, const float* __restrict__ beta, const double* __restrict__ wz,
+                       double* __restrict__ lap, double* psi) {
     double s = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.nvox; k += gridDim.x * blockDim.x) {
-        const double v = lap_at(g, beta, k);
-        lap[k] = v;
+        const double w = wz ? wz[k / (g.nx * g.ny)] : 1.0;
+        const double v = w * lap_at(g, beta, k);
+        lap[k] = w * v;
         s += v * v;
     }
     s = warp_sum(s);
@@ -318,7 +321,7 @@ cudaError_t launch_regularizer(const mst_grid* g, const float* beta, double eta,
     const int nb = nblocks(g->geo.nvox, kTB, 4096);
     cudaError_t e = cudaMemsetAsync(psi, 0, sizeof(double), st);
     if (e != cudaSuccess) return e;
-    k_lap1<<<nb, kTB, 0, st>>>(g->geo, beta, lap, psi);
+    k_lap1<<<nb, kTB, 0, st>>>(g->geo, beta, g->reg_wz, lap, psi);
     if (grad) k_lap2<<<nb, kTB, 0, st>>>(g->geo, lap, eta, grad);
     if (loss) k_add_scaled<<<1, 32, 0, st>>>(loss, psi, eta);
     return cudaGetLastError();

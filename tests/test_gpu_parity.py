@@ -86,14 +86,22 @@ def test_ray_counts(m):
     assert np.mean(diff == 0) > 0.9995
 
 
-def test_regularizer(m, torch):
+@pytest.mark.parametrize("weighted", [False, True])
+def test_regularizer(m, torch, weighted):
+    import dataclasses
     sc = f32_scene(_small_scene())
+    if weighted:  # altitude weights W of Sec. 6, one per layer
+        sc = dataclasses.replace(sc, reg_wz=np.linspace(2.0, 0.25, sc.shape[2]))
     grid = m.Grid.from_scene(sc)
+    grid.set_reg_weights(sc.reg_wz)
     g = torch.zeros(sc.nvox, dtype=torch.float64, device="cuda")
     psi = grid.regularizer(dev(sc.beta, np.float32), 0.7, g)
     psi_or, g_or = oracle.laplacian(sc)
     assert abs(psi.item() - psi_or) <= 1e-12 * psi_or
     assert rel_l2(g.cpu().numpy(), 0.7 * g_or) < 1e-12
+    grid.set_reg_weights(None)
+    psi_u = grid.regularizer(dev(sc.beta, np.float32), 0.7, None)
+    assert weighted or abs(psi_u.item() - psi_or) <= 1e-12 * psi_or
 
 
 @pytest.mark.parametrize("cond", ["none", "inv_count"])

@@ -78,3 +78,39 @@ def test_surrogate_gd_loop_descends_with_a_safe_step():
     assert st.it == 20 and st.n_renders == 20 and len(st.losses) == 100
     assert all(b <= a + 1e-12 for a, b in zip(st.losses, st.losses[1:]))
     assert np.all(st.beta >= 0.0)
+
+
+def test_blocks_parametrisation():
+    """beta = B theta over ragged 3-D blocks: B^T is the adjoint of B, block means invert the
+    expansion, and every voxel lands in the block its coordinates give."""
+    from paper_1512_02110_gb300.autograd import Blocks
+    shape, block = (5, 4, 3), (2, 3, 2)
+    P = Blocks(shape, block)
+    assert P.n == 3 * 2 * 2 and P.count.sum() == 60
+    for k in range(60):
+        ix, iy, iz = k % 5, (k // 5) % 4, k // 20
+        assert P.bid[k] == ix // 2 + 3 * (iy // 3 + 2 * (iz // 2))
+    rng = np.random.default_rng(2)
+    th, g = rng.random(P.n), rng.random(60)
+    assert abs(np.dot(P.expand(th), g) - np.dot(th, P.reduce(g))) < 1e-12
+    assert np.allclose(P.restrict(P.expand(th)), th)
+
+
+def test_block_reconstruction_reaches_the_block_optimum(tmp_path):
+    scipy_opt = __import__("pytest").importorskip("scipy.optimize")
+    from paper_1512_02110_gb300.autograd import Blocks, ReconState, reconstruct
+    A, y = _nnls_case(m=40, n=24)
+    grid = _QuadGrid(A, y)
+    grid.shape = (4, 3, 2)
+    P = Blocks(grid.shape, (2, 2, 1))
+    B = np.stack([P.expand(np.eye(P.n)[b]) for b in range(P.n)], axis=1)  # [nvox, nblocks]
+    th_ref, _ = scipy_opt.nnls(A @ B, y)
+    st = reconstruct(grid, None, np.full(24, 0.5), None, iters=200, method="lbfgs", block=(2, 2, 1))
+    assert np.allclose(st.x, th_ref, atol=1e-4) and np.allclose(st.beta, B @ st.x)
+    path = str(tmp_path / "s.npz")
+    st.save(path)
+    r = ReconState.load(path)
+    assert np.array_equal(r.x, st.x) and np.array_equal(r.beta, st.beta)
+    g = reconstruct(grid, None, np.full(24, 0.5), None, iters=10, method="gd", step=0.5 / np.linalg.norm(A @ B, 2) ** 2,
+                    n_gd=5, block=(2, 2, 1))
+    assert all(b2 <= b1 + 1e-12 for b1, b2 in zip(g.losses, g.losses[1:])) and np.allclose(g.beta, B @ g.x)
