@@ -78,6 +78,7 @@ def lib():
         L.or_laplacian.argtypes = [P, P, P, P]
         L.or_surrogate_grad.argtypes = [P, P, P, P, P, ctypes.c_int, ctypes.c_double, P, P, P]
         L.or_full_grad.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P, P, P]
+        L.or_full_grad_classic.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P, P]
         L.or_bmc_pixel.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P]
         _lib = L
     return _lib
@@ -239,7 +240,9 @@ def surrogate_grad(scene, L_ref, beta_ref, meas, mask=None, conditioning="none",
     return dict(images=img, grad=g, loss=loss.value)
 
 
-def full_grad(scene, params, meas, mask=None, eta=0.0, nthreads=0, skip=None):
+def full_grad(scene, params, meas, mask=None, eta=0.0, nthreads=0, skip=None, classic=False):
+    """Loss and full gradient (score replay) of the voxel estimator, or of the classic local
+    estimator with classic=True (images by Eq. fle; no L)."""
     b = _Bound(scene)
     q = _params(params)
     m = np.ascontiguousarray(meas, dtype=np.float64).ravel()
@@ -250,8 +253,13 @@ def full_grad(scene, params, meas, mask=None, eta=0.0, nthreads=0, skip=None):
     L = np.zeros((scene.n_cams, scene.nvox))
     st = np.zeros(16)
     loss = ctypes.c_double()
-    lib().or_full_grad(b.ref, ctypes.byref(q), _ptr(m), _ptr(mk), float(eta), int(nthreads), _ptr(img), _ptr(g),
-                       ctypes.byref(loss), _ptr(L), _ptr(st), _ptr(sk))
+    if classic:
+        lib().or_full_grad_classic(b.ref, ctypes.byref(q), _ptr(m), _ptr(mk), float(eta), int(nthreads), _ptr(img),
+                                   _ptr(g), ctypes.byref(loss), _ptr(st), _ptr(sk))
+        L = None
+    else:
+        lib().or_full_grad(b.ref, ctypes.byref(q), _ptr(m), _ptr(mk), float(eta), int(nthreads), _ptr(img),
+                           _ptr(g), ctypes.byref(loss), _ptr(L), _ptr(st), _ptr(sk))
     return dict(images=img, grad=g, loss=loss.value, L=L, stats=dict(zip(ST_NAMES, st.tolist())))
 
 

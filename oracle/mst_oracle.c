@@ -332,6 +332,23 @@ static void tau_visit(void *c, long k, double len) {
     t->tau += t->beta[k] * len;
 }
 
+/* adds weight * (length in voxel m) to g[m] along the segment from X (in voxel v) to point Y */
+typedef struct { double *g; double weight; } scatter_ctx;
+static void scatter_visit(void *c, long k, double len) {
+    scatter_ctx *t = (scatter_ctx *)c;
+    t->g[k] += t->weight * len;
+}
+
+static void shadow_scatter(const or_scene *s, const double X[3], const int v[3], const double Y[3], double weight,
+                           double *g) {
+    double d[3] = {Y[0] - X[0], Y[1] - X[1], Y[2] - X[2]};
+    double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (dist == 0.0) return;
+    for (int a = 0; a < 3; ++a) d[a] /= dist;
+    scatter_ctx t = {g, weight};
+    walk(s, X, d, v, 0.0, dist, scatter_visit, &t);
+}
+
 /* optical depth from X (in voxel v) to point Y, clipped to the grid */
 static double tau_to_point(const or_scene *s, const double X[3], const int v[3], const double Y[3]) {
     double d[3] = {Y[0] - X[0], Y[1] - X[1], Y[2] - X[2]};
@@ -367,6 +384,8 @@ typedef struct {
     double *cimg;      /* classic images [sum W*H] or NULL */
     double *stats;     /* [ST_N] */
     const double *adj; /* a_c(k) [C][nvox] or NULL (full gradient replay) */
+    const double *cres; /* dE/di per pixel [sum W*H] or NULL (classic-estimator gradient replay) */
+    double *gsh;       /* [nvox] receives the shadow-ray terms of the classic-estimator gradient */
     path_rec *rec;     /* non-NULL in full-gradient replay */
 } tctx;
 
@@ -478,6 +497,19 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
                 if (pix >= 0) {
                     double t = exp(-tau_to_point(s, Xn, vn, Pc));
                     c->cimg[pix_offset(s, cam) + pix] += contrib * t / (r2 * omega);
+                }
+            }
+            if (c->cres) {  /* classic-estimator gradient: f_s weighted by its pixel's dE/di */
+                double omega;
+                long pix = project(s, cam, Xn, &omega);
+                if (pix >= 0) {
+                    const double cr = c->cres[pix_offset(s, cam) + pix];
+                    if (cr != 0.0) {
+                        const double f = contrib * exp(-tau_to_point(s, Xn, vn, Pc)) / (r2 * omega);
+                        w += cr * f;
+                        /* d f / d beta_m = -f * (length of the shadow ray in voxel m) */
+                        shadow_scatter(s, Xn, vn, Pc, -cr * f, c->gsh);
+                    }
                 }
             }
         }
@@ -843,27 +875,16 @@ void or_surrogate_grad(const or_scene *s, const double *L_ref, const double *bet
 /* that ends in a collision, S_j = sum_{s>=j} w_s multiplies                                */
 /*   -(length of flight j inside voxel m)  +  [m == k_j] / beta(k_j).                        */
 
-void or_full_grad(const or_scene *s, const or_params *P, const double *meas, const uint8_t *mask, double eta,
-                  int nthreads, double *img, double *grad, double *loss, double *L_out, double *stats,
-                  const uint8_t *skip) {
-    const long nvox = nvox_of(s), nL = (long)s->n_cams * nvox, np = total_pixels(s);
-    double *L = L_out ? L_out : (double *)malloc(sizeof(double) * nL);
-    double *T = (double *)malloc(sizeof(double) * nL);
-    double *b = (double *)malloc(sizeof(double) * nL);
-    double *sv = (double *)malloc(sizeof(double) * nL);
-    double *gT = (double *)malloc(sizeof(double) * nL);
-    double *rr = (double *)malloc(sizeof(double) * np);
-    double st_local[ST_N];
-    or_render(s, P, L, NULL, stats ? stats : st_local, NULL, skip, nthreads);
-    or_transmittance(s, NULL, T);
-    or_images(s, L, T, img);
-    double E = residual(s, img, meas, mask, rr);
-    or_backproject(s, rr, b);
-    for (long i = 0; i < nL; ++i) sv[i] = L[i] * T[i] * b[i];
-    or_los_adjoint(s, sv, gT);
-    double *adj = (double *)malloc(sizeof(double) * nL);
-    for (long i = 0; i < nL; ++i) adj[i] = T[i] * b[i];
-
+/* Score part of the full gradient (Sec. 5 extended: the score of the free-flight density of
+ * Eq. beer-lambert / Eq. MCextinct): every photon is replayed with its Philox key and records its
+ * voxel segments and events; w_s is the event's contribution to <dE/di, i> through the
+ * estimator (adj: voxel estimator, a_c(k) = T_c(k) b_c(k); cres: classic estimator, dE/di of
+ * the pixel each camera sees the event in, plus the shadow-ray terms into the same sums);
+ * S_j = sum_{s >= j} w_s; each flight j scatters -S_j * length into the voxels it crosses and
+ * S_j / beta at its collision voxel. Adds into gout [nvox]. */
+static void replay_score(const or_scene *s, const or_params *P, int nthreads, const double *adj, const double *cres,
+                         const uint8_t *skip, double *gout) {
+    const long nvox = nvox_of(s);
     int nt = nthreads_of(nthreads);
     double *accG = (double *)calloc((size_t)nt * nvox, sizeof(double));
     const long n = (long)P->n_photons;
@@ -881,6 +902,8 @@ void or_full_grad(const or_scene *s, const or_params *P, const double *meas, con
         tctx_init(&c, s, P);
         c.stats = st_dummy;
         c.adj = adj;
+        c.cres = cres;
+        c.gsh = g;
         c.rec = &rec;
         double *S = NULL;
         long capS = 0;
@@ -911,12 +934,37 @@ void or_full_grad(const or_scene *s, const or_params *P, const double *meas, con
         free(S);
         free(rec.seg_k); free(rec.seg_len); free(rec.flight_of_seg); free(rec.ev_k); free(rec.ev_w);
     }
+    for (long k = 0; k < nvox; ++k)
+        for (int t = 0; t < nt; ++t) gout[k] += accG[(size_t)t * nvox + k];
+    free(accG);
+}
+
+void or_full_grad(const or_scene *s, const or_params *P, const double *meas, const uint8_t *mask, double eta,
+                  int nthreads, double *img, double *grad, double *loss, double *L_out, double *stats,
+                  const uint8_t *skip) {
+    const long nvox = nvox_of(s), nL = (long)s->n_cams * nvox, np = total_pixels(s);
+    double *L = L_out ? L_out : (double *)malloc(sizeof(double) * nL);
+    double *T = (double *)malloc(sizeof(double) * nL);
+    double *b = (double *)malloc(sizeof(double) * nL);
+    double *sv = (double *)malloc(sizeof(double) * nL);
+    double *gT = (double *)malloc(sizeof(double) * nL);
+    double *rr = (double *)malloc(sizeof(double) * np);
+    double st_local[ST_N];
+    or_render(s, P, L, NULL, stats ? stats : st_local, NULL, skip, nthreads);
+    or_transmittance(s, NULL, T);
+    or_images(s, L, T, img);
+    double E = residual(s, img, meas, mask, rr);
+    or_backproject(s, rr, b);
+    for (long i = 0; i < nL; ++i) sv[i] = L[i] * T[i] * b[i];
+    or_los_adjoint(s, sv, gT);
+    double *adj = (double *)malloc(sizeof(double) * nL);
+    for (long i = 0; i < nL; ++i) adj[i] = T[i] * b[i];
     for (long k = 0; k < nvox; ++k) {
         double g = 0.0;
-        for (int t = 0; t < nt; ++t) g += accG[(size_t)t * nvox + k];
         for (int c = 0; c < s->n_cams; ++c) g -= gT[(long)c * nvox + k];
         grad[k] = g;
     }
+    replay_score(s, P, nthreads, adj, NULL, skip, grad);
     if (eta != 0.0) {
         double psi;
         double *gr = (double *)malloc(sizeof(double) * nvox);
@@ -926,9 +974,37 @@ void or_full_grad(const or_scene *s, const or_params *P, const double *meas, con
         free(gr);
     }
     *loss = E;
-    free(accG); free(adj);
+    free(adj);
     if (!L_out) free(L);
     free(T); free(b); free(sv); free(gT); free(rr);
+}
+
+/* Full gradient of the loss of the classic local estimate (Eq. fle): images by the forward
+ * classic estimator, r = dE/di, then the score replay with w_s = sum_c r(p_c(s)) f_c(s), where
+ * f_c(s) = albedo I_s P exp(-tau(X_s -> X_c)) / (|X_c - X_s|^2 Omega_p) is the event's
+ * contribution to pixel p_c(s), plus each contribution's own dependence on beta through its
+ * shadow ray, -r f * (length of the shadow ray in voxel m). */
+void or_full_grad_classic(const or_scene *s, const or_params *P, const double *meas, const uint8_t *mask,
+                          double eta, int nthreads, double *img, double *grad, double *loss, double *stats,
+                          const uint8_t *skip) {
+    const long nvox = nvox_of(s), np = total_pixels(s);
+    double *rr = (double *)malloc(sizeof(double) * np);
+    double st_local[ST_N];
+    for (long p = 0; p < np; ++p) img[p] = 0.0;
+    or_render(s, P, NULL, img, stats ? stats : st_local, NULL, skip, nthreads);
+    double E = residual(s, img, meas, mask, rr);
+    for (long k = 0; k < nvox; ++k) grad[k] = 0.0;
+    replay_score(s, P, nthreads, NULL, rr, skip, grad);
+    if (eta != 0.0) {
+        double psi;
+        double *gr = (double *)malloc(sizeof(double) * nvox);
+        or_laplacian(s, s->beta, &psi, gr);
+        E += eta * psi;
+        for (long k = 0; k < nvox; ++k) grad[k] += eta * gr[k];
+        free(gr);
+    }
+    *loss = E;
+    free(rr);
 }
 
 /* ----------------------------------------------------------------------------------------- */

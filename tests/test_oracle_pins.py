@@ -591,6 +591,44 @@ def test_full_gradient_matches_fd_crn(orc):
     assert np.median(np.abs(tg)) > 5.0, tg
 
 
+@pytest.mark.slow
+def test_classic_gradient_along_beta_matches_the_slab_closed_form(orc):
+    """Classic-estimator gradient (path score plus shadow-ray terms), first order in the
+    homogeneous slab with the camera below the medium: with a measured value M far above the
+    images the loss is linear in them, so beta . dE/dbeta / (-2M) estimates
+    sum_p tau d i_p / d tau, which the closed form of the slab gives exactly (derivative in tau
+    of the single-scattering radiance, averaged over each pixel's solid angle)."""
+    beta, albedo, g = 2.5e-3, 0.9, 0.5
+    sc = slab_scene(beta, cam_z=-50.0)
+    p = synth.Params(albedo=albedo, g=g, sun_zenith=math.radians(30), n_photons=1_600_000, seed=23, max_order=1,
+                     rr_threshold=0.0)
+    M = 1e6
+    meas = np.full(sc.n_pix, M)
+    dots = batched(orc, sc, p, 8, lambda q: float(np.dot(sc.beta, orc.full_grad(sc, q, meas, classic=True)["grad"])))
+    est_b = dots / (-2.0 * M)                     # per batch: its share of sum_p tau d i_p / d tau
+    est, sig = est_b.sum(), est_b.std(ddof=1) * math.sqrt(8)
+    sun = np.array([-math.sin(p.sun_zenith), 0.0, -math.cos(p.sun_zenith)])
+    mu0, n, ref = math.cos(p.sun_zenith), 12, 0.0
+    for pix in range(16):
+        i, j = pix % 4, pix // 4
+        acc = wsum = 0.0
+        for a in range(n):
+            for b in range(n):
+                px, py = i + (a + 0.5) / n, j + (b + 0.5) / n
+                d = rg.pixel_dir(sc, 0, px, py)
+                tx = math.tan(0.5 * sc.cam_fov[0])
+                x, y = (2 * px / 4 - 1) * tx, (2 * py / 4 - 1) * tx
+                w = (1 + x * x + y * y) ** -1.5
+                e = 1e-4  # tau d I / d tau of the closed form, by a central difference in beta
+                dI = (_slab_radiance(1.0, albedo, g, beta * (1 + e), 200.0, mu0, sun, d)
+                      - _slab_radiance(1.0, albedo, g, beta * (1 - e), 200.0, mu0, sun, d)) / (2 * e)
+                acc += w * dI
+                wsum += w
+        ref += acc / wsum
+    assert abs(est - ref) < 3.5 * sig + 5e-3 * abs(ref), (est, ref, sig)
+    assert abs(ref) > 10 * sig  # resolved
+
+
 # ------------------------------------------------------------------------------------------
 # sharding and threading: the photon-id split does not change the result
 
