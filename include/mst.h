@@ -163,8 +163,10 @@ int mst_render(mst_grid *g, const float *beta_dev, const mst_params *p, double *
  * Eq. MCextinct) over paths replayed from their Philox keys. W = sum_s w_s per photon and the
  * w_s come from the events the forward render stored (44 B per event, within the handle's
  * budget, see mst_set_replay_memory), or, when they do not fit, from a first replay of every
- * path; a last replay scatters the score. Results agree either way. Requires the voxel
- * estimator. */
+ * path; a last replay scatters the score. Results agree either way. With MST_EST_CLASSIC the
+ * images are Eq. fle's, w_s weights each camera's classic contribution by its pixel's dE/di,
+ * and each contribution's shadow ray adds its own term (no events are stored). The surrogate
+ * gradient needs the voxel estimator. */
 int mst_render_grad(mst_grid *g, const float *beta_dev, const mst_params *p, const double *images_meas_dev,
                     const uint8_t *mask_dev, double *images_dev, double *grad_dev, double *loss_dev, void *stream);
 

@@ -172,9 +172,13 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
     const int nl = (int)((n + span - 1) / span);
     MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * nl * (replay ? 2 : 1), st));
     const int est = replay ? 0 : p->estimator;
+    // replay modes: 3 / 2 for the voxel estimator, 5 / 6 for the classic one (w_s from its images)
+    const bool classic_adj = replay && p->estimator == MST_EST_CLASSIC;
+    const int m_p1 = classic_adj ? 5 : 3, m_p2 = classic_adj ? 6 : 2;
+    if (classic_adj) a.cres = g->resid;
     const int b_fwd = g->sm_count * transport_blocks_per_sm(p->grid_dtype, est);
-    const int b_p1 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, 3);
-    const int b_p2 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, 2);
+    const int b_p1 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, m_p1);
+    const int b_p2 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, m_p2);
     if (replay) set_fold(a, (uint64_t)g->geo.nvox);
     else if (est == MST_EST_VOXEL) set_fold(a, (uint64_t)g->geo.nvox * g->cp);
     if (store_events) {
@@ -192,7 +196,7 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
             a.ticket = g->tickets + 2 * l;
             {
                 Phase ph(g, MST_PH_REPLAY, st);
-                MST_CK(launch_transport(g, a, p->grid_dtype, 3, b_p1, st));
+                MST_CK(launch_transport(g, a, p->grid_dtype, m_p1, b_p1, st));
             }
             {
                 Phase ph(g, MST_PH_REPLAY_LIST, st);
@@ -201,7 +205,7 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
             a.ticket = g->tickets + 2 * l + 1;
             {
                 Phase ph(g, MST_PH_REPLAY2, st);
-                MST_CK(launch_transport(g, a, p->grid_dtype, 2, b_p2, st));
+                MST_CK(launch_transport(g, a, p->grid_dtype, m_p2, b_p2, st));
             }
             Phase ph(g, MST_PH_FOLD, st);
             MST_CK(launch_fold_grad(g, st));
@@ -371,7 +375,7 @@ double radical_inverse(int base, int i) {
 
 void free_all(mst_grid* g) {
     void* ptrs[] = {g->ext, g->Lacc, g->L64, g->T, g->R, g->bacc, g->gT, g->adj, g->gacc, g->g64,
-                    g->resid, g->lap, g->omega, g->Qw, g->stats, g->tickets, g->wbuf, g->nevbuf, g->plist, g->score_cnt};
+                    g->resid, g->cimg, g->lap, g->omega, g->Qw, g->stats, g->tickets, g->wbuf, g->nevbuf, g->plist, g->score_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     cudaFree(g->evrec);
@@ -525,6 +529,7 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
         {(void**)&g->score_cnt, (2 * kScoreBins + 1) * 4},
         {(void**)&g->g64, nvox * 8},
         {(void**)&g->resid, (size_t)off * 8},
+        {(void**)&g->cimg, (size_t)off * 8},
         {(void**)&g->lap, nvox * 8},
         {(void**)&g->omega, (size_t)off * 4},
         {(void**)&g->stats, MST_NSTATS * 8 + 64},
@@ -652,7 +657,8 @@ int check_render_grad(mst_grid* g, const float* beta, const mst_params* p, const
     if (!beta || !meas || !grad) return fail(g, MST_ERR_INVALID_ARG, "beta, images_meas and grad are required");
     const int rc = check_params(g, p, true);
     if (rc) return rc;
-    if (p->estimator != MST_EST_VOXEL) return fail(g, MST_ERR_UNSUPPORTED, "gradients need the voxel estimator");
+    if (p->estimator != MST_EST_VOXEL && p->grad_mode != MST_GRAD_FULL)
+        return fail(g, MST_ERR_UNSUPPORTED, "the surrogate gradient needs the voxel estimator");
     return MST_OK;
 }
 
@@ -667,6 +673,32 @@ int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const 
         MST_CK(launch_stage(g, beta, p->grid_dtype, st));
     }
     MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
+    if (p->estimator == MST_EST_CLASSIC) {  // Eq. fle images, their loss, and the score replay
+        MST_CK(cudaMemsetAsync(g->cimg, 0, sizeof(double) * g->total_pix, st));
+        rc = run_photons(g, p, false, g->cimg, st);
+        if (rc) return rc;
+        MST_CK(cudaMemsetAsync(lossp, 0, sizeof(double), st));
+        {
+            Phase ph(g, MST_PH_IMAGES, st);
+            MST_CK(launch_classic_residual(g, g->cimg, meas, mask, g->resid, lossp, st));
+        }
+        if (images)
+            MST_CK(cudaMemcpyAsync(images, g->cimg, sizeof(double) * g->total_pix, cudaMemcpyDeviceToDevice, st));
+        rc = ensure_replay(g, kReplayChunk);
+        if (rc) return rc;
+        MST_CK(cudaMemsetAsync(g->g64, 0, sizeof(double) * g->geo.nvox, st));
+        rc = run_photons(g, p, true, nullptr, st);
+        if (rc) return rc;
+        {
+            Phase ph(g, MST_PH_COMBINE, st);
+            MST_CK(launch_combine_full(g, nullptr, g->g64, grad, st));
+        }
+        if (p->reg_eta != 0.0) {
+            Phase ph(g, MST_PH_COMBINE, st);
+            MST_CK(launch_regularizer(g, beta, p->reg_eta, g->lap, g->stats + MST_NSTATS + 1, lossp, grad, st));
+        }
+        return MST_OK;
+    }
     MST_CK(cudaMemsetAsync(g->L64, 0, sizeof(double) * nL, st));
     // full gradient: the forward stores its events when they can be held (W without pass 1)
     bool stored = false;
@@ -1052,7 +1084,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
                 b->err = g->err;
                 return rc;
             }
-            for (int mode = 0; mode < 5; ++mode) transport_blocks_per_sm(params[i].grid_dtype, mode);
+            for (int mode = 0; mode < 7; ++mode) transport_blocks_per_sm(params[i].grid_dtype, mode);
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             b->err = "stream error before capture";

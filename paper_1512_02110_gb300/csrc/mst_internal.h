@@ -54,6 +54,7 @@ struct TransportArgs {
     float* Lacc;               // [nvox][cp] FP32 accumulator (voxel estimator)
     double* cimg;              // classic images (classic estimator)
     const float* omega;        // [total pix] pixel solid angles (classic estimator)
+    const double* cres;        // [total pix] dE/di of the classic images (classic-estimator gradient)
     const float* adj;          // [nvox][cp] a_c(k) = T_c(k) b_c(k) (replay)
     float* gacc;               // [nvox] FP32 gradient accumulator (replay)
     double* wbuf;              // [photons of the chunk] W per photon (replay pass 1, stored-event adjoint)
@@ -117,6 +118,7 @@ struct mst_grid {
     unsigned int* score_cnt = nullptr;  // [2 kScoreBins + 1] list bin counts, bin fill, list length
     double* g64 = nullptr;        // [nvox]
     double* resid = nullptr;      // [total_pix] 2 M (i - i_meas)
+    double* cimg = nullptr;       // [total_pix] classic images of a gradient call
     double* lap = nullptr;        // [nvox] W^T W Lap beta
     double* reg_wz = nullptr;     // [nz] altitude weights W of the regulariser, NULL: W = I
     float* omega = nullptr;       // [total_pix]
@@ -145,7 +147,8 @@ namespace mst {
 // launchers (all enqueue on `st`; return cudaGetLastError())
 cudaError_t launch_stage(const mst_grid* g, const float* beta, int dtype, cudaStream_t st);
 // transport kernel modes: 0 forward voxel LE, 1 forward classic LE, 3 replay pass 1, 2 replay pass 2,
-// 4 replay pass 2 reading w_s from the stored events
+// 4 replay pass 2 reading w_s from the stored events, 5 / 6 passes 1 / 2 of the classic-estimator
+// gradient
 cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int mode, int blocks,
                              cudaStream_t st);
 cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st);
@@ -171,6 +174,8 @@ cudaError_t launch_combine_surrogate(const mst_grid* g, const double* Lsrc, cons
                                      const float* beta, const float* T, const float* bacc, const float* gT,
                                      const float* Qw, double* grad, cudaStream_t st);
 cudaError_t launch_combine_full(const mst_grid* g, const float* gT, const double* gL, double* grad, cudaStream_t st);
+cudaError_t launch_classic_residual(const mst_grid* g, const double* img, const double* meas, const uint8_t* mask,
+                                    double* resid, double* loss, cudaStream_t st);
 cudaError_t launch_regularizer(const mst_grid* g, const float* beta, double eta, double* lap, double* psi,
                                double* loss, double* grad, cudaStream_t st);
 int transport_blocks_per_sm(int dtype, int mode);

@@ -199,9 +199,23 @@ __global__ void k_combine_full(const float* __restrict__ gT, const double* __res
                                int nvox, int C) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nvox; k += gridDim.x * blockDim.x) {
         double acc = gL[k];
-        for (int c = 0; c < C; ++c) acc -= (double)gT[(size_t)c * nvox + k];
+        if (gT)  // voxel estimator: the LOS term; the classic estimator has none
+            for (int c = 0; c < C; ++c) acc -= (double)gT[(size_t)c * nvox + k];
         grad[k] = acc;
     }
+}
+
+// Loss of the classic images (Eq. Cost): r = M (i - i_meas), E += sum r^2, resid = dE/di = 2 r.
+__global__ void k_classic_resid(const double* __restrict__ img, const double* __restrict__ meas,
+                                const uint8_t* __restrict__ mask, double* __restrict__ resid, double* loss, int npix) {
+    double e = 0.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        const double r = (mask && !mask[p]) ? 0.0 : img[p] - meas[p];
+        resid[p] = 2.0 * r;
+        e += r * r;
+    }
+    e = warp_sum(e);
+    if ((threadIdx.x & 31u) == 0u && e != 0.0) atomicAdd(loss, e);
 }
 
 // Laplacian of a dense field: out(k) = sum over in-grid 6-neighbours n of (x(n) - x(k))
@@ -313,6 +327,12 @@ cudaError_t launch_combine_surrogate(const mst_grid* g, const double* Lsrc, cons
 
 cudaError_t launch_combine_full(const mst_grid* g, const float* gT, const double* gL, double* grad, cudaStream_t st) {
     k_combine_full<<<nblocks(g->geo.nvox, kTB, 4096), kTB, 0, st>>>(gT, gL, grad, g->geo.nvox, g->n_cams);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classic_residual(const mst_grid* g, const double* img, const double* meas, const uint8_t* mask,
+                                    double* resid, double* loss, cudaStream_t st) {
+    k_classic_resid<<<nblocks(g->total_pix, kTB, 4096), kTB, 0, st>>>(img, meas, mask, resid, loss, g->total_pix);
     return cudaGetLastError();
 }
 

@@ -199,8 +199,14 @@ __device__ __forceinline__ float le_adjoint(const TransportArgs& A, const Photon
 }
 
 // Eq. fle: pixel p(X_s) of camera c += albedo I_s P t_{s->c} / (|V|^2 Omega_p)
-template <int DT>
-__device__ __forceinline__ void le_classic(const TransportArgs& A, const Photon& ph, float w) {
+// Eq. fle: for each camera whose image holds the event, the pixel p gets
+// f = albedo I P(mu) exp(-tau(X_s -> X_c)) / (|X_c - X_s|^2 Omega_p). OP 0 adds f to the
+// classic image; OP 1 returns w_s = sum_c cres[p] f (the event's share of <dE/di, i>, for the
+// classic-estimator gradient); OP 2 also scatters the shadow-ray terms d f / d beta_m =
+// -f * (length of the ray in voxel m), weighted by cres[p], into the gradient tile.
+template <int DT, int OP>
+__device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon& ph, float w, float* gacc) {
+    float acc = 0.f;
     for (int c = 0; c < A.cams.n; ++c) {
         const Cam& cm = A.cams.c[c];
         // point relative to the camera
@@ -216,14 +222,29 @@ __device__ __forceinline__ void le_classic(const TransportArgs& A, const Photon&
         const int gp = cm.pix_off + (int)py * cm.w + (int)px;
         const float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
         if (!(r2 > 0.f)) continue;
+        float cr = 0.f;
+        if (OP > 0) {
+            cr = (float)A.cres[gp];
+            if (cr == 0.f) continue;
+        }
         const float mu = -(ph.d.x * v.x + ph.d.y * v.y + ph.d.z * v.z) * rsqrtf(r2);
         float tau = 0.f;
         unsigned long long ns = 0;
         walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p,
                        [&](const Walk& wk, float len) { tau += BetaFetch<DT>::get(A.beta, wk.lin) * len; }, ns);
         const float val = w * hg_phase(A.hg, mu) * expf(-tau) / (r2 * A.omega[gp]);
-        atomicAdd(A.cimg + gp, (double)val);
+        if (OP == 0) {
+            atomicAdd(A.cimg + gp, (double)val);
+        } else {
+            acc += cr * val;
+            if (OP == 2) {
+                const float sw = -cr * val;
+                walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p,
+                               [&](const Walk& wk, float len) { atomicAdd(gacc + wk.lin, sw * len); }, ns);
+            }
+        }
     }
+    return acc;
 }
 
 // step v (albedo weighting, Russian roulette) and step vi (HG direction, next free path).
@@ -304,8 +325,9 @@ constexpr int kMinBlocksPass1 = 3;
 constexpr int kMinBlocksPass2 = 3;
 
 // kernel modes
-// kPass2W: replay pass 2 reading w_s from the stored events instead of recomputing them
-constexpr int kFwdVoxel = 0, kFwdClassic = 1, kPass2 = 2, kPass1 = 3, kPass2W = 4;
+// kPass2W: replay pass 2 reading w_s from the stored events instead of recomputing them;
+// kPass1C, kPass2C: passes 1 and 2 of the classic-estimator gradient
+constexpr int kFwdVoxel = 0, kFwdClassic = 1, kPass2 = 2, kPass1 = 3, kPass2W = 4, kPass1C = 5, kPass2C = 6;
 
 template <int NW>
 struct Stack {
@@ -378,7 +400,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // 32-bit atomics, so nothing added is lost; each bin's FP32 partial covers at most one sweep.
 template <int MODE>
 __device__ __forceinline__ void fold_slice(const TransportArgs& A, uint32_t batch, unsigned lane) {
-    if constexpr (MODE == kFwdVoxel || MODE == kPass2 || MODE == kPass2W) {
+    if constexpr (MODE == kFwdVoxel || MODE == kPass2 || MODE == kPass2W || MODE == kPass2C) {
         if (A.fold_bins == 0u) return;
         const uint64_t i0 = (uint64_t)(batch % A.fold_nslices) * A.fold_slice;
         const uint64_t i1 = min(i0 + A.fold_slice, A.fold_bins);
@@ -475,9 +497,13 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
 template <int DT, int MODE>
 __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMinBlocksPass2
                                                        : (MODE == kPass1 ? kMinBlocksPass1
-                                                          : (MODE == kFwdClassic ? kMinBlocksClassic : kMinBlocksForward)))
+                                                          : ((MODE == kFwdClassic || MODE == kPass1C || MODE == kPass2C)
+                                                                 ? kMinBlocksClassic
+                                                                 : kMinBlocksForward)))
     k_transport(const TransportArgs A) {
-    constexpr bool PASS1 = MODE == kPass1, PASS2 = MODE == kPass2 || MODE == kPass2W;
+    constexpr bool PASS1 = MODE == kPass1 || MODE == kPass1C;
+    constexpr bool PASS2 = MODE == kPass2 || MODE == kPass2W || MODE == kPass2C;
+    constexpr bool CLASSIC_ADJ = MODE == kPass1C || MODE == kPass2C;
     constexpr bool REPLAY = PASS1 || PASS2;
     constexpr int kStepsPerTrip = PASS2 ? kStepsPass2 : (PASS1 ? kStepsPass1 : kStepsForward);
     constexpr int NW = Rec<REPLAY>::NW;
@@ -608,11 +634,14 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                     e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
                     if (MODE == kFwdVoxel && A.ev_cap && ev_base + lane < A.ev_cap) store_event(A, ev_base + lane, e, wgt);
                     if (MODE == 0) le_voxel(A, e, wgt, k);
-                    else le_classic<DT>(A, e, wgt);
+                    else le_classic<DT, 0>(A, e, wgt, nullptr);
                     term = after_event(A, e, t);
                     if (term) finish_photon(A, e, term);
                 } else {
-                    const float we = MODE == kPass2W ? A.wseq[e.hash + e.s - 1u] : le_adjoint(A, e, wgt, k);
+                    float we;
+                    if constexpr (MODE == kPass2W) we = A.wseq[e.hash + e.s - 1u];
+                    else if constexpr (CLASSIC_ADJ) we = le_classic<DT, PASS2 ? 2 : 1>(A, e, wgt, A.gacc);
+                    else we = le_adjoint(A, e, wgt, k);
                     if (PASS1) {
                         eacc += (double)we;
                         term = after_event(A, e, t);
@@ -886,6 +915,8 @@ int occupancy_mode(int mode) {
         case kFwdClassic: return occupancy(k_transport<DT, kFwdClassic>, smem_bytes<false>());
         case kPass2: return occupancy(k_transport<DT, kPass2>, smem_bytes<true>());
         case kPass2W: return occupancy(k_transport<DT, kPass2W>, smem_bytes<true>());
+        case kPass1C: return occupancy(k_transport<DT, kPass1C>, smem_bytes<true>());
+        case kPass2C: return occupancy(k_transport<DT, kPass2C>, smem_bytes<true>());
         default: return occupancy(k_transport<DT, kPass1>, smem_bytes<true>());
     }
 }
@@ -897,6 +928,8 @@ cudaError_t launch_dt(const TransportArgs& a, int mode, int blocks, cudaStream_t
         case kFwdClassic: return launch_mode<DT, kFwdClassic>(a, blocks, st);
         case kPass2: return launch_mode<DT, kPass2>(a, blocks, st);
         case kPass2W: return launch_mode<DT, kPass2W>(a, blocks, st);
+        case kPass1C: return launch_mode<DT, kPass1C>(a, blocks, st);
+        case kPass2C: return launch_mode<DT, kPass2C>(a, blocks, st);
         default: return launch_mode<DT, kPass1>(a, blocks, st);
     }
 }
@@ -904,7 +937,7 @@ cudaError_t launch_dt(const TransportArgs& a, int mode, int blocks, cudaStream_t
 }  // namespace
 
 int transport_blocks_per_sm(int dtype, int mode) {
-    static int cache[3][5] = {{0}};
+    static int cache[3][7] = {{0}};
     if (cache[dtype][mode]) return cache[dtype][mode];
     const int n = dtype == 0 ? occupancy_mode<0>(mode) : (dtype == 1 ? occupancy_mode<1>(mode) : occupancy_mode<2>(mode));
     cache[dtype][mode] = n;

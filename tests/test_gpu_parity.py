@@ -306,6 +306,27 @@ def test_full_gradient(m, torch):
     assert ei < 1e-4 and el < 1e-4 and eg < 1e-3
 
 
+def test_full_gradient_classic_estimator(m, torch):
+    """Full gradient of the classic local estimate (path score plus shadow-ray terms) against
+    the oracle's, photons that FP32 and FP64 send apart excluded from both."""
+    sc, p, meas, mask = _grad_case()
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    skip, _, _ = _diverged(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render_grad(beta, m.make_params(p, grad_mode="full", estimator="classic", reg_eta=0.05),
+                           dev(meas, np.float64), dev(mask, np.uint8))
+    st = grid.stats()
+    grid.set_debug(None, None)
+    ref = oracle.full_grad(sc, p, meas, mask, eta=0.05, skip=skip, classic=True)
+    ei = max_rel(out["images"].cpu().numpy(), ref["images"], 1e-3 * np.abs(ref["images"]).max())
+    el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
+    eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    record("full_gradient_classic", diverged_frac=skip.mean(), images_max_rel=ei, loss_rel=el, grad_rel_l2=eg)
+    assert st["events_stored"] == 0 and st["replay_segments"] > 0
+    assert ei < 2e-4 and el < 1e-4 and eg < 1e-3, (ei, el, eg)
+
+
 @pytest.mark.parametrize("budget", ["replay", "overflow"])
 def test_full_gradient_stored_events_match_replay(m, torch, budget):
     """W from the forward's stored events (the default) against W from replay pass 1: same
