@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
     ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
-    ap.add_argument("--study", default=None, choices=["precision", "recon", "bmc"],
+    ap.add_argument("--study", default=None, choices=["precision", "recon", "bmc", "classic"],
                     help="FP16/BF16 brick forms against FP32 at equal photon count (prints one JSON line)")
     return ap.parse_args()
 
@@ -446,6 +446,38 @@ def run_batch(args):
     return 0
 
 
+def run_classic_study(args):
+    """Forward + full gradient with the classic local estimator (Eq. fle: shadow ray per camera
+    and event, score replay plus shadow-ray terms) against the voxelised estimator, cumulus64 at
+    1e7 photons. Prints one JSON line with the times and stage split."""
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(0)
+    n = int(1e7)
+    sc, p = synth.cfg_cumulus64(n)
+    grid = m.Grid.from_scene(sc)
+    beta = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
+    meas = grid.render(beta, m.make_params(p, seed=4))["images"]
+    out = {"study": "classic", "workload": "cumulus64, 9 in-situ 128x128 cameras", "photons": n}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for est in ("voxel", "classic"):
+        prm = m.make_params(p, grad_mode="full", estimator=est)
+        grid.render_grad(beta, prm, meas, images=False)  # warm-up
+        grid.set_profiling(True)
+        a.record()
+        grid.render_grad(beta, prm, meas, images=False)
+        b.record()
+        torch.cuda.synchronize()
+        st = grid.stats()
+        out[est] = {"ms": a.elapsed_time(b), "phase_ms": {k: v[0] for k, v in grid.phase_times().items() if v[1]},
+                    "segments": st["segments"], "replay_segments": st["replay_segments"], "events": st["events"]}
+        grid.set_profiling(False)
+    print(json.dumps(out))
+    return 0
+
+
 def run_bmc_study(args):
     """Backward MC (Eq. ble) on the benchmark scene: throughput (paths and voxel segments per
     second), the pixels' relative standard errors, and the images against the forward render
@@ -590,6 +622,8 @@ def main():
         return run_recon_study(args)
     if args.study == "bmc":
         return run_bmc_study(args)
+    if args.study == "classic":
+        return run_classic_study(args)
     if args.workload == "batch16":
         return run_batch(args)
     return run_ours(args)
