@@ -287,8 +287,10 @@ def run_ours(args):
         "k_transport": (phase_acc["transport"], 15 * seg1 + ops_ev * ev1,
                         4 * seg1 + 8 * C * ev1 + (36 * stored + 4 * st["traced"] if stored > 0 else 0)),
         "k_replay_pass1": (phase_acc["replay"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 4 * C * ev1),
-        "k_replay_pass2": (phase_acc["replay2"], 15 * seg2 + ops_ev * ev2 + 2 * st["replay_scatters"],
-                           4 * seg2 + 4 * C * ev2 + 8 * st["replay_scatters"]),
+        # with stored events pass 2 reads each w_s (4 B) instead of summing over the cameras
+        "k_replay_pass2": (phase_acc["replay2"], 15 * seg2 + (35 if stored > 0 else ops_ev) * ev2
+                           + 2 * st["replay_scatters"],
+                           4 * seg2 + (4 if stored > 0 else 4 * C) * ev2 + 8 * st["replay_scatters"]),
         "k_event_adjoint": (phase_acc.get("event_adjoint", [0.0, 0]), 27 * C * stored,
                             (36 + 4 * C + 8) * stored),
     }
