@@ -38,7 +38,7 @@ class _Scene(ctypes.Structure):
                 ("h", ctypes.c_double * 3), ("o", ctypes.c_double * 3),
                 ("beta", ctypes.c_void_p), ("cam_pos", ctypes.c_void_p), ("cam_rot", ctypes.c_void_p),
                 ("cam_w", ctypes.c_void_p), ("cam_h", ctypes.c_void_p), ("cam_fov", ctypes.c_void_p),
-                ("reg_wz", ctypes.c_void_p)]
+                ("reg_wz", ctypes.c_void_p), ("beta_air", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -47,7 +47,7 @@ class _Params(ctypes.Structure):
                 ("rr_threshold", ctypes.c_double), ("rr_survival", ctypes.c_double),
                 ("n_photons", ctypes.c_uint64), ("photon_offset", ctypes.c_uint64),
                 ("n_photons_total", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("max_order", ctypes.c_int), ("max_events", ctypes.c_int)]
+                ("max_order", ctypes.c_int), ("max_events", ctypes.c_int), ("albedo_air", ctypes.c_double)]
 
 
 _lib = None
@@ -66,6 +66,10 @@ def lib():
         L.or_hg_phase.restype = ctypes.c_double
         L.or_hg_sample.argtypes = [ctypes.c_double, ctypes.c_double]
         L.or_hg_sample.restype = ctypes.c_double
+        L.or_rayleigh_phase.argtypes = [ctypes.c_double]
+        L.or_rayleigh_phase.restype = ctypes.c_double
+        L.or_rayleigh_sample.argtypes = [ctypes.c_double]
+        L.or_rayleigh_sample.restype = ctypes.c_double
         L.or_rotate.argtypes = [P, ctypes.c_double, ctypes.c_double, P]
         L.or_radical_inverse.argtypes = [ctypes.c_int, ctypes.c_int]
         L.or_radical_inverse.restype = ctypes.c_double
@@ -106,6 +110,12 @@ class _Bound:
         s.o = (ctypes.c_double * 3)(*scene.origin)
         s.beta, s.cam_pos, s.cam_rot = _ptr(self.beta), _ptr(self.pos), _ptr(self.rot)
         s.cam_w, s.cam_h, s.cam_fov = _ptr(self.w), _ptr(self.h), _ptr(self.fov)
+        air = getattr(scene, "beta_air", None)
+        if air is not None:  # two species: the oracle's beta is the total extinction
+            self.air = np.ascontiguousarray(air, dtype=np.float64)
+            self.beta = np.ascontiguousarray(self.beta + self.air)
+            s.beta = _ptr(self.beta)
+            s.beta_air = _ptr(self.air)
         wz = getattr(scene, "reg_wz", None)
         self.wz = None if wz is None else np.ascontiguousarray(wz, dtype=np.float64)
         s.reg_wz = None if self.wz is None else _ptr(self.wz)
@@ -123,6 +133,7 @@ def _params(p) -> _Params:
     q.rr_threshold, q.rr_survival = p.rr_threshold, p.rr_survival
     q.n_photons, q.photon_offset, q.n_photons_total, q.seed = p.n_photons, p.photon_offset, p.n_photons_total, p.seed
     q.max_order, q.max_events = p.max_order, p.max_events
+    q.albedo_air = getattr(p, "albedo_air", 1.0)
     return q
 
 
@@ -148,6 +159,14 @@ def hg_phase(g: float, mu: float) -> float:
 
 def hg_sample(g: float, u: float) -> float:
     return lib().or_hg_sample(g, u)
+
+
+def rayleigh_phase(mu: float) -> float:
+    return lib().or_rayleigh_phase(mu)
+
+
+def rayleigh_sample(u: float) -> float:
+    return lib().or_rayleigh_sample(u)
 
 
 def rotate(d, ct: float, phi: float):

@@ -59,6 +59,8 @@ typedef struct {
     const int *cam_h;        /* [C] */
     const double *cam_fov;   /* [C] horizontal field of view, rad */
     const double *reg_wz;    /* [nz] altitude weights W of the regulariser (Sec. 6), NULL: W = I */
+    const double *beta_air;  /* [nvox] air (Rayleigh) extinction, or NULL; beta is then the total */
+                             /* extinction beta_air + beta_aerosol (Sec. 2, two species)          */
 } or_scene;
 
 typedef struct {
@@ -66,6 +68,7 @@ typedef struct {
     double rr_threshold, rr_survival;
     uint64_t n_photons, photon_offset, n_photons_total, seed;
     int max_order, max_events;
+    double albedo_air;       /* single-scattering albedo of air (two species; ~1 in the visible) */
 } or_params;
 
 enum {
@@ -136,6 +139,24 @@ double or_hg_sample(double g, double u) {
     if (c < -1.0) c = -1.0;
     return c;
 }
+
+/* Eq. Pray: Rayleigh phase function of air molecules */
+double or_rayleigh_phase(double mu) { return 3.0 / (16.0 * OR_PI) * (1.0 + mu * mu); }
+
+/* Eq. thetaREY: inverse CDF of Eq. Pray, cos = gamma^(1/3) - gamma^(-1/3) with
+ * gamma = 4u - 2 + sqrt((4u - 2)^2 + 1) (Cardano's root of mu^3 + 3 mu + 4 - 8u = 0) */
+double or_rayleigh_sample(double u) {
+    const double q = 4.0 * u - 2.0;
+    const double gam = q + sqrt(q * q + 1.0);
+    double c = cbrt(gam) - 1.0 / cbrt(gam);
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    return c;
+}
+
+/* Step iv with two species: the event's particle is air with probability beta_air / beta in
+ * its voxel (Sec. 2.1.2), drawn from Philox stream word 0xFFFFFFFF of the event. */
+#define TYPE_STREAM 0xFFFFFFFFu
 
 /* New direction at polar cosine ct and azimuth phi about d. The transverse frame is
  * e2 = normalize(a x d), e1 = e2 x d with reference axis a = z, or a = x when |d_z| >= 0.9. */
@@ -372,6 +393,7 @@ typedef struct {
     long n_seg, cap_seg;
     long *ev_k;     /* event voxel, 1-based event index s -> ev_k[s-1] */
     double *ev_w;   /* w_s = sum_c a_c(k_s) * albedo * I_s * P_c(s) */
+    int *ev_air;    /* event s scattered off air (two species) */
     long n_ev, cap_ev;
 } path_rec;
 
@@ -403,15 +425,17 @@ static void rec_seg(path_rec *r, long k, double len, int flight) {
     r->n_seg++;
 }
 
-static void rec_event(path_rec *r, long k, double w) {
+static void rec_event(path_rec *r, long k, double w, int air) {
     if (!r) return;
     if (r->n_ev == r->cap_ev) {
         r->cap_ev = r->cap_ev ? 2 * r->cap_ev : 64;
         r->ev_k = (long *)realloc(r->ev_k, r->cap_ev * sizeof(long));
         r->ev_w = (double *)realloc(r->ev_w, r->cap_ev * sizeof(double));
+        r->ev_air = (int *)realloc(r->ev_air, r->cap_ev * sizeof(int));
     }
     r->ev_k[r->n_ev] = k;
     r->ev_w[r->n_ev] = w;
+    r->ev_air[r->n_ev] = air;
     r->n_ev++;
 }
 
@@ -465,7 +489,6 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
     uint32_t hash = FNV_OFFSET;
     uint32_t s_ev = 0;
     int term;
-    const double alb = P->albedo;
     for (;;) {
         double Xn[3];
         int vn[3], face = -1;
@@ -479,6 +502,14 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
         long k = lin(s, vn);
         hash = (hash ^ (uint32_t)k) * FNV_PRIME;
         c->stats[ST_EVENTS] += 1.0;
+        /* step iv: the particle (one species unless the scene has air) and its albedo */
+        int air = 0;
+        if (s->beta_air) {
+            double ut[4];
+            draws4(P->seed, p, s_ev, TYPE_STREAM, ut);
+            air = ut[0] * s->beta[k] < s->beta_air[k];
+        }
+        const double alb = air ? P->albedo_air : P->albedo;
         /* local estimates toward every camera (Eq. Lcupdate; Eq. fle) */
         double w = 0.0;
         for (int cam = 0; cam < s->n_cams; ++cam) {
@@ -488,7 +519,7 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
             if (r2 == 0.0) continue;
             double rr = sqrt(r2);
             double mu = (d[0] * vv[0] + d[1] * vv[1] + d[2] * vv[2]) / rr;
-            double contrib = alb * I * or_hg_phase(P->g, mu);
+            double contrib = alb * I * (air ? or_rayleigh_phase(mu) : or_hg_phase(P->g, mu));
             if (c->L) c->L[(long)cam * c->nvox + k] += contrib;
             if (c->adj) w += c->adj[(long)cam * c->nvox + k] * contrib;
             if (c->cimg) {
@@ -513,7 +544,7 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
                 }
             }
         }
-        rec_event(c->rec, k, w);
+        rec_event(c->rec, k, w, air);
         /* step v: albedo weighting and Russian roulette */
         c->stats[ST_ABSORBED] += (1.0 - alb) * I;
         I *= alb;
@@ -540,8 +571,8 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
                 break;
             }
         }
-        /* step vi: new direction by HG inverse transform, uniform azimuth */
-        double ct = or_hg_sample(P->g, u[0]);
+        /* step vi: new direction by the particle's inverse transform, uniform azimuth */
+        double ct = air ? or_rayleigh_sample(u[0]) : or_hg_sample(P->g, u[0]);
         double nd[3];
         or_rotate(d, ct, 2.0 * OR_PI * u[1], nd);
         for (int q = 0; q < 3; ++q) { X[q] = Xn[q]; d[q] = nd[q]; v[q] = vn[q]; }
@@ -803,6 +834,19 @@ void or_laplacian(const or_scene *s, const double *beta, double *psi, double *gr
     free(lb);
 }
 
+/* the regulariser acts on the variable field: beta_aerosol = beta - beta_air */
+static void laplacian_of_aerosol(const or_scene *s, double *psi, double *grad) {
+    if (!s->beta_air) {
+        or_laplacian(s, s->beta, psi, grad);
+        return;
+    }
+    const long nvox = nvox_of(s);
+    double *a = (double *)malloc(sizeof(double) * nvox);
+    for (long k = 0; k < nvox; ++k) a[k] = s->beta[k] - s->beta_air[k];
+    or_laplacian(s, a, psi, grad);
+    free(a);
+}
+
 /* ----------------------------------------------------------------------------------------- */
 /* loss (Eq. Cost, one channel) and surrogate gradient with j fixed (Eq. Jaco1-DivTc)        */
 
@@ -860,7 +904,7 @@ void or_surrogate_grad(const or_scene *s, const double *L_ref, const double *bet
     if (eta != 0.0) {
         double psi;
         double *gr = (double *)malloc(sizeof(double) * nvox);
-        or_laplacian(s, s->beta, &psi, gr);
+        laplacian_of_aerosol(s, &psi, gr);
         E += eta * psi;
         for (long k = 0; k < nvox; ++k) grad[k] += eta * gr[k];
         free(gr);
@@ -927,12 +971,17 @@ static void replay_score(const or_scene *s, const or_params *P, int nthreads, co
                 g[rec.seg_k[q]] -= S[f - 1] * rec.seg_len[q];
             }
             for (long e = 0; e < rec.n_ev; ++e) {
+                /* collision density of the event's particle: beta_aerosol(k) for an aerosol
+                 * event (score 1 / beta_aerosol), beta_air(k) for an air event (no beta_aerosol
+                 * dependence) */
                 long k = rec.ev_k[e];
-                g[k] += S[e] / s->beta[k];
+                if (rec.ev_air[e]) continue;
+                g[k] += S[e] / (s->beta[k] - (s->beta_air ? s->beta_air[k] : 0.0));
             }
         }
         free(S);
         free(rec.seg_k); free(rec.seg_len); free(rec.flight_of_seg); free(rec.ev_k); free(rec.ev_w);
+        free(rec.ev_air);
     }
     for (long k = 0; k < nvox; ++k)
         for (int t = 0; t < nt; ++t) gout[k] += accG[(size_t)t * nvox + k];
@@ -968,7 +1017,7 @@ void or_full_grad(const or_scene *s, const or_params *P, const double *meas, con
     if (eta != 0.0) {
         double psi;
         double *gr = (double *)malloc(sizeof(double) * nvox);
-        or_laplacian(s, s->beta, &psi, gr);
+        laplacian_of_aerosol(s, &psi, gr);
         E += eta * psi;
         for (long k = 0; k < nvox; ++k) grad[k] += eta * gr[k];
         free(gr);
@@ -998,7 +1047,7 @@ void or_full_grad_classic(const or_scene *s, const or_params *P, const double *m
     if (eta != 0.0) {
         double psi;
         double *gr = (double *)malloc(sizeof(double) * nvox);
-        or_laplacian(s, s->beta, &psi, gr);
+        laplacian_of_aerosol(s, &psi, gr);
         E += eta * psi;
         for (long k = 0; k < nvox; ++k) grad[k] += eta * gr[k];
         free(gr);

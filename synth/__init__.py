@@ -43,6 +43,7 @@ class Scene:
     cam_fov: np.ndarray     # [C] float64, horizontal field of view, radians
     n_rays: int = 10        # sub-pixel rays per pixel (N_rays, Sec. 3.1)
     reg_wz: Optional[np.ndarray] = None  # [nz] altitude weights of the regulariser, None: all 1
+    beta_air: Optional[np.ndarray] = None  # [nvox] air (Rayleigh) extinction, None: one species
 
     @property
     def nvox(self) -> int:
@@ -78,6 +79,7 @@ class Params:
     max_events: int = 100_000
     rr_threshold: float = 0.01     # Russian roulette below this fraction of I0
     rr_survival: float = 0.1       # survival probability in roulette
+    albedo_air: float = 1.0        # single-scattering albedo of air (two species)
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -630,6 +630,107 @@ def test_classic_gradient_along_beta_matches_the_slab_closed_form(orc):
 
 
 # ------------------------------------------------------------------------------------------
+# two species: air (Rayleigh, Eq. Pray / Eq. thetaREY) and aerosol (HG), particle chosen by
+# beta_air / beta at each event (Sec. 2.1.2, step iv)
+
+
+def test_rayleigh_phase_and_sampler(orc):
+    # normalised over the sphere (midpoint rule in mu is exact to 1e-9 for this quadratic)
+    mus = (np.arange(20000) + 0.5) / 10000.0 - 1.0
+    assert abs(2 * math.pi * sum(orc.rayleigh_phase(m) for m in mus) / 10000.0 - 1.0) < 1e-8
+    # the sampler inverts the CDF of (3/8)(1 + mu^2) on [-1, 1]: F(mu) = (mu^3 + 3 mu + 4) / 8
+    for u in np.linspace(1e-6, 1 - 1e-6, 101):
+        c = orc.rayleigh_sample(u)
+        assert -1.0 <= c <= 1.0 and abs((c ** 3 + 3 * c + 4) / 8 - u) < 1e-12, (u, c)
+    # moments of the sampled cosine: E[mu] = 0, E[mu^2] = 2/5
+    us = (np.arange(200000) + 0.5) / 200000
+    cs = np.array([orc.rayleigh_sample(u) for u in us])
+    assert abs(cs.mean()) < 1e-9 and abs((cs ** 2).mean() - 0.4) < 1e-6
+
+
+def _slab_two_species(F, alb_air, alb_aer, g, b_air, b_aer, H, mu0, sun, d):
+    """Single scattering by a homogeneous two-species slab: the one-species closed form with
+    the scattering phase replaced by the species-weighted sum (b_air alb_air P_Ray + b_aer alb_aer
+    P_HG) / (b_air + b_aer) and the total optical depth."""
+    b = b_air + b_aer
+    mu, tau = d[2], b * H
+    cs = float(np.dot(sun, -d))
+    p_hg = (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * cs) ** 1.5)
+    p_ray = 3.0 / (16 * math.pi) * (1 + cs * cs)
+    mix = (b_air * alb_air * p_ray + b_aer * alb_aer * p_hg) / b
+    if abs(mu - mu0) < 1e-9:
+        return F * mix * tau / mu0 * math.exp(-tau / mu0)
+    return F * mix * mu0 / (mu - mu0) * (math.exp(-tau / mu) - math.exp(-tau / mu0))
+
+
+def _two_species_slab(b_air, b_aer):
+    import dataclasses
+    sc = slab_scene(b_aer, cam_z=-50.0)
+    return dataclasses.replace(sc, beta_air=np.full(sc.nvox, b_air))
+
+
+def _pixel_avg(sc, fn, pix, n=12):
+    i, j = pix % 4, pix // 4
+    acc = wsum = 0.0
+    tx = math.tan(0.5 * sc.cam_fov[0])
+    for a in range(n):
+        for b in range(n):
+            px, py = i + (a + 0.5) / n, j + (b + 0.5) / n
+            x, y = (2 * px / 4 - 1) * tx, (2 * py / 4 - 1) * tx
+            w = (1 + x * x + y * y) ** -1.5
+            acc += w * fn(rg.pixel_dir(sc, 0, px, py))
+            wsum += w
+    return acc / wsum
+
+
+@pytest.mark.slow
+def test_two_species_slab_single_scatter(orc):
+    """Classic estimate, first order, air + aerosol: the species-weighted closed form."""
+    b_air, b_aer, alb_aer, alb_air, g = 1.0e-3, 1.5e-3, 0.8, 1.0, 0.6
+    sc = _two_species_slab(b_air, b_aer)
+    p = synth.Params(albedo=alb_aer, albedo_air=alb_air, g=g, sun_zenith=math.radians(30), n_photons=6_400_000,
+                     seed=24, max_order=1, rr_threshold=0.0)
+    nb = 16
+    imgs = batched(orc, sc, p, nb, lambda q: orc.render(sc, q, want_L=False, classic=True)["classic"])
+    est, sig = imgs.sum(0), imgs.std(0, ddof=1) * math.sqrt(nb)
+    sun = np.array([-math.sin(p.sun_zenith), 0.0, -math.cos(p.sun_zenith)])
+    mu0 = math.cos(p.sun_zenith)
+    ref = np.array([_pixel_avg(sc, lambda d: _slab_two_species(1.0, alb_air, alb_aer, g, b_air, b_aer, 200.0, mu0,
+                                                                 sun, d), pix) for pix in range(16)])
+    # each pixel sees a few thousand events, so its estimate is skewed (the sum of inverse-square
+    # weighted contributions); the total over the pixels is tested at 3.5 sigma, pixels at 5
+    tot = imgs.sum(1)
+    assert abs(tot.sum() - ref.sum()) < 3.5 * tot.std(ddof=1) * math.sqrt(nb), (tot.sum(), ref.sum())
+    assert np.all(np.abs(est - ref) < 5.0 * sig + 2e-3 * ref), ((est - ref) / sig)
+
+
+@pytest.mark.slow
+def test_two_species_gradient_along_the_aerosol(orc):
+    """The aerosol gradient with two species (collision score 1/beta_aerosol for aerosol events,
+    none for air events): beta_aer . dE/dbeta_aer / (-2M), with a measured value M far above the
+    images, estimates sum_p beta_aer d i_p / d beta_aer, from the closed form of the slab."""
+    b_air, b_aer, alb_aer, g = 1.0e-3, 1.5e-3, 0.8, 0.6
+    sc = _two_species_slab(b_air, b_aer)
+    p = synth.Params(albedo=alb_aer, albedo_air=1.0, g=g, sun_zenith=math.radians(30), n_photons=6_400_000, seed=25,
+                     max_order=1, rr_threshold=0.0)
+    M = 1e6
+    meas = np.full(sc.n_pix, M)
+    dots = batched(orc, sc, p, 16, lambda q: float(np.dot(sc.beta, orc.full_grad(sc, q, meas, classic=True)["grad"])))
+    est_b = dots / (-2.0 * M)
+    est, sig = est_b.sum(), est_b.std(ddof=1) * math.sqrt(16)
+    sun = np.array([-math.sin(p.sun_zenith), 0.0, -math.cos(p.sun_zenith)])
+    mu0, e = math.cos(p.sun_zenith), 1e-4
+    ref = 0.0
+    for pix in range(16):
+        ref += _pixel_avg(sc, lambda d: (_slab_two_species(1.0, 1.0, alb_aer, g, b_air, b_aer * (1 + e), 200.0, mu0,
+                                                           sun, d)
+                                         - _slab_two_species(1.0, 1.0, alb_aer, g, b_air, b_aer * (1 - e), 200.0, mu0,
+                                                             sun, d)) / (2 * e), pix)
+    assert abs(est - ref) < 3.5 * sig + 5e-3 * abs(ref), (est, ref, sig)
+    assert abs(ref) > 10 * sig
+
+
+# ------------------------------------------------------------------------------------------
 # sharding and threading: the photon-id split does not change the result
 
 
