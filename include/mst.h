@@ -222,6 +222,59 @@ int mst_set_reg_weights(mst_grid *g, const double *wz_host);
 int mst_render_bmc(mst_grid *g, const float *beta_dev, const mst_params *p, uint32_t n_per_pixel, double *images_dev,
                    double *var_dev, void *stream);
 
+/* Two-species medium (Sec. 2; Sec. 2.1.2 steps iv-vi): air molecules beside the aerosol field
+ * that beta describes. The extinction the photons see is beta + beta_air; at each scattering
+ * event the particle is air with probability beta_air / (beta + beta_air) in the event's voxel
+ * (Philox counter (id lo, id hi, event, 0xFFFFFFFF), first uniform u: air when
+ * u (beta + beta_air) < beta_air, evaluated in FP64), and the event takes that particle's albedo
+ * (albedo_air for air, params.albedo for aerosol) and phase function: Rayleigh (Eq. Pray),
+ * sampled by Eq. thetaREY, for air; Henyey-Greenstein (Eq. Phg) for aerosol.
+ *   beta_air_dev [nvox] float, >= 0, on the handle's device, or NULL for one species. Borrowed:
+ *                the caller keeps it alive and unchanged until it is replaced or the handle
+ *                is destroyed; it is read by every later call.
+ *   albedo_air   in [0, 1] (1: air absorbs nothing at visible wavelengths).
+ * With air set, mst_render and mst_render_grad render the mixture, and the gradients are
+ * dE/dbeta w.r.t. the aerosol field (the air field is known). MST_GRAD_FULL: the free-flight
+ * score of every flight plus 1/beta for aerosol events only, and the LOS transmittance through
+ * the total extinction. MST_GRAD_SURROGATE and mst_surrogate_grad (whose beta and beta_ref are
+ * then aerosol fields too): j = L / (beta + beta_air) held fixed, every term a derivative
+ * w.r.t. the total, which equals the derivative w.r.t. the aerosol. The regulariser acts on the
+ * aerosol field. mst_render_bmc returns MST_ERR_UNSUPPORTED (one species); mst_transmittance,
+ * mst_form_images, mst_ray_counts and mst_regularizer use the field they are given. The first
+ * call with a field allocates two [nvox] float buffers on the handle (the FP32 totals); no
+ * other device work. Returns MST_ERR_INVALID_ARG for albedo_air outside [0, 1]. */
+int mst_set_air(mst_grid *g, const float *beta_air_dev, double albedo_air);
+
+#define MST_MAX_CHANNELS 8
+
+/* One colour channel mu of a multi-channel reconstruction (Sec. 5, Eq. channelBeta). */
+typedef struct {
+    mst_params params;              /* the channel's render: aerosol albedo and g, sun irradiance F_mu, photons,
+                                       seed, estimator, grad_mode, conditioning, grid_dtype; reg_eta is
+                                       ignored (the regulariser acts once, on the reference field) */
+    const float *beta_air_dev;      /* [nvox] float air extinction in this channel, or NULL (no air) */
+    double albedo_air;              /* air albedo in this channel, in [0, 1] */
+    double sigma_ratio;             /* sigma~_mu = sigma_aerosol,mu / sigma_aerosol,ref, > 0 */
+    const double *images_meas_dev;  /* [sum W*H] measured images of the channel */
+    double *images_dev;             /* [sum W*H] rendered images of the channel, or NULL */
+} mst_channel;
+
+/* Multi-channel loss and gradient w.r.t. the reference channel's aerosol field
+ * (Eq. channelBeta, Eq. Cost, Eq. divCost1). Channel mu renders the two-species medium with
+ * aerosol sigma_ratio_mu * beta_aer_dev (rounded to float) and its own air field, as
+ * mst_render_grad with mst_set_air would; then
+ *   E = sum_mu E_mu + eta Psi(beta_aer),  dE/dbeta_aer = sum_mu sigma_ratio_mu dE_mu/dbeta_mu + eta dPsi,
+ * E_mu the masked L2 loss of channel mu (Eq. Cost) and Psi the regulariser of mst_regularizer.
+ *   beta_aer_dev [nvox] float >= 0; channels [n_channels] host structs (1..MST_MAX_CHANNELS);
+ *   mask_dev [sum W*H] uint8 or NULL, shared by all channels; grad_dev [nvox] double, written;
+ *   loss_dev [1] double or NULL.
+ * With MST_GRAD_SURROGATE in a channel's params, dE_mu/dbeta_mu is the surrogate of
+ * mst_render_grad (Eq. divCost1 with Q_c, j of the channel fixed). The handle's own mst_set_air
+ * setting is left as it was. Channels run one after another on the stream; mst_get_stats then
+ * holds the last channel's statistics. */
+int mst_render_grad_channels(mst_grid *g, const float *beta_aer_dev, int n_channels, const mst_channel *channels,
+                             const uint8_t *mask_dev, double eta, double *grad_dev, double *loss_dev, void *stream);
+
 /* Device memory the handle may hold for the events a full-gradient forward render stores
  * (44 B per scattering event: voxel, position, incoming direction, weight, photon index, event
  * number, and its w_s), for

@@ -282,6 +282,39 @@ def full_grad(scene, params, meas, mask=None, eta=0.0, nthreads=0, skip=None, cl
     return dict(images=img, grad=g, loss=loss.value, L=L, stats=dict(zip(ST_NAMES, st.tolist())))
 
 
+def channels_grad(scene, beta_ref, channels, mask=None, eta=0.0, skip=None, nthreads=0, classic=False,
+                  surrogate=False, conditioning="none"):
+    """Multi-channel loss and gradient w.r.t. the reference aerosol field (Eq. channelBeta,
+    Eq. Cost, Eq. divCost1). Channel mu renders the two-species medium with aerosol
+    sigma_mu * beta_ref and its own air field: beta_mu = beta_air_mu + sigma_mu beta_ref. The loss
+    is the sum of the channels' masked L2 losses plus eta Psi(beta_ref), once; the gradient is
+    sum_mu sigma_mu dE_mu/dbeta_aerosol_mu + eta dPsi/dbeta_ref (chain rule through
+    Eq. channelBeta). channels: dicts with params (albedo_air inside), sigma, meas and beta_air
+    (None: no air in that channel). surrogate=True: each channel's dE_mu/dbeta_mu is the
+    surrogate with j = L_mu / beta_mu fixed (Eq. divCost1 with Q_c), L_mu rendered here at the
+    channel's total field."""
+    import dataclasses
+    beta_ref = np.asarray(beta_ref, dtype=np.float64)
+    loss, grad, imgs = 0.0, np.zeros(scene.nvox), []
+    for ch in channels:
+        sc = dataclasses.replace(scene, beta=ch["sigma"] * beta_ref, beta_air=ch.get("beta_air"))
+        if surrogate:
+            L = render(sc, ch["params"], skip=skip, nthreads=nthreads)["L"]
+            tot = sc.beta + (0.0 if sc.beta_air is None else np.asarray(sc.beta_air, dtype=np.float64))
+            r = surrogate_grad(sc, L, tot, ch["meas"], mask, conditioning, eta=0.0)
+        else:
+            r = full_grad(sc, ch["params"], ch["meas"], mask, eta=0.0, nthreads=nthreads, skip=skip,
+                          classic=classic)
+        loss += r["loss"]
+        grad += ch["sigma"] * r["grad"]
+        imgs.append(r["images"])
+    if eta != 0.0:
+        psi, dpsi = laplacian(dataclasses.replace(scene, beta_air=None), beta_ref)
+        loss += eta * psi
+        grad += eta * dpsi
+    return dict(loss=loss, grad=grad, images=imgs)
+
+
 def bmc_pixel(scene, params, cam: int, i: int, j: int, n: int):
     b = _Bound(scene)
     q = _params(params)

@@ -39,7 +39,7 @@ EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy"
            "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
            "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
            "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory", "mst_render_bmc",
-           "mst_set_reg_weights"]
+           "mst_set_reg_weights", "mst_set_air", "mst_render_grad_channels"]
 PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine", "replay2",
           "replay_list", "event_adjoint", "bmc"]
 
@@ -69,6 +69,11 @@ class Params(ctypes.Structure):
                 ("reg_eta", ctypes.c_double)]
 
 
+class Channel(ctypes.Structure):  # mst_channel
+    _fields_ = [("params", Params), ("beta_air", ctypes.c_void_p), ("albedo_air", ctypes.c_double),
+                ("sigma_ratio", ctypes.c_double), ("images_meas", ctypes.c_void_p), ("images", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
@@ -89,6 +94,8 @@ def _load():
     L.mst_set_debug.argtypes = [P, P, P]
     L.mst_set_replay_memory.argtypes = [P, ctypes.c_uint64]
     L.mst_set_reg_weights.argtypes = [P, P]
+    L.mst_set_air.argtypes = [P, P, ctypes.c_double]
+    L.mst_render_grad_channels.argtypes = [P, P, I, P, P, D, P, P, P]
     L.mst_render_bmc.argtypes = [P, P, P, ctypes.c_uint32, P, P, P]
     L.mst_get_stats.argtypes = [P, P]
     L.mst_set_profiling.argtypes = [P, I]
@@ -295,6 +302,42 @@ class Grid:
         if w.shape != (self.shape[2],):
             raise ValueError(f"need {self.shape[2]} weights, one per layer")
         self._check(lib.mst_set_reg_weights(self._h, w.ctypes.data_as(ctypes.c_void_p)), "mst_set_reg_weights")
+
+    def set_air(self, beta_air=None, albedo_air: float = 1.0):
+        """Two-species medium: air extinction [nvox] (float32 on the device) beside the aerosol
+        beta of later calls, Rayleigh phase and albedo albedo_air; None restores one species.
+        The tensor is kept referenced here while attached (the library borrows it)."""
+        beta_air = self._t(beta_air, self.nvox, torch.float32, "beta_air")
+        self._check(lib.mst_set_air(self._h, _ptr(beta_air), float(albedo_air)), "mst_set_air")
+        self._air = beta_air
+
+    def render_grad_channels(self, beta, channels, mask=None, eta: float = 0.0, images=True, stream=None):
+        """Multi-channel loss and gradient w.r.t. the reference aerosol field beta (Eq. channelBeta,
+        Eq. Cost, Eq. divCost1). channels: list of dicts with keys params (Params, grad_mode full),
+        meas ([n_pix] float64 CUDA tensor), sigma (sigma~_mu), and optionally beta_air ([nvox]
+        float32 CUDA tensor) and albedo_air (default 1). Returns dict(loss, grad, images=[per
+        channel] or None)."""
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        mask = self._t(mask, self.n_pix, torch.uint8, "mask")
+        n = len(channels)
+        arr = (Channel * max(n, 1))()
+        keep, imgs = [], []
+        for i, c in enumerate(channels):
+            meas = self._t(c["meas"], self.n_pix, torch.float64, f"channel {i} meas")
+            air = self._t(c.get("beta_air"), self.nvox, torch.float32, f"channel {i} beta_air")
+            img = self._new(self.n_pix) if images else None
+            arr[i].params = c["params"]
+            arr[i].beta_air = _ptr(air)
+            arr[i].albedo_air = float(c.get("albedo_air", 1.0))
+            arr[i].sigma_ratio = float(c["sigma"])
+            arr[i].images_meas = _ptr(meas)
+            arr[i].images = _ptr(img)
+            keep += [meas, air]
+            imgs.append(img)
+        grad, loss = self._new(self.nvox), self._new(1)
+        self._check(lib.mst_render_grad_channels(self._h, _ptr(beta), n, arr, _ptr(mask), float(eta), _ptr(grad),
+                                                 _ptr(loss), _stream(stream)), "mst_render_grad_channels")
+        return dict(loss=loss, grad=grad, images=imgs if images else None)
 
     def set_replay_memory(self, nbytes: int):
         """Budget for the events a full-gradient forward render stores (0: W by replay)."""

@@ -117,6 +117,9 @@ TransportArgs transport_args(mst_grid* g, const mst_params* p) {
     a.hg.tg = (float)(2.0 * gg);
     a.hg.iso = std::fabs(gg) < 1e-6;
     a.beta = g->ext;
+    a.beta_air = g->air;  // two species (Sec. 2): the particle of each event is drawn
+    a.beta_aer = g->air ? g->beta_in : nullptr;
+    a.albedo_air = (float)g->albedo_air;
     const double th = p->sun_zenith_rad, ph = p->sun_azimuth_rad;
     a.sun = make_float3((float)(-std::sin(th) * std::cos(ph)), (float)(-std::sin(th) * std::sin(ph)),
                         (float)(-std::cos(th)));
@@ -176,9 +179,9 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
     const bool classic_adj = replay && p->estimator == MST_EST_CLASSIC;
     const int m_p1 = classic_adj ? 5 : 3, m_p2 = classic_adj ? 6 : 2;
     if (classic_adj) a.cres = g->resid;
-    const int b_fwd = g->sm_count * transport_blocks_per_sm(p->grid_dtype, est);
-    const int b_p1 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, m_p1);
-    const int b_p2 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, m_p2);
+    const int b_fwd = g->sm_count * transport_blocks_per_sm(p->grid_dtype, est, g->air != nullptr);
+    const int b_p1 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, m_p1, g->air != nullptr);
+    const int b_p2 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, m_p2, g->air != nullptr);
     if (replay) set_fold(a, (uint64_t)g->geo.nvox);
     else if (est == MST_EST_VOXEL) set_fold(a, (uint64_t)g->geo.nvox * g->cp);
     if (store_events) {
@@ -251,10 +254,12 @@ int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
         MST_CK(launch_event_offsets(g, a.n, st));
         MST_CK(launch_event_adjoint(g, a, p->grid_dtype, st));
     }
+    const bool two = g->air != nullptr;
+    auto blocks = [&](int mode) { return g->sm_count * transport_blocks_per_sm(p->grid_dtype, mode, two); };
     a.ticket = g->tickets;
     {
         Phase ph(g, MST_PH_REPLAY, st);  // returns at once when the events fitted
-        MST_CK(launch_transport(g, a, p->grid_dtype, 3, g->sm_count * transport_blocks_per_sm(p->grid_dtype, 3), st));
+        MST_CK(launch_transport(g, a, p->grid_dtype, 3, blocks(3), st));
     }
     {
         Phase ph(g, MST_PH_REPLAY_LIST, st);
@@ -263,8 +268,8 @@ int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
     a.ticket = g->tickets + 1;
     {
         Phase ph(g, MST_PH_REPLAY2, st);  // on the stored w_s (mode 4), or recomputing them when they did not fit
-        MST_CK(launch_transport(g, a, p->grid_dtype, 4, g->sm_count * transport_blocks_per_sm(p->grid_dtype, 4), st));
-        MST_CK(launch_transport(g, a, p->grid_dtype, 2, g->sm_count * transport_blocks_per_sm(p->grid_dtype, 2), st));
+        MST_CK(launch_transport(g, a, p->grid_dtype, 4, blocks(4), st));
+        MST_CK(launch_transport(g, a, p->grid_dtype, 2, blocks(2), st));
     }
     Phase ph(g, MST_PH_FOLD, st);
     MST_CK(launch_fold_grad(g, st));
@@ -382,12 +387,31 @@ void free_all(mst_grid* g) {
     cudaFree(g->wseq);
     cudaFree(g->evoff);
     cudaFree(g->reg_wz);
+    cudaFree(g->ch_beta);
+    cudaFree(g->ch_grad);
+    cudaFree(g->btot);
+    cudaFree(g->btot_ref);
     cudaFree(g->ev_count);
     if (g->ev_seen) cudaFreeHost(g->ev_seen);
     if (g->ev_seen_ready) cudaEventDestroy(g->ev_seen_ready);
 }
 
 int check_render_grad(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const double* grad);
+
+// Two species: the FP32 totals beta + beta_air (and beta_ref + beta_air) of the surrogate.
+int ensure_air_totals(mst_grid* g) {
+    const size_t n = sizeof(float) * (size_t)g->geo.nvox;
+    if (!g->btot && cudaMalloc(&g->btot, n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(g, MST_ERR_OOM, "air buffers: out of device memory");
+    }
+    if (!g->btot_ref && cudaMalloc(&g->btot_ref, n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(g, MST_ERR_OOM, "air buffers: out of device memory");
+    }
+    return MST_OK;
+}
+
 int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const double* meas, const uint8_t* mask,
                      double* images, double* grad, double* loss, cudaStream_t st);
 
@@ -587,9 +611,10 @@ int mst_render(mst_grid* g, const float* beta, const mst_params* p, double* imag
     DeviceGuard dg(g->device);
     cudaStream_t st = as_stream(stream);
     prof_reset(g);
+    g->beta_in = beta;
     {
         Phase ph(g, MST_PH_STAGE, st);
-        MST_CK(launch_stage(g, beta, p->grid_dtype, st));
+        MST_CK(launch_stage(g, beta, g->air, p->grid_dtype, st));
     }
     MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
     const size_t nL = (size_t)g->n_cams * g->geo.nvox;
@@ -624,12 +649,13 @@ int mst_render_bmc(mst_grid* g, const float* beta, const mst_params* p, uint32_t
     if (n_per_pixel < 1) return fail(g, MST_ERR_INVALID_ARG, "n_per_pixel must be >= 1");
     if (p->max_events < 1) return fail(g, MST_ERR_INVALID_ARG, "max_events must be >= 1");
     if (p->max_order < 0) return fail(g, MST_ERR_INVALID_ARG, "max_order must be >= 0");
+    if (g->air) return fail(g, MST_ERR_UNSUPPORTED, "backward Monte Carlo renders one species (mst_set_air is set)");
     DeviceGuard dg(g->device);
     cudaStream_t st = as_stream(stream);
     prof_reset(g);
     {
         Phase ph(g, MST_PH_STAGE, st);
-        MST_CK(launch_stage(g, beta, p->grid_dtype, st));
+        MST_CK(launch_stage(g, beta, nullptr, p->grid_dtype, st));
     }
     MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
     MST_CK(cudaMemsetAsync(images, 0, sizeof(double) * g->total_pix, st));
@@ -668,9 +694,10 @@ int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const 
     int rc = MST_OK;
     const size_t nL = (size_t)g->n_cams * g->geo.nvox;
     double* lossp = loss ? loss : g->stats + MST_NSTATS;
+    g->beta_in = beta;
     {
         Phase ph(g, MST_PH_STAGE, st);
-        MST_CK(launch_stage(g, beta, p->grid_dtype, st));
+        MST_CK(launch_stage(g, beta, g->air, p->grid_dtype, st));
     }
     MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
     if (p->estimator == MST_EST_CLASSIC) {  // Eq. fle images, their loss, and the score replay
@@ -735,7 +762,8 @@ int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const 
         if (rc) return rc;
         {
             Phase ph(g, MST_PH_COMBINE, st);
-            MST_CK(launch_combine_surrogate(g, g->L64, nullptr, beta, beta, g->T, g->bacc, g->gT,
+            const float* bt = g->air ? g->btot : beta;  // two species: j = L / (beta + beta_air)
+            MST_CK(launch_combine_surrogate(g, g->L64, nullptr, bt, bt, g->T, g->bacc, g->gT,
                                             p->conditioning ? g->Qw : nullptr, grad, st));
         }
     } else {
@@ -773,7 +801,7 @@ int mst_transmittance(mst_grid* g, const float* beta, int dtype, float* T, void*
     prof_reset(g);
     {
         Phase ph(g, MST_PH_STAGE, st);
-        MST_CK(launch_stage(g, beta, dtype, st));
+        MST_CK(launch_stage(g, beta, nullptr, dtype, st));
     }
     {
         Phase ph(g, MST_PH_LOS, st);
@@ -791,7 +819,7 @@ int mst_form_images(mst_grid* g, const float* beta, int dtype, const double* L, 
     prof_reset(g);
     {
         Phase ph(g, MST_PH_STAGE, st);
-        MST_CK(launch_stage(g, beta, dtype, st));
+        MST_CK(launch_stage(g, beta, nullptr, dtype, st));
     }
     {
         Phase ph(g, MST_PH_LOS, st);
@@ -817,13 +845,18 @@ int mst_surrogate_grad(mst_grid* g, const float* beta, const double* L_ref, cons
     prof_reset(g);
     const size_t nL = (size_t)g->n_cams * g->geo.nvox;
     double* lossp = loss ? loss : g->stats + MST_NSTATS;
+    // two species: j = L_ref / (beta_ref + beta_air) and L = j (beta + beta_air); the terms of
+    // the gradient are derivatives w.r.t. the total, which equal those w.r.t. the aerosol
+    const float* bt = g->air ? g->btot : beta;
+    const float* btr = g->air ? g->btot_ref : beta_ref;
     {
         Phase ph(g, MST_PH_STAGE, st);
-        MST_CK(launch_stage(g, beta, p->grid_dtype, st));
+        MST_CK(launch_stage(g, beta, g->air, p->grid_dtype, st));
+        if (g->air) MST_CK(launch_add_air(g, beta_ref, g->air, g->btot_ref, st));
     }
     {
         Phase ph(g, MST_PH_LOS, st);
-        MST_CK(launch_los(g, p->grid_dtype, L_ref, nullptr, beta_ref, beta, g->T, g->R, st));
+        MST_CK(launch_los(g, p->grid_dtype, L_ref, nullptr, btr, bt, g->T, g->R, st));
     }
     MST_CK(cudaMemsetAsync(lossp, 0, sizeof(double), st));
     {
@@ -844,7 +877,7 @@ int mst_surrogate_grad(mst_grid* g, const float* beta, const double* L_ref, cons
     if (rc) return rc;
     {
         Phase ph(g, MST_PH_COMBINE, st);
-        MST_CK(launch_combine_surrogate(g, L_ref, nullptr, beta_ref, beta, g->T, g->bacc, g->gT,
+        MST_CK(launch_combine_surrogate(g, L_ref, nullptr, btr, bt, g->T, g->bacc, g->gT,
                                         p->conditioning ? g->Qw : nullptr, grad, st));
     }
     if (p->reg_eta != 0.0) {
@@ -927,6 +960,80 @@ int mst_set_reg_weights(mst_grid* g, const double* wz) {
         if (!std::isfinite(wz[z])) return fail(g, MST_ERR_INVALID_ARG, "altitude weights must be finite");
     if (!g->reg_wz) MST_CK(cudaMalloc(&g->reg_wz, sizeof(double) * g->geo.nz));
     MST_CK(cudaMemcpy(g->reg_wz, wz, sizeof(double) * g->geo.nz, cudaMemcpyHostToDevice));
+    return MST_OK;
+}
+
+int mst_set_air(mst_grid* g, const float* beta_air, double albedo_air) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!(albedo_air >= 0.0 && albedo_air <= 1.0)) return fail(g, MST_ERR_INVALID_ARG, "albedo_air must be in [0, 1]");
+    if (beta_air) {
+        const int rc = ensure_air_totals(g);
+        if (rc) return rc;
+    }
+    g->air = beta_air;
+    g->albedo_air = albedo_air;
+    return MST_OK;
+}
+
+int mst_render_grad_channels(mst_grid* g, const float* beta, int n, const mst_channel* ch, const uint8_t* mask,
+                             double eta, double* grad, double* loss, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta || !ch || !grad) return fail(g, MST_ERR_INVALID_ARG, "beta, channels and grad are required");
+    if (n < 1 || n > MST_MAX_CHANNELS) return fail(g, MST_ERR_INVALID_ARG, "n_channels must be in 1..MST_MAX_CHANNELS");
+    if (!std::isfinite(eta)) return fail(g, MST_ERR_INVALID_ARG, "eta must be finite");
+    const float* air0 = g->air;
+    const double alb0 = g->albedo_air;
+    for (int i = 0; i < n; ++i) {
+        const std::string tag = "channel " + std::to_string(i) + ": ";
+        if (!(ch[i].sigma_ratio > 0.0 && std::isfinite(ch[i].sigma_ratio)))
+            return fail(g, MST_ERR_INVALID_ARG, tag + "sigma_ratio must be finite and > 0");
+        if (!(ch[i].albedo_air >= 0.0 && ch[i].albedo_air <= 1.0))
+            return fail(g, MST_ERR_INVALID_ARG, tag + "albedo_air must be in [0, 1]");
+        if (ch[i].beta_air_dev) {
+            const int rc = ensure_air_totals(g);
+            if (rc) return rc;
+        }
+        const int rc = check_render_grad(g, beta, &ch[i].params, ch[i].images_meas_dev, grad);
+        if (rc) return fail(g, rc, tag + g->err);
+    }
+    DeviceGuard dg(g->device);
+    cudaStream_t st = as_stream(stream);
+    prof_reset(g);
+    const size_t nvox = (size_t)g->geo.nvox;
+    if (!g->ch_beta && cudaMalloc(&g->ch_beta, sizeof(float) * nvox) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(g, MST_ERR_OOM, "channel buffers: out of device memory");
+    }
+    if (!g->ch_grad && cudaMalloc(&g->ch_grad, sizeof(double) * nvox) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(g, MST_ERR_OOM, "channel buffers: out of device memory");
+    }
+    double* lossp = loss ? loss : g->stats + MST_NSTATS + 2;  // slots past the statistics: scratch
+    double* loss_mu = g->stats + MST_NSTATS + 3;
+    MST_CK(cudaMemsetAsync(grad, 0, sizeof(double) * nvox, st));
+    MST_CK(cudaMemsetAsync(lossp, 0, sizeof(double), st));
+    int rc = MST_OK;
+    for (int i = 0; i < n && rc == MST_OK; ++i) {
+        if (launch_channel_beta(g, beta, ch[i].sigma_ratio, g->ch_beta, st) != cudaSuccess) {
+            rc = fail(g, MST_ERR_CUDA, "launch_channel_beta failed");
+            break;
+        }
+        g->air = ch[i].beta_air_dev;
+        g->albedo_air = ch[i].albedo_air;
+        mst_params pc = ch[i].params;
+        pc.reg_eta = 0.0;
+        rc = render_grad_impl(g, g->ch_beta, &pc, ch[i].images_meas_dev, mask, ch[i].images_dev, g->ch_grad, loss_mu,
+                              st);
+        if (rc == MST_OK && launch_channel_add(g, grad, ch[i].sigma_ratio, g->ch_grad, lossp, loss_mu, st) != cudaSuccess)
+            rc = fail(g, MST_ERR_CUDA, "launch_channel_add failed");
+    }
+    g->air = air0;
+    g->albedo_air = alb0;
+    if (rc) return rc;
+    if (eta != 0.0) {
+        Phase ph(g, MST_PH_COMBINE, st);
+        MST_CK(launch_regularizer(g, beta, eta, g->lap, g->stats + MST_NSTATS + 1, lossp, grad, st));
+    }
     return MST_OK;
 }
 
@@ -1066,6 +1173,8 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
         key_add(key, grads[i]);
         key_add(key, b->grids[i]->dbg_hash);
         key_add(key, b->grids[i]->dbg_skip);
+        key_add(key, b->grids[i]->air);
+        key_add(key, b->grids[i]->albedo_air);
     }
     key_add(key, losses);
     if (!b->exec || key != b->key) {
@@ -1084,7 +1193,8 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
                 b->err = g->err;
                 return rc;
             }
-            for (int mode = 0; mode < 7; ++mode) transport_blocks_per_sm(params[i].grid_dtype, mode);
+            for (int mode = 0; mode < 7; ++mode)
+                transport_blocks_per_sm(params[i].grid_dtype, mode, g->air != nullptr);
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             b->err = "stream error before capture";

@@ -106,6 +106,19 @@ __device__ __forceinline__ void hg_sample(const HG& h, float u, float& ct, float
     st = sqrtf(fmaxf(omc * opc, 0.f));
 }
 
+// Rayleigh phase function of air molecules (Eq. Pray): 3 / (16 pi) (1 + mu^2).
+__device__ __forceinline__ float rayleigh_phase(float mu) { return 0.05968310365946075f * fmaf(mu, mu, 1.f); }
+
+// Inverse CDF of Eq. Pray (Eq. thetaREY): the CDF of the cosine is (mu^3 + 3 mu + 4) / 8, and
+// Cardano's root of mu^3 + 3 mu + 4 - 8u = 0 is mu = c - 1/c with c = cbrt(q + sqrt(q^2 + 1)),
+// q = 4u - 2. q + sqrt(q^2 + 1) lies in [0.23, 4.3] for u in [0, 1], so nothing cancels.
+__device__ __forceinline__ void rayleigh_sample(float u, float& ct, float& st) {
+    const float q = fmaf(4.f, u, -2.f);
+    const float c = cbrtf(q + sqrtf(fmaf(q, q, 1.f)));
+    ct = fminf(1.f, fmaxf(-1.f, c - 1.f / c));
+    st = sqrtf(fmaxf((1.f - ct) * (1.f + ct), 0.f));
+}
+
 // New unit direction at polar angle (cos ct, sin st) and azimuth 2 pi u1 about d. Transverse
 // frame: e2 = normalize(axis x d), e1 = e2 x d, axis = z unless |d_z| >= 0.9, then x.
 __device__ __forceinline__ float3 rotate_dir(float3 d, float ct, float st, float u1) {

@@ -43,8 +43,11 @@ struct TransportArgs {
     CamSet cams;
     HG hg;
     const void* beta;          // staged extinction [nvox] in the compute dtype
+    const float* beta_air;     // two species: air extinction [nvox] (NULL: one species)
+    const float* beta_aer;     // two species: aerosol extinction [nvox], the unknown
     float3 sun;                // photon direction at launch
     float albedo, I0, rr_below, rr_survival, inv_rr_survival;
+    float albedo_air;          // single-scattering albedo of air (two species)
     uint2 key;
     uint64_t first_id;         // global id of chunk photon 0
     uint32_t n;                // photons in this chunk
@@ -121,6 +124,13 @@ struct mst_grid {
     double* cimg = nullptr;       // [total_pix] classic images of a gradient call
     double* lap = nullptr;        // [nvox] W^T W Lap beta
     double* reg_wz = nullptr;     // [nz] altitude weights W of the regulariser, NULL: W = I
+    const float* air = nullptr;   // [nvox] air extinction (borrowed, mst_set_air), NULL: one species
+    double albedo_air = 1.0;      // single-scattering albedo of air
+    const float* beta_in = nullptr;  // the running call's beta (the aerosol field with air)
+    float* btot = nullptr;        // [nvox] two species: beta + beta_air in FP32, written by the staging
+    float* btot_ref = nullptr;    // [nvox] two species: beta_ref + beta_air (mst_surrogate_grad)
+    float* ch_beta = nullptr;     // [nvox] mst_render_grad_channels: the channel's aerosol field
+    double* ch_grad = nullptr;    // [nvox] mst_render_grad_channels: the channel's gradient
     float* omega = nullptr;       // [total_pix]
     float* Qw = nullptr;          // [C][nvox] conditioning weights for qw_mode
     int qw_mode = -1;
@@ -145,7 +155,11 @@ struct mst_grid {
 namespace mst {
 
 // launchers (all enqueue on `st`; return cudaGetLastError())
-cudaError_t launch_stage(const mst_grid* g, const float* beta, int dtype, cudaStream_t st);
+cudaError_t launch_stage(const mst_grid* g, const float* beta, const float* air, int dtype, cudaStream_t st);
+cudaError_t launch_add_air(const mst_grid* g, const float* beta, const float* air, float* out, cudaStream_t st);
+cudaError_t launch_channel_beta(const mst_grid* g, const float* ref, double sigma, float* out, cudaStream_t st);
+cudaError_t launch_channel_add(const mst_grid* g, double* grad, double sigma, const double* gmu, double* loss,
+                               const double* loss_mu, cudaStream_t st);
 // transport kernel modes: 0 forward voxel LE, 1 forward classic LE, 3 replay pass 1, 2 replay pass 2,
 // 4 replay pass 2 reading w_s from the stored events, 5 / 6 passes 1 / 2 of the classic-estimator
 // gradient
@@ -178,6 +192,6 @@ cudaError_t launch_classic_residual(const mst_grid* g, const double* img, const 
                                     double* resid, double* loss, cudaStream_t st);
 cudaError_t launch_regularizer(const mst_grid* g, const float* beta, double eta, double* lap, double* psi,
                                double* loss, double* grad, cudaStream_t st);
-int transport_blocks_per_sm(int dtype, int mode);
+int transport_blocks_per_sm(int dtype, int mode, bool two);
 
 }  // namespace mst

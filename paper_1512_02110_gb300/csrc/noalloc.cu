@@ -109,7 +109,7 @@ extern "C" int mst_transmittance_noalloc(const mst_grid_desc* d, int n_cams, con
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // staging writes every voxel of this grid, so no clearing is needed
-    if (mst::launch_stage(&g, beta_dev, MST_GRID_F32, st) != cudaSuccess) return MST_ERR_CUDA;
+    if (mst::launch_stage(&g, beta_dev, nullptr, MST_GRID_F32, st) != cudaSuccess) return MST_ERR_CUDA;
     if (mst::launch_los(&g, MST_GRID_F32, nullptr, nullptr, nullptr, beta_dev, T_dev, nullptr, st) != cudaSuccess)
         return MST_ERR_CUDA;
     g.ext = nullptr;  // not owned

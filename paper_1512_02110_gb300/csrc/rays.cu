@@ -15,11 +15,21 @@ constexpr int kTB = 256;
 
 // The extinction grid in the compute dtype, in the linear voxel order of the input.
 template <int DT>
-__global__ void k_stage(const float* __restrict__ beta, void* __restrict__ ext, int nvox) {
+__global__ void k_stage(const float* __restrict__ beta, const float* __restrict__ air, void* __restrict__ ext,
+                        float* __restrict__ tot, int nvox) {
     typedef typename BetaFetch<DT>::T T;
     T* out = static_cast<T*>(ext);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nvox; k += gridDim.x * blockDim.x)
-        out[k] = BetaFetch<DT>::make(beta[k]);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nvox; k += gridDim.x * blockDim.x) {
+        const float b = air ? beta[k] + air[k] : beta[k];  // Sec. 2: beta = beta_aerosol + beta_air
+        out[k] = BetaFetch<DT>::make(b);
+        if (tot) tot[k] = b;  // two species: the FP32 total for the surrogate's j = L / beta
+    }
+}
+
+// beta_ref + beta_air in FP32 (the surrogate's reference total)
+__global__ void k_add_air(const float* __restrict__ beta, const float* __restrict__ air, float* __restrict__ out,
+                          int nvox) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nvox; k += gridDim.x * blockDim.x) out[k] = beta[k] + air[k];
 }
 
 __device__ __forceinline__ void flush_count(double* stats, int slot, unsigned long long n) {
@@ -263,12 +273,18 @@ inline int nblocks(long long n, int tb = kTB, int cap = 1 << 20) {
 
 }  // namespace
 
-cudaError_t launch_stage(const mst_grid* g, const float* beta, int dtype, cudaStream_t st) {
+cudaError_t launch_stage(const mst_grid* g, const float* beta, const float* air, int dtype, cudaStream_t st) {
     const int nvox = g->geo.nvox;
     const int nb = nblocks(nvox, kTB, 8192);
-    if (dtype == 0) k_stage<0><<<nb, kTB, 0, st>>>(beta, g->ext, nvox);
-    else if (dtype == 1) k_stage<1><<<nb, kTB, 0, st>>>(beta, g->ext, nvox);
-    else k_stage<2><<<nb, kTB, 0, st>>>(beta, g->ext, nvox);
+    float* tot = air ? g->btot : nullptr;
+    if (dtype == 0) k_stage<0><<<nb, kTB, 0, st>>>(beta, air, g->ext, tot, nvox);
+    else if (dtype == 1) k_stage<1><<<nb, kTB, 0, st>>>(beta, air, g->ext, tot, nvox);
+    else k_stage<2><<<nb, kTB, 0, st>>>(beta, air, g->ext, tot, nvox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_air(const mst_grid* g, const float* beta, const float* air, float* out, cudaStream_t st) {
+    k_add_air<<<nblocks(g->geo.nvox, kTB, 4096), kTB, 0, st>>>(beta, air, out, g->geo.nvox);
     return cudaGetLastError();
 }
 
@@ -333,6 +349,32 @@ cudaError_t launch_combine_full(const mst_grid* g, const float* gT, const double
 cudaError_t launch_classic_residual(const mst_grid* g, const double* img, const double* meas, const uint8_t* mask,
                                     double* resid, double* loss, cudaStream_t st) {
     k_classic_resid<<<nblocks(g->total_pix, kTB, 4096), kTB, 0, st>>>(img, meas, mask, resid, loss, g->total_pix);
+    return cudaGetLastError();
+}
+
+// Eq. channelBeta: the aerosol of channel mu, sigma~_mu times the reference field (FP64 product,
+// rounded to FP32 like every beta the library reads).
+__global__ void k_channel_beta(const float* __restrict__ ref, double sigma, float* __restrict__ out, int nvox) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nvox; k += gridDim.x * blockDim.x)
+        out[k] = (float)(sigma * (double)ref[k]);
+}
+
+// Eq. divCost1 and Eq. Cost over channels: grad += sigma~_mu dE_mu/dbeta_mu, loss += E_mu.
+__global__ void k_channel_add(double* __restrict__ grad, double sigma, const double* __restrict__ gmu, int nvox,
+                              double* loss, const double* loss_mu) {
+    const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int k = k0; k < nvox; k += gridDim.x * blockDim.x) grad[k] += sigma * gmu[k];
+    if (k0 == 0) *loss += *loss_mu;
+}
+
+cudaError_t launch_channel_beta(const mst_grid* g, const float* ref, double sigma, float* out, cudaStream_t st) {
+    k_channel_beta<<<nblocks(g->geo.nvox, kTB, 4096), kTB, 0, st>>>(ref, sigma, out, g->geo.nvox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_channel_add(const mst_grid* g, double* grad, double sigma, const double* gmu, double* loss,
+                               const double* loss_mu, cudaStream_t st) {
+    k_channel_add<<<nblocks(g->geo.nvox, kTB, 4096), kTB, 0, st>>>(grad, sigma, gmu, g->geo.nvox, loss, loss_mu);
     return cudaGetLastError();
 }
 

@@ -119,10 +119,11 @@ __device__ __forceinline__ void launch_photon(const TransportArgs& A, Photon& ph
 // on, kCollided on a collision (ph.p and the voxel updated) or the exit face 0..5
 // (kWalkOverflow if the walk was abandoned). With S != 0 it also scatters the score of the
 // flight into the gradient tile: -S * length in every voxel crossed and S * (1/beta - length)
-// in the collision voxel.
+// in the collision voxel (with two species, TWO, only -S * length there: the event adds
+// S / beta_aer once it knows the particle).
 constexpr int kCollided = -2;
 
-template <int DT>
+template <int DT, bool TWO>
 __device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, Walk& w, float& tau, float S,
                                            unsigned& nsc) {
     const float b = BetaFetch<DT>::get(A.beta, w.lin);
@@ -136,7 +137,7 @@ __device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, W
         ph.iy = w.iy;
         ph.iz = w.iz;
         if (S != 0.f) {
-            atomicAdd(A.gacc + w.lin, S * (1.f / b - l));
+            atomicAdd(A.gacc + w.lin, S * ((TWO ? 0.f : 1.f / b) - l));
             ++nsc;
         }
         return kCollided;
@@ -157,9 +158,32 @@ __device__ __forceinline__ float cam_cosine(const TransportArgs& A, const Photon
     return r2 > 0.f ? (ph.d.x * v.x + ph.d.y * v.y + ph.d.z * v.z) * rsqrtf(r2) : 0.f;
 }
 
+// Step iv with two species (Sec. 2): the event's particle is air with probability
+// beta_air / (beta_air + beta_aer) in its voxel, drawn from Philox stream word 0xFFFFFFFF of
+// the event. The test u (beta_air + beta_aer) < beta_air runs in FP64 on the FP32 fields and the
+// 24-bit uniform, so it takes the same branch as an FP64 evaluation of the same expression; an
+// empty aerosol voxel always gives air (u < 1), an empty air voxel always aerosol.
+constexpr uint32_t kTypeStream = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool particle_is_air(const TransportArgs& A, const Photon& e, int k) {
+    const float u = draws(A.key, e.id, e.s, kTypeStream).x;
+    const double ba = (double)__ldg(A.beta_air + k);
+    return (double)u * (ba + (double)__ldg(A.beta_aer + k)) < ba;
+}
+
+// phase function of the event's particle: Rayleigh (Eq. Pray) for air, HG (Eq. Phg) otherwise.
+// The local estimates take the particle as a template parameter, so the one-species code keeps
+// no per-camera select.
+template <bool AIR>
+__device__ __forceinline__ float phase_of(const TransportArgs& A, float mu) {
+    if constexpr (AIR) return rayleigh_phase(mu);
+    else return hg_phase(A.hg, mu);
+}
+
 // Eq. Lcupdate: L_c(k) += albedo I_s P(angle between the incoming ray and X_c - X_s), for all
 // cameras at once, four cameras per vector atomic into the [nvox][cp] FP32 tile.
-__device__ __forceinline__ void le_voxel(const TransportArgs& A, const Photon& ph, float w, int k) {
+template <bool AIR>
+__device__ __forceinline__ void le_voxel_p(const TransportArgs& A, const Photon& ph, float w, int k) {
     float* row = A.Lacc + (size_t)k * A.cp;
     for (int c0 = 0; c0 < A.cams.n; c0 += 4) {
         float v[4];
@@ -170,7 +194,7 @@ __device__ __forceinline__ void le_voxel(const TransportArgs& A, const Photon& p
             if (c < A.cams.n) {
                 float r2;
                 const float mu = cam_cosine(A, ph, A.cams.c[c], r2);
-                if (r2 > 0.f) val = w * hg_phase(A.hg, mu);
+                if (r2 > 0.f) val = w * phase_of<AIR>(A, mu);
             }
             v[j] = val;
         }
@@ -178,8 +202,14 @@ __device__ __forceinline__ void le_voxel(const TransportArgs& A, const Photon& p
     }
 }
 
+__device__ __forceinline__ void le_voxel(const TransportArgs& A, const Photon& ph, float w, int k, bool air) {
+    if (air) le_voxel_p<true>(A, ph, w, k);
+    else le_voxel_p<false>(A, ph, w, k);
+}
+
 // w_s = sum_c a_c(k) albedo I_s P_c(s): the event's contribution to <a, L>.
-__device__ __forceinline__ float le_adjoint(const TransportArgs& A, const Photon& ph, float w, int k) {
+template <bool AIR>
+__device__ __forceinline__ float le_adjoint_p(const TransportArgs& A, const Photon& ph, float w, int k) {
     const float4* row = reinterpret_cast<const float4*>(A.adj + (size_t)k * A.cp);
     float acc = 0.f;
     for (int c0 = 0; c0 < A.cams.n; c0 += 4) {
@@ -191,11 +221,15 @@ __device__ __forceinline__ float le_adjoint(const TransportArgs& A, const Photon
             if (c < A.cams.n && aa[j] != 0.f) {
                 float r2;
                 const float mu = cam_cosine(A, ph, A.cams.c[c], r2);
-                if (r2 > 0.f) acc += aa[j] * w * hg_phase(A.hg, mu);
+                if (r2 > 0.f) acc += aa[j] * w * phase_of<AIR>(A, mu);
             }
         }
     }
     return acc;
+}
+
+__device__ __forceinline__ float le_adjoint(const TransportArgs& A, const Photon& ph, float w, int k, bool air) {
+    return air ? le_adjoint_p<true>(A, ph, w, k) : le_adjoint_p<false>(A, ph, w, k);
 }
 
 // Eq. fle: pixel p(X_s) of camera c += albedo I_s P t_{s->c} / (|V|^2 Omega_p)
@@ -205,7 +239,7 @@ __device__ __forceinline__ float le_adjoint(const TransportArgs& A, const Photon
 // classic-estimator gradient); OP 2 also scatters the shadow-ray terms d f / d beta_m =
 // -f * (length of the ray in voxel m), weighted by cres[p], into the gradient tile.
 template <int DT, int OP>
-__device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon& ph, float w, float* gacc) {
+__device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon& ph, float w, float* gacc, bool air) {
     float acc = 0.f;
     for (int c = 0; c < A.cams.n; ++c) {
         const Cam& cm = A.cams.c[c];
@@ -232,7 +266,7 @@ __device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon
         unsigned long long ns = 0;
         walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p,
                        [&](const Walk& wk, float len) { tau += BetaFetch<DT>::get(A.beta, wk.lin) * len; }, ns);
-        const float val = w * hg_phase(A.hg, mu) * expf(-tau) / (r2 * A.omega[gp]);
+        const float val = w * (air ? rayleigh_phase(mu) : hg_phase(A.hg, mu)) * expf(-tau) / (r2 * A.omega[gp]);
         if (OP == 0) {
             atomicAdd(A.cimg + gp, (double)val);
         } else {
@@ -247,12 +281,13 @@ __device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon
     return acc;
 }
 
-// step v (albedo weighting, Russian roulette) and step vi (HG direction, next free path).
-// Returns 0 to continue or the termination code.
+// step v (albedo weighting, Russian roulette) and step vi (new direction by the particle's
+// phase function, next free path). Returns 0 to continue or the termination code.
 template <typename TallyT>
-__device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, TallyT& t) {
-    t.add_absorbed((1.f - A.albedo) * ph.I);
-    ph.I *= A.albedo;
+__device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, TallyT& t, bool air) {
+    const float alb = air ? A.albedo_air : A.albedo;
+    t.add_absorbed((1.f - alb) * ph.I);
+    ph.I *= alb;
     if (ph.I == 0.f) return 2;
     if (A.max_order > 0 && (int)ph.s >= A.max_order) {
         t.add_forced(ph.I);
@@ -274,7 +309,8 @@ __device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, T
         }
     }
     float ct, st;
-    hg_sample(A.hg, u.x, ct, st);
+    if (air) rayleigh_sample(u.x, ct, st);
+    else hg_sample(A.hg, u.x, ct, st);
     ph.d = rotate_dir(ph.d, ct, st, u.y);
     ph.tau = -logf(1.f - u.w);
     return 0;
@@ -288,7 +324,9 @@ __device__ __forceinline__ void finish_photon(const TransportArgs& A, const Phot
 }
 
 // One stored event (forward, full gradient): what w_s = sum_c a_c(k) albedo I_s P_c(s) needs.
-__device__ __forceinline__ void store_event(const TransportArgs& A, unsigned long long i, const Photon& e, float wgt) {
+// Word 9 holds the event number, with the particle (1: air) in bit 31.
+__device__ __forceinline__ void store_event(const TransportArgs& A, unsigned long long i, const Photon& e, float wgt,
+                                            bool air) {
     const unsigned long long C = A.ev_cap;
     uint32_t* r = A.evrec + i;
     r[0] = (uint32_t)e.ix | ((uint32_t)e.iy << 11) | ((uint32_t)e.iz << 22);
@@ -300,7 +338,7 @@ __device__ __forceinline__ void store_event(const TransportArgs& A, unsigned lon
     r[6 * C] = __float_as_uint(e.d.z);
     r[7 * C] = __float_as_uint(wgt);
     r[8 * C] = e.idx - A.out_base;
-    r[9 * C] = e.s;
+    r[9 * C] = e.s | (air ? 0x80000000u : 0u);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -494,7 +532,9 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
 // listed photons again, with S_j = W - sum_{s<j} w_s (FP64), and
 // scatters the score of every flight that ends in an event; it stops at pass 1's last event.
 // Both passes run the same flight and event arithmetic, so they see the same path.
-template <int DT, int MODE>
+// TWO: two-species medium (the launch has an air field); one-species kernels carry none of its
+// code.
+template <int DT, int MODE, bool TWO>
 __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMinBlocksPass2
                                                        : (MODE == kPass1 ? kMinBlocksPass1
                                                           : ((MODE == kFwdClassic || MODE == kPass1C || MODE == kPass2C)
@@ -584,7 +624,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
         if (fly) {
             const float S = PASS2 ? (float)acc : 0.f;
 #pragma unroll 1
-            for (; nstep < kStepsPerTrip && r == -1; ++nstep) r = flight_step<DT>(A, ph, w, tau, S, scatters);
+            for (; nstep < kStepsPerTrip && r == -1; ++nstep) r = flight_step<DT, TWO>(A, ph, w, tau, S, scatters);
         }
         if (fly) {  // a flight longer than any straight walk through the grid is abandoned
             segments += nstep;
@@ -629,29 +669,36 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                 e.s += 1u;
                 ++events;
                 const int k = lin_index(A.g, e.ix, e.iy, e.iz);
-                const float wgt = A.albedo * e.I;
+                const bool air = TWO && particle_is_air(A, e, k);
+                const float wgt = (air ? A.albedo_air : A.albedo) * e.I;
                 if (!REPLAY) {
                     e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
-                    if (MODE == kFwdVoxel && A.ev_cap && ev_base + lane < A.ev_cap) store_event(A, ev_base + lane, e, wgt);
-                    if (MODE == 0) le_voxel(A, e, wgt, k);
-                    else le_classic<DT, 0>(A, e, wgt, nullptr);
-                    term = after_event(A, e, t);
+                    if (MODE == kFwdVoxel && A.ev_cap && ev_base + lane < A.ev_cap)
+                        store_event(A, ev_base + lane, e, wgt, air);
+                    if (MODE == 0) le_voxel(A, e, wgt, k, air);
+                    else le_classic<DT, 0>(A, e, wgt, nullptr, air);
+                    term = after_event(A, e, t, air);
                     if (term) finish_photon(A, e, term);
                 } else {
                     float we;
                     if constexpr (MODE == kPass2W) we = A.wseq[e.hash + e.s - 1u];
-                    else if constexpr (CLASSIC_ADJ) we = le_classic<DT, PASS2 ? 2 : 1>(A, e, wgt, A.gacc);
-                    else we = le_adjoint(A, e, wgt, k);
+                    else if constexpr (CLASSIC_ADJ) we = le_classic<DT, PASS2 ? 2 : 1>(A, e, wgt, A.gacc, air);
+                    else we = le_adjoint(A, e, wgt, k, air);
                     if (PASS1) {
                         eacc += (double)we;
-                        term = after_event(A, e, t);
+                        term = after_event(A, e, t, air);
                         if (term) {
                             A.wbuf[e.idx - A.out_base] = eacc;
                             A.nevbuf[e.idx - A.out_base] = e.s;
                         }
                     } else {
+                        const float S = (float)eacc;  // the score weight of the flight that ended here
+                        if (TWO && !air && S != 0.f) {  // two species: aerosol collision, S / beta_aer
+                            atomicAdd(A.gacc + k, S / __ldg(A.beta_aer + k));
+                            ++scatters;
+                        }
                         eacc -= (double)we;
-                        term = e.s == enev ? 1 : after_event(A, e, t);  // stop at pass 1's last event
+                        term = e.s == enev ? 1 : after_event(A, e, t, air);  // stop at pass 1's last event
                     }
                 }
             }
@@ -678,6 +725,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
 // w_s of every event the forward stored, instead of replay pass 1: the same arithmetic
 // (le_adjoint) on the same event state, written to the photon's slot in wseq for pass 2 and
 // added to W in FP64. Does nothing when the events did not fit (pass 1 then walks the paths).
+template <bool TWO>
 __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
     const unsigned long long cnt = *A.ev_count;
     if (cnt > A.ev_cap) return;
@@ -692,9 +740,11 @@ __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
         e.iz = (int)(v >> 22);
         e.p = make_float3(__uint_as_float(r[C]), __uint_as_float(r[2 * C]), __uint_as_float(r[3 * C]));
         e.d = make_float3(__uint_as_float(r[4 * C]), __uint_as_float(r[5 * C]), __uint_as_float(r[6 * C]));
-        const float w = le_adjoint(A, e, __uint_as_float(r[7 * C]), lin_index(A.g, e.ix, e.iy, e.iz));
+        const uint32_t sw = r[9 * C];  // event number, particle in bit 31
+        const float w = le_adjoint(A, e, __uint_as_float(r[7 * C]), lin_index(A.g, e.ix, e.iy, e.iz),
+                                   TWO && (sw >> 31) != 0u);
         const uint32_t j = r[8 * C];
-        A.wseq[A.evoff[j] + r[9 * C] - 1u] = w;  // event s of photon j: slot evoff[j] + s - 1
+        A.wseq[A.evoff[j] + (sw & 0x7FFFFFFFu) - 1u] = w;  // event s of photon j: slot evoff[j] + s - 1
         if (w != 0.f) atomicAdd(A.wbuf + j, (double)w);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.stats + MST_ST_EVENTS_STORED, (double)cnt);
@@ -902,53 +952,64 @@ int occupancy(K kern, size_t smem) {
     return n;
 }
 
-template <int DT, int MODE>
+template <int DT, int MODE, bool TWO>
 cudaError_t launch_mode(const TransportArgs& a, int blocks, cudaStream_t st) {
-    k_transport<DT, MODE><<<blocks, kTB, smem_bytes<(MODE >= 2)>(), st>>>(a);
+    k_transport<DT, MODE, TWO><<<blocks, kTB, smem_bytes<(MODE >= 2)>(), st>>>(a);
     return cudaGetLastError();
 }
 
-template <int DT>
+template <int DT, bool TWO>
 int occupancy_mode(int mode) {
     switch (mode) {
-        case kFwdVoxel: return occupancy(k_transport<DT, kFwdVoxel>, smem_bytes<false>());
-        case kFwdClassic: return occupancy(k_transport<DT, kFwdClassic>, smem_bytes<false>());
-        case kPass2: return occupancy(k_transport<DT, kPass2>, smem_bytes<true>());
-        case kPass2W: return occupancy(k_transport<DT, kPass2W>, smem_bytes<true>());
-        case kPass1C: return occupancy(k_transport<DT, kPass1C>, smem_bytes<true>());
-        case kPass2C: return occupancy(k_transport<DT, kPass2C>, smem_bytes<true>());
-        default: return occupancy(k_transport<DT, kPass1>, smem_bytes<true>());
+        case kFwdVoxel: return occupancy(k_transport<DT, kFwdVoxel, TWO>, smem_bytes<false>());
+        case kFwdClassic: return occupancy(k_transport<DT, kFwdClassic, TWO>, smem_bytes<false>());
+        case kPass2: return occupancy(k_transport<DT, kPass2, TWO>, smem_bytes<true>());
+        case kPass2W: return occupancy(k_transport<DT, kPass2W, TWO>, smem_bytes<true>());
+        case kPass1C: return occupancy(k_transport<DT, kPass1C, TWO>, smem_bytes<true>());
+        case kPass2C: return occupancy(k_transport<DT, kPass2C, TWO>, smem_bytes<true>());
+        default: return occupancy(k_transport<DT, kPass1, TWO>, smem_bytes<true>());
     }
 }
 
-template <int DT>
+template <int DT, bool TWO>
 cudaError_t launch_dt(const TransportArgs& a, int mode, int blocks, cudaStream_t st) {
     switch (mode) {
-        case kFwdVoxel: return launch_mode<DT, kFwdVoxel>(a, blocks, st);
-        case kFwdClassic: return launch_mode<DT, kFwdClassic>(a, blocks, st);
-        case kPass2: return launch_mode<DT, kPass2>(a, blocks, st);
-        case kPass2W: return launch_mode<DT, kPass2W>(a, blocks, st);
-        case kPass1C: return launch_mode<DT, kPass1C>(a, blocks, st);
-        case kPass2C: return launch_mode<DT, kPass2C>(a, blocks, st);
-        default: return launch_mode<DT, kPass1>(a, blocks, st);
+        case kFwdVoxel: return launch_mode<DT, kFwdVoxel, TWO>(a, blocks, st);
+        case kFwdClassic: return launch_mode<DT, kFwdClassic, TWO>(a, blocks, st);
+        case kPass2: return launch_mode<DT, kPass2, TWO>(a, blocks, st);
+        case kPass2W: return launch_mode<DT, kPass2W, TWO>(a, blocks, st);
+        case kPass1C: return launch_mode<DT, kPass1C, TWO>(a, blocks, st);
+        case kPass2C: return launch_mode<DT, kPass2C, TWO>(a, blocks, st);
+        default: return launch_mode<DT, kPass1, TWO>(a, blocks, st);
     }
+}
+
+template <bool TWO>
+cudaError_t launch_species(const TransportArgs& a, int dtype, int mode, int blocks, cudaStream_t st) {
+    return dtype == 0 ? launch_dt<0, TWO>(a, mode, blocks, st)
+                      : (dtype == 1 ? launch_dt<1, TWO>(a, mode, blocks, st) : launch_dt<2, TWO>(a, mode, blocks, st));
 }
 
 }  // namespace
 
-int transport_blocks_per_sm(int dtype, int mode) {
-    static int cache[3][7] = {{0}};
-    if (cache[dtype][mode]) return cache[dtype][mode];
-    const int n = dtype == 0 ? occupancy_mode<0>(mode) : (dtype == 1 ? occupancy_mode<1>(mode) : occupancy_mode<2>(mode));
-    cache[dtype][mode] = n;
-    return n;
+int transport_blocks_per_sm(int dtype, int mode, bool two) {
+    static int cache[2][3][7] = {{{0}}};
+    int& c = cache[two ? 1 : 0][dtype][mode];
+    if (c) return c;
+    if (two)
+        c = dtype == 0 ? occupancy_mode<0, true>(mode)
+                       : (dtype == 1 ? occupancy_mode<1, true>(mode) : occupancy_mode<2, true>(mode));
+    else
+        c = dtype == 0 ? occupancy_mode<0, false>(mode)
+                       : (dtype == 1 ? occupancy_mode<1, false>(mode) : occupancy_mode<2, false>(mode));
+    return c;
 }
 
 cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int mode, int blocks,
                              cudaStream_t st) {
     (void)g;
-    return dtype == 0 ? launch_dt<0>(a, mode, blocks, st)
-                      : (dtype == 1 ? launch_dt<1>(a, mode, blocks, st) : launch_dt<2>(a, mode, blocks, st));
+    return a.beta_air ? launch_species<true>(a, dtype, mode, blocks, st)
+                      : launch_species<false>(a, dtype, mode, blocks, st);
 }
 
 cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st) {
@@ -964,7 +1025,8 @@ cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st) {
 
 cudaError_t launch_event_adjoint(const mst_grid* g, const TransportArgs& a, int dtype, cudaStream_t st) {
     (void)dtype;
-    k_event_adjoint<<<g->sm_count * 8, kTB, 0, st>>>(a);
+    if (a.beta_air) k_event_adjoint<true><<<g->sm_count * 8, kTB, 0, st>>>(a);
+    else k_event_adjoint<false><<<g->sm_count * 8, kTB, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -241,6 +241,17 @@ def homogeneous(shape, value: float) -> np.ndarray:
     return np.full(int(np.prod(shape)), float(value))
 
 
+def air_profile(shape, h, beta0: float, scale_height: float = 8000.0, origin_z: float = 0.0) -> np.ndarray:
+    """Air (Rayleigh) extinction beta0 exp(-z / scale_height) at each voxel centre's altitude z,
+    flattened x fastest. The molecular scattering coefficient of sea-level air is about 0.0116
+    1/km at 550 nm and scales as wavelength^-4; the test scenes raise it so that events on
+    air and on aerosol are both frequent."""
+    nx, ny, nz = (int(s) for s in shape)
+    z = origin_z + (np.arange(nz) + 0.5) * float(h[2])
+    col = beta0 * np.exp(-z / scale_height)
+    return np.ascontiguousarray(np.broadcast_to(col[:, None, None], (nz, ny, nx)).ravel(), dtype=np.float64)
+
+
 # --------------------------------------------------------------------------------------------
 # named workloads
 

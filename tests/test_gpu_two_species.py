@@ -1,0 +1,224 @@
+"""Two-species medium on the GPU (Sec. 2; Sec. 2.1.2 steps iv-vi): air molecules (Rayleigh,
+Eq. Pray, sampled by Eq. thetaREY) beside the aerosol field, the particle of each event drawn
+from beta_air / beta, against the oracle on the same Philox streams: forward L and images, the
+full gradient w.r.t. the aerosol field (stored events, replay, classic estimator), and the
+reduction to one species when the air field is zero."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import dev, f32_scene, gpu_hashes, max_rel, need_gpu, record, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    return need_gpu()
+
+
+def _scene(aerosol=True, n_photons=30_000):
+    """The 16^3 blob scene with an air column of 2 1/km at the ground and an 8 km scale height
+    (about 170 times sea-level air at 550 nm, so that a good share of the events is on air)."""
+    sc, p = synth.cfg_blobs16(n_photons)
+    sc = f32_scene(sc if aerosol else sc.with_beta(np.zeros(sc.nvox)))
+    air = synth.air_profile(sc.shape, sc.h, 2.0 * synth.KM).astype(np.float32).astype(np.float64)
+    return dataclasses.replace(sc, beta_air=air), p.replace(albedo_air=0.97)
+
+
+def _grid(m, sc, p):
+    grid = m.Grid.from_scene(sc)
+    grid.set_air(dev(sc.beta_air, np.float32), p.albedo_air)
+    return grid
+
+
+def _skip(m, grid, sc, p, beta):
+    """Photons whose GPU path checksum differs from the oracle's (FP32 vs FP64 near a voxel face)."""
+    h_gpu = gpu_hashes(m, grid, beta, m.make_params(p), p.n_photons)
+    h_or = oracle.render(sc, p, want_L=False, hashes=True)["hash"]
+    skip = (h_gpu != h_or).astype(np.uint8)
+    assert skip.mean() < 2e-3, skip.mean()
+    return skip
+
+
+@pytest.mark.parametrize("case", ["air+aerosol", "air only"])
+def test_two_species_forward(m, case):
+    sc, p = _scene(aerosol=case == "air+aerosol")
+    grid = _grid(m, sc, p)
+    beta = dev(sc.beta, np.float32)
+    skip = _skip(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render(beta, m.make_params(p), images=True, L=True)
+    st = grid.stats()
+    grid.set_debug(None, None)
+    ref = oracle.render(sc, p, skip=skip)
+    _, T = oracle.transmittance(sc)   # through the total extinction
+    img_ref = oracle.images(sc, ref["L"], T)
+    Lr = ref["L"]
+    eL = max_rel(out["L"].cpu().numpy(), Lr, 1e-3 * np.abs(Lr).max())
+    eI = max_rel(out["images"].cpu().numpy(), img_ref, 1e-3 * np.abs(img_ref).max())
+    record(f"two_species_forward[{case}]", diverged_frac=skip.mean(), L_max_rel=eL, images_max_rel=eI)
+    assert eL < 1e-4 and eI < 1e-4, (eL, eI)
+    rs = ref["stats"]
+    for k in ["events", "traced", "escaped_n"]:
+        assert st[k] == rs[k], (k, st[k], rs[k])
+    # absorbed weight: albedo 0.99 on aerosol, 0.97 on air, per event
+    assert abs(st["absorbed"] - rs["absorbed"]) <= 1e-5 * rs["launched"], (st["absorbed"], rs["absorbed"])
+
+
+def _grad_inputs(sc, p):
+    meas = oracle.forward_images(sc, p.replace(seed=4))[0]
+    guess = synth.smoothed(sc.beta, sc.shape, 0.3).astype(np.float32).astype(np.float64)
+    mask = (np.arange(sc.n_pix) % 7 != 3).astype(np.uint8)
+    return sc.with_beta(guess), meas, mask
+
+
+@pytest.mark.parametrize("estimator,memory", [("voxel", "stored"), ("voxel", "replay"), ("classic", "replay")])
+def test_two_species_full_gradient(m, estimator, memory):
+    """dE/dbeta_aerosol: every flight's free-flight score, 1/beta_aerosol at aerosol events only,
+    the LOS transmittance through the total extinction and the regulariser on the aerosol."""
+    sc, p = _scene()
+    sc, meas, mask = _grad_inputs(sc, p)
+    grid = _grid(m, sc, p)
+    if memory == "replay":
+        grid.set_replay_memory(0)
+    beta = dev(sc.beta, np.float32)
+    skip = _skip(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render_grad(beta, m.make_params(p, grad_mode="full", estimator=estimator, reg_eta=0.05),
+                           dev(meas, np.float64), dev(mask, np.uint8))
+    st = grid.stats()
+    grid.set_debug(None, None)
+    ref = oracle.full_grad(sc, p, meas, mask, eta=0.05, skip=skip, classic=estimator == "classic")
+    img, ri = out["images"].cpu().numpy(), ref["images"]
+    # Classic estimator: an event within FP32 rounding of a pixel edge may be counted in the
+    # neighbouring pixel; with air at the floor cameras one such event changes a faint pixel by
+    # 1e-6 of the brightest (a 1e-5 m camera shift moves the FP64 oracle's image the same way).
+    # Pixel assignment is not unique there, so per pixel only those above 1 % of the brightest
+    # are compared, and the whole image in relative L2.
+    floor = (1e-2 if estimator == "classic" else 1e-3) * np.abs(ri).max()
+    ei = max_rel(img, ri, floor)
+    e2 = rel_l2(img, ri)
+    el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
+    eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    record(f"two_species_full_gradient[{estimator},{memory}]", diverged_frac=skip.mean(), images_max_rel=ei,
+           images_rel_l2=e2, loss_rel=el, grad_rel_l2=eg)
+    if memory == "stored":
+        assert st["events_stored"] == st["events"] > 0
+    else:
+        assert st["events_stored"] == 0
+    assert ei < 2e-4 and e2 < 1e-4 and el < 1e-4 and eg < 1e-3, (ei, e2, el, eg)
+
+
+def test_zero_air_field_is_one_species(m):
+    """An all-zero air field gives every event to the aerosol: the same L as one species, and
+    the same gradient with the collision score 1/beta added at the event instead of in the
+    flight (two FP32 atomics instead of one)."""
+    sc, p = _scene()
+    sc, meas, mask = _grad_inputs(sc, p)
+    beta = dev(sc.beta, np.float32)
+    g1 = m.Grid.from_scene(sc)
+    g2 = m.Grid.from_scene(sc)
+    g2.set_air(dev(np.zeros(sc.nvox), np.float32), 0.5)  # the air albedo never applies
+    mp = m.make_params(p, grad_mode="full")
+    a = g1.render(beta, mp, images=False, L=True)["L"].cpu().numpy()
+    b = g2.render(beta, mp, images=False, L=True)["L"].cpu().numpy()
+    eL = max_rel(b, a, 1e-3 * np.abs(a).max())
+    args = (beta, mp, dev(meas, np.float64), dev(mask, np.uint8))
+    ga = g1.render_grad(*args)
+    gb = g2.render_grad(*args)
+    el = abs(ga["loss"].item() - gb["loss"].item()) / abs(ga["loss"].item())
+    eg = rel_l2(gb["grad"].cpu().numpy(), ga["grad"].cpu().numpy())
+    record("two_species_zero_air", L_max_rel=eL, loss_rel=el, grad_rel_l2=eg)
+    assert eL < 1e-5 and el < 1e-6 and eg < 1e-5, (eL, el, eg)
+
+
+@pytest.mark.parametrize("entry", ["render_grad", "surrogate_grad"])
+def test_two_species_surrogate(m, entry):
+    """The paper's surrogate (Eq. divCost1 with j fixed) in the two-species medium:
+    j = L / (beta_aer + beta_air), L = j (beta_aer + beta_air), the LOS through the total, the
+    regulariser on the aerosol; against the oracle's surrogate given the total reference field."""
+    sc, p = _scene()
+    truth = sc
+    sc, meas, mask = _grad_inputs(sc, p)
+    grid = _grid(m, sc, p)
+    beta = dev(sc.beta, np.float32)
+    mp = m.make_params(p, grad_mode="surrogate", conditioning="inv_count", reg_eta=0.05)
+    if entry == "render_grad":
+        skip = _skip(m, grid, sc, p, beta)
+        grid.set_debug(None, dev(skip, np.uint8))
+        out = grid.render_grad(beta, mp, dev(meas, np.float64), dev(mask, np.uint8))
+        grid.set_debug(None, None)
+        L = oracle.render(sc, p, skip=skip)["L"]
+        ref = oracle.surrogate_grad(sc, L, sc.beta + sc.beta_air, meas, mask, "inv_count", eta=0.05)
+    else:
+        L_ref = oracle.render(truth, p)["L"]
+        out = grid.surrogate_grad(beta, dev(L_ref, np.float64), dev(truth.beta, np.float32), mp,
+                                  dev(meas, np.float64), dev(mask, np.uint8))
+        ref = oracle.surrogate_grad(sc, L_ref, truth.beta + truth.beta_air, meas, mask, "inv_count", eta=0.05)
+    ei = max_rel(out["images"].cpu().numpy(), ref["images"], 1e-3 * np.abs(ref["images"]).max())
+    el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
+    eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    record(f"two_species_surrogate[{entry}]", images_max_rel=ei, loss_rel=el, grad_rel_l2=eg)
+    assert ei < 1e-4 and el < 1e-4 and eg < 1e-3, (ei, el, eg)
+
+
+def test_two_species_bmc_rejected_and_air_reset(m):
+    sc, p = _scene(n_photons=2000)
+    grid = _grid(m, sc, p)
+    beta = dev(sc.beta, np.float32)
+    with pytest.raises(m.MSTError, match="UNSUPPORTED|one species"):
+        grid.render_bmc(beta, m.make_params(p), 4)
+    with pytest.raises(m.MSTError):
+        grid.set_air(dev(sc.beta_air, np.float32), 1.5)
+    grid.set_air(None)  # back to one species
+    grid.render_bmc(beta, m.make_params(p), 4)
+
+
+@pytest.mark.parametrize("mode", ["full", "surrogate"])
+def test_rgb_channels_against_oracle(m, mode):
+    """Three colour channels through mst_render_grad_channels (Eq. channelBeta, Eq. Cost,
+    Eq. divCost1) against the oracle's composition: per-channel aerosol cross-section ratios,
+    HG anisotropy and sun irradiance of Sec. 4 (sigma 16.5 : 16.2 : 15.9, g 0.763 / 0.775 /
+    0.786, F 255 : 236 : 224), air scaled as wavelength^-4 from 550 nm to 650 / 450 nm."""
+    sc, p = _scene()
+    sc, _, mask = _grad_inputs(sc, p)
+    beta_G = sc.beta
+    chans = []
+    for mu, (sig, g, F, lam, seed) in enumerate([(16.5, 0.763, 255, 650.0, 3), (16.2, 0.775, 236, 550.0, 5),
+                                                 (15.9, 0.786, 224, 450.0, 7)]):
+        air = (sc.beta_air * (550.0 / lam) ** 4).astype(np.float32).astype(np.float64)
+        pm = p.replace(g=g, sun_irradiance=F / 255.0, seed=seed, albedo_air=0.97)
+        s = sig / 16.2
+        truth = dataclasses.replace(sc, beta=s * synth.cfg_blobs16()[0].beta, beta_air=air)
+        meas = oracle.forward_images(truth, pm.replace(seed=100 + mu))[0]
+        chans.append(dict(params=pm, sigma=s, beta_air=air, meas=meas))
+    grid = m.Grid.from_scene(sc)
+    # photons that FP32 and FP64 send apart in any channel are left out of every channel
+    skip = np.zeros(p.n_photons, np.uint8)
+    for c in chans:
+        b_mu = (c["sigma"] * beta_G).astype(np.float32)  # what the library renders for the channel
+        grid.set_air(dev(c["beta_air"], np.float32), c["params"].albedo_air)
+        h_gpu = gpu_hashes(m, grid, dev(b_mu, np.float32), m.make_params(c["params"]), p.n_photons)
+        sc_mu = dataclasses.replace(sc, beta=c["sigma"] * beta_G, beta_air=c["beta_air"])
+        h_or = oracle.render(sc_mu, c["params"], want_L=False, hashes=True)["hash"]
+        skip |= (h_gpu != h_or).astype(np.uint8)
+    grid.set_air(None)
+    assert skip.mean() < 5e-3, skip.mean()
+    grid.set_debug(None, dev(skip, np.uint8))
+    gch = [dict(params=m.make_params(c["params"], grad_mode=mode, conditioning="inv_count"), sigma=c["sigma"],
+                beta_air=dev(c["beta_air"], np.float32), albedo_air=c["params"].albedo_air,
+                meas=dev(c["meas"], np.float64)) for c in chans]
+    out = grid.render_grad_channels(dev(beta_G, np.float32), gch, dev(mask, np.uint8), eta=0.05)
+    grid.set_debug(None, None)
+    ref = oracle.channels_grad(sc, beta_G, chans, mask, eta=0.05, skip=skip, surrogate=mode == "surrogate",
+                               conditioning="inv_count")
+    el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
+    eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    ei = max(max_rel(a.cpu().numpy(), b, 1e-3 * np.abs(b).max()) for a, b in zip(out["images"], ref["images"]))
+    record(f"rgb_channels[{mode}]", diverged_frac=skip.mean(), images_max_rel=ei, loss_rel=el, grad_rel_l2=eg)
+    assert ei < 2e-4 and el < 1e-4 and eg < 1e-3, (ei, el, eg)
+    grid.render_bmc(dev(beta_G, np.float32), m.make_params(p), 2)  # the handle is back to one species

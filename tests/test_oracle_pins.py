@@ -731,6 +731,54 @@ def test_two_species_gradient_along_the_aerosol(orc):
 
 
 # ------------------------------------------------------------------------------------------
+# colour channels (Eq. channelBeta, Eq. Cost, Eq. divCost1)
+
+
+def _channel_case(orc):
+    import dataclasses
+    sc, p = synth.cfg_blobs16(3000)
+    air = synth.air_profile(sc.shape, sc.h, 2.0 * synth.KM)
+    sc = dataclasses.replace(sc, beta_air=air)
+    p = p.replace(albedo_air=0.97)
+    meas = orc.forward_images(sc, p.replace(seed=4))[0]
+    b = synth.smoothed(sc.beta, sc.shape, 0.3)
+    return sc, p, air, meas, b
+
+
+@pytest.mark.parametrize("surrogate", [False, True])
+def test_channels_reparametrisation(orc, surrogate):
+    """A channel with sigma = 2 at beta_ref = b / 2 renders the same medium as the one-channel
+    problem at b: the same loss, and by the chain rule through Eq. channelBeta twice the
+    gradient w.r.t. the aerosol field (a dropped or inverted sigma fails here)."""
+    import dataclasses
+    sc, p, air, meas, b = _channel_case(orc)
+    sb = dataclasses.replace(sc, beta=b)
+    if surrogate:
+        r0 = orc.surrogate_grad(sb, orc.render(sb, p)["L"], b + air, meas)
+    else:
+        r0 = orc.full_grad(sb, p, meas)
+    r1 = orc.channels_grad(sc, b / 2, [dict(params=p, sigma=2.0, beta_air=air, meas=meas)], surrogate=surrogate)
+    assert abs(r1["loss"] - r0["loss"]) <= 1e-12 * r0["loss"]
+    assert np.allclose(r1["grad"], 2.0 * r0["grad"], rtol=1e-10, atol=1e-12 * np.abs(r0["grad"]).max())
+    assert np.allclose(r1["images"][0], r0["images"], rtol=1e-12, atol=0)
+
+
+def test_channels_sum_and_single_regulariser(orc):
+    """Two identical channels: twice the one-channel loss and gradient, with eta Psi(beta_ref)
+    counted once (Eq. Cost), not once per channel."""
+    import dataclasses
+    sc, p, air, meas, b = _channel_case(orc)
+    eta = 0.1
+    r0 = orc.full_grad(dataclasses.replace(sc, beta=b), p, meas)
+    ch = dict(params=p, sigma=1.0, beta_air=air, meas=meas)
+    r2 = orc.channels_grad(sc, b, [ch, ch], eta=eta)
+    psi, dpsi = orc.laplacian(dataclasses.replace(sc, beta_air=None), b)
+    assert psi > 0
+    assert abs(r2["loss"] - (2 * r0["loss"] + eta * psi)) <= 1e-12 * r2["loss"]
+    assert np.allclose(r2["grad"], 2 * r0["grad"] + eta * dpsi, rtol=1e-10, atol=1e-12 * np.abs(r2["grad"]).max())
+
+
+# ------------------------------------------------------------------------------------------
 # sharding and threading: the photon-id split does not change the result
 
 
