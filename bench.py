@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
     ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
-    ap.add_argument("--study", default=None, choices=["precision", "recon", "bmc", "classic"],
+    ap.add_argument("--study", default=None, choices=["precision", "recon", "bmc", "classic", "species"],
                     help="FP16/BF16 brick forms against FP32 at equal photon count (prints one JSON line)")
     return ap.parse_args()
 
@@ -142,12 +142,13 @@ def cpu_baseline(sc, p, meas, n_sample):
     oracle.build()
     q = p.replace(n_photons=int(n_sample), n_photons_total=int(n_sample))
     dt, segs = oracle_step(sc, q, meas)
+    dt1, segs1 = oracle_step(sc, q, meas, nthreads=1)
     cores = os.cpu_count()
     return {"value": segs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"cumulus64 scene, {int(n_sample)} photons forward + full gradient incl. all deterministic "
                       f"stages in full (LOS, images, back-projection, LOS adjoint), FP64, OpenMP over {cores} "
-                      f"threads; {dt:.2f} s",
-            "step_s": dt}
+                      f"threads; {dt:.2f} s (1 thread: {dt1:.2f} s)",
+            "step_s": dt, "value_1_core": segs1 / dt1}
 
 
 def run_reference(args):
@@ -522,6 +523,64 @@ def run_bmc_study(args):
     return 0
 
 
+def run_species_study(args):
+    """Two-species medium and colour channels at the benchmark scale (cumulus64, 1e8 photons per
+    channel, forward + full gradient): one species; air at the sea-level molecular scattering of
+    550 nm (0.0116 1/km, 8 km scale height); air 100 times denser; and three RGB channels through
+    mst_render_grad_channels (Sec. 4 cross-section ratios, g and irradiance; air scaled as
+    wavelength^-4). Measured images come from a seed-4 render of each medium. Prints one JSON
+    line with CUDA-event times (3 calls after 1 warm-up) and the forward work."""
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(0)
+    n = int(args.photons)
+    sc, p = synth.cfg_cumulus64(n)
+    beta = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=3):
+        fn()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    air0 = synth.air_profile(sc.shape, sc.h, 0.0116 * synth.KM)
+    out = {"study": "species", "workload": "cumulus64, 9 in-situ 128x128 cameras", "photons_per_channel": n}
+    for name, scale in (("one_species", None), ("air_550nm", 1.0), ("air_550nm_x100", 100.0)):
+        grid = m.Grid.from_scene(sc)
+        if scale is not None:
+            air = torch.from_numpy((air0 * scale).astype(np.float32)).cuda()
+            grid.set_air(air, 1.0)
+        meas = grid.render(beta, m.make_params(p, seed=4))["images"]
+        prm = m.make_params(p, grad_mode="full")
+        ms = timed(lambda: grid.render_grad(beta, prm, meas, images=False))
+        st = grid.stats()
+        out[name] = {"ms": ms, "segments": st["segments"], "events": st["events"],
+                     "segments_per_s": st["segments"] / (ms * 1e-3), "events_stored": st["events_stored"],
+                     "air_event_fraction": st["air_events"] / max(st["events"], 1.0)}
+        grid.close()
+    grid = m.Grid.from_scene(sc)
+    chans = []
+    for sig, g, F, lam, seed in ((16.5, 0.763, 255, 650.0, 3), (16.2, 0.775, 236, 550.0, 5),
+                                 (15.9, 0.786, 224, 450.0, 7)):
+        air = torch.from_numpy((air0 * (550.0 / lam) ** 4).astype(np.float32)).cuda()
+        pm = m.make_params(p, g=g, sun_irradiance=F / 255.0, seed=seed, grad_mode="full")
+        grid.set_air(air, 1.0)
+        b_mu = (beta.double() * (sig / 16.2)).float()
+        meas = grid.render(b_mu, m.make_params(p, g=g, sun_irradiance=F / 255.0, seed=100 + seed))["images"]
+        chans.append(dict(params=pm, sigma=sig / 16.2, beta_air=air, albedo_air=1.0, meas=meas))
+    grid.set_air(None)
+    ms = timed(lambda: grid.render_grad_channels(beta, chans, images=False))
+    out["rgb_3_channels"] = {"ms": ms, "ms_per_channel": ms / 3}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_recon_study(args):
     """Reconstruction of the cumulus64 field from its seed-4 images, 1e8 photons per render,
     from beta = 1 1/km everywhere (Sec. 5 loop at the benchmark scale): projected L-BFGS on the
@@ -626,6 +685,8 @@ def main():
         return run_bmc_study(args)
     if args.study == "classic":
         return run_classic_study(args)
+    if args.study == "species":
+        return run_species_study(args)
     if args.workload == "batch16":
         return run_batch(args)
     return run_ours(args)

@@ -66,7 +66,8 @@ enum {
     MST_ST_PIXEL_SEGMENTS = 19, MST_ST_BACKPROJ_SEGMENTS = 20, MST_ST_LOSADJ_SEGMENTS = 21,
     MST_ST_REPLAY_SCATTERS = 22, MST_ST_LOST = 23, /* walks abandoned (non-finite direction); 0 in valid use */
     MST_ST_EVENTS_STORED = 24, /* full gradient: events the forward stored for the adjoint (0: replayed instead) */
-    MST_ST_BMC_PATHS = 25, MST_ST_BMC_EVENTS = 26, MST_ST_BMC_SEGMENTS = 27 /* mst_render_bmc: flight + sun-ray voxels */
+    MST_ST_BMC_PATHS = 25, MST_ST_BMC_EVENTS = 26, MST_ST_BMC_SEGMENTS = 27, /* mst_render_bmc: flight + sun-ray voxels */
+    MST_ST_AIR_EVENTS = 28 /* two-species medium (mst_set_air): forward events whose particle was air */
 };
 
 /* phases timed by the profiler (mst_get_phase_times) */
@@ -169,6 +170,16 @@ int mst_render(mst_grid *g, const float *beta_dev, const mst_params *p, double *
  * gradient needs the voxel estimator. */
 int mst_render_grad(mst_grid *g, const float *beta_dev, const mst_params *p, const double *images_meas_dev,
                     const uint8_t *mask_dev, double *images_dev, double *grad_dev, double *loss_dev, void *stream);
+
+/* Sun mask M_c of Eq. Cost (Sec. 5: pixels around the sun are left out of the loss):
+ * mask_dev[p] = 0 for the pixels whose centre ray (image point (i + 1/2, j + 1/2)) makes an
+ * angle below radius_rad with the direction to the sun (sun_zenith_rad, sun_azimuth_rad as in
+ * mst_params), 1 for the others; the result is the mask_dev argument of mst_render_grad.
+ *   mask_dev [sum W*H] uint8, written. radius_rad in [0, pi]; 0 masks nothing.
+ * The camera axes are held in FP32, so a pixel within ~1e-6 rad of the edge may fall either way.
+ * Returns MST_ERR_INVALID_ARG for a radius outside [0, pi] or non-finite sun angles. */
+int mst_sun_mask(mst_grid *g, double sun_zenith_rad, double sun_azimuth_rad, double radius_rad, uint8_t *mask_dev,
+                 void *stream);
 
 /* LOS transmittance T_c(k) = exp(-tau_c(k)), tau_c = W_c beta, from the centre of voxel k to
  * X_c (Eq. taoKtoc, Eq. Dvc, Eq. bTck, Eq. Tck). T_dev [C][nvox] float. grid_dtype as above. */

@@ -84,6 +84,7 @@ def lib():
         L.or_full_grad.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P, P, P]
         L.or_full_grad_classic.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P, P]
         L.or_bmc_pixel.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P]
+        L.or_sun_mask.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
         _lib = L
     return _lib
 
@@ -313,6 +314,15 @@ def channels_grad(scene, beta_ref, channels, mask=None, eta=0.0, skip=None, nthr
         loss += eta * psi
         grad += eta * dpsi
     return dict(loss=loss, grad=grad, images=imgs)
+
+
+def sun_mask(scene, zenith, azimuth, radius):
+    """M_c of Eq. Cost: uint8 [n_pix], 0 where the pixel's centre ray is within radius of the
+    direction to the sun."""
+    b = _Bound(scene)
+    m = np.zeros(scene.n_pix, np.uint8)
+    lib().or_sun_mask(b.ref, float(zenith), float(azimuth), float(radius), _ptr(m))
+    return m
 
 
 def bmc_pixel(scene, params, cam: int, i: int, j: int, n: int):

@@ -788,6 +788,27 @@ void or_ray_counts(const or_scene *s, double *Q) {
 }
 
 /* ----------------------------------------------------------------------------------------- */
+/* sun mask M_c of Eq. Cost: 0 for the pixels whose centre ray lies within radius of the      */
+/* direction to the sun, 1 elsewhere                                                         */
+
+void or_sun_mask(const or_scene *s, double zenith, double azimuth, double radius, uint8_t *mask) {
+    const double to_sun[3] = {sin(zenith) * cos(azimuth), sin(zenith) * sin(azimuth), cos(zenith)};
+    long off = 0;
+    for (int c = 0; c < s->n_cams; ++c) {
+        const int w = s->cam_w[c], h = s->cam_h[c];
+        for (int j = 0; j < h; ++j)
+            for (int i = 0; i < w; ++i) {
+                double d[3];
+                pixel_dir(s, c, i + 0.5, j + 0.5, d);
+                const double cosang = d[0] * to_sun[0] + d[1] * to_sun[1] + d[2] * to_sun[2];
+                const double ang = acos(cosang > 1.0 ? 1.0 : (cosang < -1.0 ? -1.0 : cosang));
+                mask[off + (long)j * w + i] = ang < radius ? 0 : 1;
+            }
+        off += (long)w * h;
+    }
+}
+
+/* ----------------------------------------------------------------------------------------- */
 /* regulariser: Psi = || W Lap beta ||^2 with the 6-neighbour graph Laplacian and W diagonal */
 /* in altitude (the scene's reg_wz per layer; identity when it is NULL)                      */
 

@@ -33,13 +33,14 @@ NSTATS = 32
 STAT_NAMES = ["esc_xm", "esc_xp", "esc_ym", "esc_yp", "esc_zm", "esc_zp", "absorbed", "rr_killed", "rr_gained",
               "forced", "events", "segments", "capped", "escaped_n", "launched", "traced", "replay_segments",
               "replay_events", "los_segments", "pixel_segments", "backproj_segments", "losadj_segments",
-              "replay_scatters", "lost", "events_stored", "bmc_paths", "bmc_events", "bmc_segments"]
+              "replay_scatters", "lost", "events_stored", "bmc_paths", "bmc_events", "bmc_segments",
+              "air_events"]
 EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy", "mst_render", "mst_render_grad",
            "mst_transmittance", "mst_form_images", "mst_surrogate_grad", "mst_ray_counts", "mst_regularizer",
            "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
            "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
            "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory", "mst_render_bmc",
-           "mst_set_reg_weights", "mst_set_air", "mst_render_grad_channels"]
+           "mst_set_reg_weights", "mst_set_air", "mst_render_grad_channels", "mst_sun_mask"]
 PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine", "replay2",
           "replay_list", "event_adjoint", "bmc"]
 
@@ -95,6 +96,7 @@ def _load():
     L.mst_set_replay_memory.argtypes = [P, ctypes.c_uint64]
     L.mst_set_reg_weights.argtypes = [P, P]
     L.mst_set_air.argtypes = [P, P, ctypes.c_double]
+    L.mst_sun_mask.argtypes = [P, D, D, D, P, P]
     L.mst_render_grad_channels.argtypes = [P, P, I, P, P, D, P, P, P]
     L.mst_render_bmc.argtypes = [P, P, P, ctypes.c_uint32, P, P, P]
     L.mst_get_stats.argtypes = [P, P]
@@ -261,6 +263,14 @@ class Grid:
                                            _ptr(meas), _ptr(mask), _ptr(img), _ptr(grad), _ptr(loss),
                                            _stream(stream)), "mst_surrogate_grad")
         return dict(loss=loss, grad=grad, images=img)
+
+    def sun_mask(self, sun_zenith: float, sun_azimuth: float, radius: float, stream=None):
+        """M_c of Eq. Cost: uint8 [n_pix], 0 where the pixel's centre ray is within radius of
+        the direction to the sun."""
+        m = self._new(self.n_pix, torch.uint8)
+        self._check(lib.mst_sun_mask(self._h, float(sun_zenith), float(sun_azimuth), float(radius), _ptr(m),
+                                     _stream(stream)), "mst_sun_mask")
+        return m
 
     def ray_counts(self, stream=None):
         Q = self._new(self.n_cams * self.nvox, torch.float32)

@@ -887,6 +887,17 @@ int mst_surrogate_grad(mst_grid* g, const float* beta, const double* L_ref, cons
     return MST_OK;
 }
 
+int mst_sun_mask(mst_grid* g, double zenith, double azimuth, double radius, uint8_t* mask, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!mask) return fail(g, MST_ERR_INVALID_ARG, "mask is NULL");
+    if (!(radius >= 0.0 && radius <= M_PI)) return fail(g, MST_ERR_INVALID_ARG, "radius must be in [0, pi]");
+    if (!std::isfinite(zenith) || !std::isfinite(azimuth))
+        return fail(g, MST_ERR_INVALID_ARG, "sun angles must be finite");
+    DeviceGuard dg(g->device);
+    MST_CK(launch_sun_mask(g, zenith, azimuth, radius, mask, as_stream(stream)));
+    return MST_OK;
+}
+
 int mst_ray_counts(mst_grid* g, float* Q, void* stream) {
     if (!g) return MST_ERR_INVALID_ARG;
     if (!Q) return fail(g, MST_ERR_INVALID_ARG, "Q is NULL");

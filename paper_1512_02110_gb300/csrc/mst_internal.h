@@ -156,6 +156,8 @@ namespace mst {
 
 // launchers (all enqueue on `st`; return cudaGetLastError())
 cudaError_t launch_stage(const mst_grid* g, const float* beta, const float* air, int dtype, cudaStream_t st);
+cudaError_t launch_sun_mask(const mst_grid* g, double zenith, double azimuth, double radius, uint8_t* mask,
+                            cudaStream_t st);
 cudaError_t launch_add_air(const mst_grid* g, const float* beta, const float* air, float* out, cudaStream_t st);
 cudaError_t launch_channel_beta(const mst_grid* g, const float* ref, double sigma, float* out, cudaStream_t st);
 cudaError_t launch_channel_add(const mst_grid* g, double* grad, double sigma, const double* gmu, double* loss,

@@ -6,6 +6,8 @@
 // Geometry is never stored: every Pi_c and W_c product re-walks its rays through the grid.
 // LOS threads run x-fastest over voxels of one camera, so a warp walks 32 nearly parallel
 // rays toward the same X_c.
+#include <cmath>
+
 #include "mst_internal.h"
 
 namespace mst {
@@ -349,6 +351,30 @@ cudaError_t launch_combine_full(const mst_grid* g, const float* gT, const double
 cudaError_t launch_classic_residual(const mst_grid* g, const double* img, const double* meas, const uint8_t* mask,
                                     double* resid, double* loss, cudaStream_t st) {
     k_classic_resid<<<nblocks(g->total_pix, kTB, 4096), kTB, 0, st>>>(img, meas, mask, resid, loss, g->total_pix);
+    return cudaGetLastError();
+}
+
+// Sun mask M_c of Eq. Cost: 0 where the pixel's centre ray is within `radius` of the direction
+// to the sun (cos of the angle above cos(radius), evaluated in FP64), 1 elsewhere.
+__global__ void k_sun_mask(const CamSet cs, double3 to_sun, double cos_r, uint8_t* __restrict__ mask, int npix) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        const int c = cam_of_pixel(cs, p);
+        const Cam& cm = cs.c[c];
+        const int li = p - cm.pix_off, i = li % cm.w, j = li / cm.w;
+        const double x = (2.0 * (i + 0.5) / cm.w - 1.0) * (double)cm.tx;
+        const double y = (2.0 * (j + 0.5) / cm.h - 1.0) * (double)cm.ty;
+        const double dx = cm.fx + x * cm.rx + y * cm.ux, dy = cm.fy + x * cm.ry + y * cm.uy;
+        const double dz = cm.fz + x * cm.rz + y * cm.uz;
+        const double cosang = (dx * to_sun.x + dy * to_sun.y + dz * to_sun.z) / sqrt(dx * dx + dy * dy + dz * dz);
+        mask[p] = cosang > cos_r ? 0 : 1;
+    }
+}
+
+cudaError_t launch_sun_mask(const mst_grid* g, double zenith, double azimuth, double radius, uint8_t* mask,
+                            cudaStream_t st) {
+    const double3 s = make_double3(std::sin(zenith) * std::cos(azimuth), std::sin(zenith) * std::sin(azimuth),
+                                   std::cos(zenith));
+    k_sun_mask<<<nblocks(g->total_pix, kTB, 4096), kTB, 0, st>>>(g->cams, s, std::cos(radius), mask, g->total_pix);
     return cudaGetLastError();
 }
 

@@ -79,6 +79,22 @@ struct LaneTally {
     }
 };
 
+// A per-thread event counter that exists only when ON (the one-species kernels carry none).
+template <bool ON>
+struct EventCount {
+    unsigned n = 0u;
+    __device__ __forceinline__ void add() { ++n; }
+    __device__ __forceinline__ void flush(double* slot, unsigned lane) const {
+        const unsigned long long s = warp_sumu(n);
+        if (lane == 0u && s) atomicAdd(slot, (double)s);
+    }
+};
+template <>
+struct EventCount<false> {
+    __device__ __forceinline__ void add() {}
+    __device__ __forceinline__ void flush(double*, unsigned) const {}
+};
+
 struct NoTally {
     __device__ __forceinline__ void zero() {}
     __device__ __forceinline__ void add_absorbed(float) {}
@@ -571,6 +587,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
     bool fly = false, dry = false;
     uint32_t wbase = 0u, wend = 0u;
     unsigned segments = 0u, scatters = 0u, events = 0u;
+    EventCount<TWO && !REPLAY> air_events;  // two species: forward events on air
     const uint32_t pool_n = PASS2 ? *A.plist_n : A.n;  // pass 2 walks the list built from pass 1
     if (A.ev_cap) {  // a call whose forward stored its events: one of each pair of kernels works
         const bool fit = *A.ev_count <= A.ev_cap;
@@ -670,6 +687,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                 ++events;
                 const int k = lin_index(A.g, e.ix, e.iy, e.iz);
                 const bool air = TWO && particle_is_air(A, e, k);
+                if (air) air_events.add();
                 const float wgt = (air ? A.albedo_air : A.albedo) * e.I;
                 if (!REPLAY) {
                     e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
@@ -719,6 +737,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
         }
     } else {
         flush_tally(A, t.load(), segments, events, lane);
+        air_events.flush(A.stats + MST_ST_AIR_EVENTS, lane);
     }
 }
 

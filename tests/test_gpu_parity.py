@@ -86,6 +86,26 @@ def test_ray_counts(m):
     assert np.mean(diff == 0) > 0.9995
 
 
+@pytest.mark.parametrize("zen_deg,az,rho_deg", [(0.0, 0.0, 12.0), (20.0, 0.7, 8.0), (30.0, 0.0, 35.0)])
+def test_sun_mask(m, zen_deg, az, rho_deg):
+    """M_c of Eq. Cost: bit-exact with the oracle except for pixels whose centre ray lies within
+    1e-5 rad of the mask edge (the camera axes are FP32 on the device)."""
+    from tests import raygeom as rg
+    sc = f32_scene(synth.cfg_blobs16()[0])
+    zen, rho = math.radians(zen_deg), math.radians(rho_deg)
+    mk = m.Grid.from_scene(sc).sun_mask(zen, az, rho).cpu().numpy()
+    ref = oracle.sun_mask(sc, zen, az, rho)
+    s = np.array([math.sin(zen) * math.cos(az), math.sin(zen) * math.sin(az), math.cos(zen)])
+    ang = np.concatenate([[math.acos(min(1.0, float(np.dot(rg.pixel_dir(sc, c, i + 0.5, j + 0.5), s))))
+                           for j in range(int(sc.cam_h[c])) for i in range(int(sc.cam_w[c]))]
+                          for c in range(sc.n_cams)])
+    far = np.abs(ang - rho) > 1e-5
+    record(f"sun_mask[{zen_deg},{rho_deg}]", masked=int((ref == 0).sum()), near_edge=int((~far).sum()),
+           mismatched_far=int((mk[far] != ref[far]).sum()))
+    assert 0 < (ref == 0).sum() < ref.size
+    assert np.array_equal(mk[far], ref[far])
+
+
 @pytest.mark.parametrize("weighted", [False, True])
 def test_regularizer(m, torch, weighted):
     import dataclasses

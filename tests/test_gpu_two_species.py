@@ -60,11 +60,16 @@ def test_two_species_forward(m, case):
     Lr = ref["L"]
     eL = max_rel(out["L"].cpu().numpy(), Lr, 1e-3 * np.abs(Lr).max())
     eI = max_rel(out["images"].cpu().numpy(), img_ref, 1e-3 * np.abs(img_ref).max())
-    record(f"two_species_forward[{case}]", diverged_frac=skip.mean(), L_max_rel=eL, images_max_rel=eI)
+    record(f"two_species_forward[{case}]", diverged_frac=skip.mean(), L_max_rel=eL, images_max_rel=eI,
+           air_event_fraction=st["air_events"] / st["events"])
     assert eL < 1e-4 and eI < 1e-4, (eL, eI)
     rs = ref["stats"]
     for k in ["events", "traced", "escaped_n"]:
         assert st[k] == rs[k], (k, st[k], rs[k])
+    if case == "air only":  # every event is on air
+        assert st["air_events"] == st["events"] > 0
+    else:
+        assert 0.05 * st["events"] < st["air_events"] < 0.95 * st["events"], (st["air_events"], st["events"])
     # absorbed weight: albedo 0.99 on aerosol, 0.97 on air, per event
     assert abs(st["absorbed"] - rs["absorbed"]) <= 1e-5 * rs["launched"], (st["absorbed"], rs["absorbed"])
 
@@ -126,6 +131,7 @@ def test_zero_air_field_is_one_species(m):
     mp = m.make_params(p, grad_mode="full")
     a = g1.render(beta, mp, images=False, L=True)["L"].cpu().numpy()
     b = g2.render(beta, mp, images=False, L=True)["L"].cpu().numpy()
+    assert g2.stats()["air_events"] == 0 and g2.stats()["events"] > 0
     eL = max_rel(b, a, 1e-3 * np.abs(a).max())
     args = (beta, mp, dev(meas, np.float64), dev(mask, np.uint8))
     ga = g1.render_grad(*args)
@@ -222,3 +228,35 @@ def test_rgb_channels_against_oracle(m, mode):
     record(f"rgb_channels[{mode}]", diverged_frac=skip.mean(), images_max_rel=ei, loss_rel=el, grad_rel_l2=eg)
     assert ei < 2e-4 and el < 1e-4 and eg < 1e-3, (ei, el, eg)
     grid.render_bmc(dev(beta_G, np.float32), m.make_params(p), 2)  # the handle is back to one species
+
+
+def test_two_species_in_a_batch(m):
+    """A graph-captured batch with a two-species scene (full and surrogate gradient) beside a
+    one-species scene: each branch equals its own single call, and replacing the air field
+    re-captures the graph."""
+    import torch
+    sc, p = _scene(n_photons=20_000)
+    sc, meas, mask = _grad_inputs(sc, p)
+    sc1 = dataclasses.replace(sc, beta_air=None)
+    grids = [_grid(m, sc, p), _grid(m, sc, p), m.Grid.from_scene(sc1)]
+    beta = dev(sc.beta, np.float32)
+    md = [dev(meas, np.float64)] * 3
+    params = [m.make_params(p, grad_mode="full"), m.make_params(p, grad_mode="surrogate", conditioning="inv_count"),
+              m.make_params(p, grad_mode="full")]
+    refs = [g.render_grad(beta, q, mm) for g, q, mm in zip(grids, params, md)]
+    batch = m.Batch(grids)
+    for rep in range(2):  # capture, then replay
+        out = batch.render_grad([beta] * 3, params, md)
+        torch.cuda.synchronize()
+        for i, r in enumerate(refs):
+            eg = rel_l2(out["grad"][i].cpu().numpy(), r["grad"].cpu().numpy())
+            el = abs(out["loss"][i].item() - r["loss"].item()) / r["loss"].item()
+            record(f"two_species_batch[{i},rep{rep}]", grad_rel_l2=eg, loss_rel=el)
+            assert eg < 1e-5 and el < 1e-6, (i, rep, eg, el)
+    air2 = dev(2.0 * sc.beta_air, np.float32)
+    grids[0].set_air(air2, p.albedo_air)
+    out = batch.render_grad([beta] * 3, params, md)
+    ref0 = grids[0].render_grad(beta, params[0], md[0])
+    assert rel_l2(out["grad"][0].cpu().numpy(), ref0["grad"].cpu().numpy()) < 1e-5
+    assert abs(out["loss"][0].item() - refs[0]["loss"].item()) > 1e-3 * refs[0]["loss"].item()
+    batch.close()

@@ -731,6 +731,52 @@ def test_two_species_gradient_along_the_aerosol(orc):
 
 
 # ------------------------------------------------------------------------------------------
+# sun mask M_c (Eq. Cost)
+
+
+def test_sun_mask_zenith_sun_is_an_image_plane_disc(orc):
+    """Upward cameras and the sun at zenith: a pixel centre is masked exactly when its
+    image-plane point lies inside the disc of radius tan(rho) (pinhole geometry, no angles)."""
+    sc, _ = synth.cfg_blobs16(10)
+    rho = math.radians(12.0)
+    m = orc.sun_mask(sc, 0.0, 0.0, rho)
+    off = 0
+    for c in range(sc.n_cams):
+        w, h = int(sc.cam_w[c]), int(sc.cam_h[c])
+        tx = math.tan(0.5 * sc.cam_fov[c])
+        ty = tx * h / w
+        i, j = np.meshgrid(np.arange(w) + 0.5, np.arange(h) + 0.5)
+        r = np.hypot((2 * i / w - 1) * tx, (2 * j / h - 1) * ty).ravel()
+        ref = np.where(r < math.tan(rho), 0, 1).astype(np.uint8)
+        far = np.abs(r - math.tan(rho)) > 1e-9
+        assert np.array_equal(m[off:off + w * h][far], ref[far])
+        assert 0 < (ref == 0).sum() < w * h
+        off += w * h
+
+
+def test_sun_mask_oblique_sun_and_limits(orc):
+    """An oblique sun: the masked set equals the pixels whose centre ray makes an angle below
+    rho with the sun direction, the angle taken as atan2(|d x s|, d . s); rho = 0 masks
+    nothing and rho = pi everything."""
+    sc, _ = synth.cfg_blobs16(10)
+    zen, az, rho = math.radians(20.0), 0.7, math.radians(8.0)
+    s = np.array([math.sin(zen) * math.cos(az), math.sin(zen) * math.sin(az), math.cos(zen)])
+    m = orc.sun_mask(sc, zen, az, rho)
+    off = 0
+    for c in range(sc.n_cams):
+        w, h = int(sc.cam_w[c]), int(sc.cam_h[c])
+        dirs = [rg.pixel_dir(sc, c, i + 0.5, j + 0.5) for j in range(h) for i in range(w)]
+        ang = np.array([math.atan2(np.linalg.norm(np.cross(d, s)), float(np.dot(d, s))) for d in dirs])
+        ref = np.where(ang < rho, 0, 1).astype(np.uint8)
+        far = np.abs(ang - rho) > 1e-9
+        assert np.array_equal(m[off:off + w * h][far], ref[far])
+        off += w * h
+    assert (m == 0).sum() > 0
+    assert np.all(orc.sun_mask(sc, zen, az, 0.0) == 1)
+    assert np.all(orc.sun_mask(sc, zen, az, math.pi + 1e-6) == 0)
+
+
+# ------------------------------------------------------------------------------------------
 # colour channels (Eq. channelBeta, Eq. Cost, Eq. divCost1)
 
 
