@@ -560,7 +560,12 @@ def run_species_study(args):
         prm = m.make_params(p, grad_mode="full")
         ms = timed(lambda: grid.render_grad(beta, prm, meas, images=False))
         st = grid.stats()
-        out[name] = {"ms": ms, "segments": st["segments"], "events": st["events"],
+        grid.set_profiling(True)
+        grid.render_grad(beta, prm, meas, images=False)
+        torch.cuda.synchronize()
+        phases = {k: round(v[0], 3) for k, v in grid.phase_times().items() if v[1]}
+        grid.set_profiling(False)
+        out[name] = {"ms": ms, "phase_ms": phases, "segments": st["segments"], "events": st["events"],
                      "segments_per_s": st["segments"] / (ms * 1e-3), "events_stored": st["events_stored"],
                      "air_event_fraction": st["air_events"] / max(st["events"], 1.0)}
         grid.close()

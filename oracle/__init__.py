@@ -85,6 +85,8 @@ def lib():
         L.or_full_grad_classic.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P, P]
         L.or_bmc_pixel.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P]
         L.or_sun_mask.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
+        L.or_particle_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]
+        L.or_particle_uniform.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -160,6 +162,10 @@ def hg_phase(g: float, mu: float) -> float:
 
 def hg_sample(g: float, u: float) -> float:
     return lib().or_hg_sample(g, u)
+
+
+def particle_uniform(seed: int, photon: int, event: int) -> float:
+    return lib().or_particle_uniform(int(seed), int(photon), int(event))
 
 
 def rayleigh_phase(mu: float) -> float:

@@ -155,8 +155,18 @@ double or_rayleigh_sample(double u) {
 }
 
 /* Step iv with two species: the event's particle is air with probability beta_air / beta in
- * its voxel (Sec. 2.1.2), drawn from Philox stream word 0xFFFFFFFF of the event. */
-#define TYPE_STREAM 0xFFFFFFFFu
+ * its voxel (Sec. 2.1.2). Its uniform comes from the bits the event's draws leave unused: each
+ * of the four uniforms of or_u01 takes the top 23 bits of its word, so the low 9 bits of words
+ * 0 and 1 and the low 5 bits of word 2 form a 23-bit integer m, independent of the other four
+ * draws, and u = (2m + 1) / 2^24 like or_u01. */
+double or_particle_uniform(uint64_t seed, uint64_t photon, uint32_t event) {
+    uint32_t ctr[4] = {(uint32_t)photon, (uint32_t)(photon >> 32), event, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    or_philox4x32_10(ctr, key, x);
+    const uint32_t m = (x[0] & 511u) | ((x[1] & 511u) << 9) | ((x[2] & 31u) << 18);
+    return (2.0 * (double)m + 1.0) * (1.0 / 16777216.0);
+}
 
 /* New direction at polar cosine ct and azimuth phi about d. The transverse frame is
  * e2 = normalize(a x d), e1 = e2 x d with reference axis a = z, or a = x when |d_z| >= 0.9. */
@@ -504,11 +514,7 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
         c->stats[ST_EVENTS] += 1.0;
         /* step iv: the particle (one species unless the scene has air) and its albedo */
         int air = 0;
-        if (s->beta_air) {
-            double ut[4];
-            draws4(P->seed, p, s_ev, TYPE_STREAM, ut);
-            air = ut[0] * s->beta[k] < s->beta_air[k];
-        }
+        if (s->beta_air) air = or_particle_uniform(P->seed, p, s_ev) * s->beta[k] < s->beta_air[k];
         const double alb = air ? P->albedo_air : P->albedo;
         /* local estimates toward every camera (Eq. Lcupdate; Eq. fle) */
         double w = 0.0;

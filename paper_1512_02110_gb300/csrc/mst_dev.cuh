@@ -71,6 +71,14 @@ __device__ __forceinline__ float4 draws(uint2 key, uint64_t photon, uint32_t eve
     return make_float4(u01(x.x), u01(x.y), u01(x.z), u01(x.w));
 }
 
+// The raw Philox block of a counter, and its four uniforms: draws() in two steps, for callers
+// that also use the low bits u01 leaves unused.
+__device__ __forceinline__ uint4 draw_bits(uint2 key, uint64_t photon, uint32_t event) {
+    return philox4x32_10(make_uint4((uint32_t)photon, (uint32_t)(photon >> 32), event, 0u), key);
+}
+
+__device__ __forceinline__ float4 u01x4(uint4 x) { return make_float4(u01(x.x), u01(x.y), u01(x.z), u01(x.w)); }
+
 // ------------------------------------------------------------------------------------------
 // Henyey-Greenstein (Eq. Phg) and its inverse CDF (Eq. thetaHG, squared reading).
 
@@ -304,25 +312,37 @@ __device__ __forceinline__ bool ray_start(const Geo& g, const Cam& c, float3 d, 
         p = make_float3(c.lx, c.ly, c.lz);
         return true;
     }
+    // Clip to the grid box in a frame at the corner of the camera's voxel (cell index c.i, which
+    // may lie outside the grid): the camera is at offset c.l there and the faces the ray enters
+    // through are near, so the entry point keeps FP32's resolution however far the grid extends
+    // (grid-local coordinates would carry ~1 mm of rounding 10 km from the origin).
+    const int ci[3] = {c.ix, c.iy, c.iz}, nn[3] = {g.nx, g.ny, g.nz};
+    const float oo[3] = {c.lx, c.ly, c.lz}, dd[3] = {d.x, d.y, d.z}, hh[3] = {g.hx, g.hy, g.hz};
     float tn = 0.f, tf = CUDART_INF_F;
-    const float oo[3] = {c.px, c.py, c.pz}, dd[3] = {d.x, d.y, d.z}, hi[3] = {g.ex, g.ey, g.ez};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+        const float lo = -(float)ci[a] * hh[a], hi = (float)(nn[a] - ci[a]) * hh[a];
         if (dd[a] == 0.f) {
-            if (oo[a] < 0.f || oo[a] > hi[a]) return false;
+            if (oo[a] < lo || oo[a] > hi) return false;
         } else {
-            float t1 = (0.f - oo[a]) / dd[a], t2 = (hi[a] - oo[a]) / dd[a];
+            float t1 = (lo - oo[a]) / dd[a], t2 = (hi - oo[a]) / dd[a];
             if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
             tn = fmaxf(tn, t1);
             tf = fminf(tf, t2);
         }
     }
     if (!(tn < tf)) return false;
-    const float3 e = make_float3(c.px + tn * d.x, c.py + tn * d.y, c.pz + tn * d.z);
-    ix = coord_vox(e.x, g.hx, g.nx);
-    iy = coord_vox(e.y, g.hy, g.ny);
-    iz = coord_vox(e.z, g.hz, g.nz);
-    p = make_float3(e.x - (float)ix * g.hx, e.y - (float)iy * g.hy, e.z - (float)iz * g.hz);
+    int iv[3];
+    float pv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float e = oo[a] + tn * dd[a];  // entry point relative to the camera voxel's corner
+        const int k = min(max(ci[a] + (int)floorf(e / hh[a]), 0), nn[a] - 1);
+        iv[a] = k;
+        pv[a] = e - (float)(k - ci[a]) * hh[a];
+    }
+    ix = iv[0]; iy = iv[1]; iz = iv[2];
+    p = make_float3(pv[0], pv[1], pv[2]);
     return true;
 }
 

@@ -135,8 +135,9 @@ __device__ __forceinline__ void launch_photon(const TransportArgs& A, Photon& ph
 // on, kCollided on a collision (ph.p and the voxel updated) or the exit face 0..5
 // (kWalkOverflow if the walk was abandoned). With S != 0 it also scatters the score of the
 // flight into the gradient tile: -S * length in every voxel crossed and S * (1/beta - length)
-// in the collision voxel (with two species, TWO, only -S * length there: the event adds
-// S / beta_aer once it knows the particle).
+// in the collision voxel. With two species (TWO) the collision voxel's term waits for the
+// particle: the flight keeps its partial length there in ph.tau (spent once the flight has
+// collided) and the event adds S * ([aerosol] / beta_aer - length) in one atomic.
 constexpr int kCollided = -2;
 
 template <int DT, bool TWO>
@@ -153,8 +154,12 @@ __device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, W
         ph.iy = w.iy;
         ph.iz = w.iz;
         if (S != 0.f) {
-            atomicAdd(A.gacc + w.lin, S * ((TWO ? 0.f : 1.f / b) - l));
-            ++nsc;
+            if constexpr (TWO) {
+                ph.tau = l;
+            } else {
+                atomicAdd(A.gacc + w.lin, S * (1.f / b - l));
+                ++nsc;
+            }
         }
         return kCollided;
     }
@@ -175,14 +180,15 @@ __device__ __forceinline__ float cam_cosine(const TransportArgs& A, const Photon
 }
 
 // Step iv with two species (Sec. 2): the event's particle is air with probability
-// beta_air / (beta_air + beta_aer) in its voxel, drawn from Philox stream word 0xFFFFFFFF of
-// the event. The test u (beta_air + beta_aer) < beta_air runs in FP64 on the FP32 fields and the
-// 24-bit uniform, so it takes the same branch as an FP64 evaluation of the same expression; an
-// empty aerosol voxel always gives air (u < 1), an empty air voxel always aerosol.
-constexpr uint32_t kTypeStream = 0xFFFFFFFFu;
-
-__device__ __forceinline__ bool particle_is_air(const TransportArgs& A, const Photon& e, int k) {
-    const float u = draws(A.key, e.id, e.s, kTypeStream).x;
+// beta_air / (beta_air + beta_aer) in its voxel. The uniform comes from the event's own Philox
+// block x (the one its scattering draws use): u01 takes the top 23 bits of each word, so the low
+// 9 bits of x.x and x.y and the low 5 bits of x.z give a 23-bit m, independent of those draws,
+// and u = (2m + 1) / 2^24 (exact in FP32). The test u (beta_air + beta_aer) < beta_air runs in
+// FP64 on the FP32 fields, so it takes the same branch as an FP64 evaluation of the same
+// expression; an empty aerosol voxel always gives air (u < 1), an empty air voxel aerosol.
+__device__ __forceinline__ bool particle_is_air(const TransportArgs& A, uint4 x, int k) {
+    const uint32_t m = (x.x & 511u) | ((x.y & 511u) << 9) | ((x.z & 31u) << 18);
+    const float u = __uint2float_rn(2u * m + 1u) * 5.9604644775390625e-08f;
     const double ba = (double)__ldg(A.beta_air + k);
     return (double)u * (ba + (double)__ldg(A.beta_aer + k)) < ba;
 }
@@ -299,8 +305,9 @@ __device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon
 
 // step v (albedo weighting, Russian roulette) and step vi (new direction by the particle's
 // phase function, next free path). Returns 0 to continue or the termination code.
-template <typename TallyT>
-__device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, TallyT& t, bool air) {
+// PRE: x is the event's Philox block, already drawn (two species: the particle came from it).
+template <bool PRE, typename TallyT>
+__device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, TallyT& t, bool air, uint4 x) {
     const float alb = air ? A.albedo_air : A.albedo;
     t.add_absorbed((1.f - alb) * ph.I);
     ph.I *= alb;
@@ -314,7 +321,7 @@ __device__ __forceinline__ int after_event(const TransportArgs& A, Photon& ph, T
         t.add_capped();
         return 5;
     }
-    const float4 u = draws(A.key, ph.id, ph.s);
+    const float4 u = PRE ? u01x4(x) : draws(A.key, ph.id, ph.s);
     if (ph.I < A.rr_below) {
         if (u.z < A.rr_survival) {
             t.add_gained(ph.I * (A.inv_rr_survival - 1.f));
@@ -441,6 +448,26 @@ __device__ __forceinline__ void get(const Stack<NW>& q, int slot, const Transpor
         nev = 0u;
         acc = 0.0;
     }
+}
+
+// Two species: the event's Philox block waits in the event's own stack slot (popped, so free
+// until the next trip pushes events) while the local estimate runs, instead of in registers.
+// Volatile, so the compiler reloads it rather than keeping the words live.
+template <int NW>
+__device__ __forceinline__ void stash_block(const Stack<NW>& q, int slot, uint4 x) {
+    volatile uint32_t* b = q.w + slot;
+    const int c = q.cap;
+    b[0] = x.x;
+    b[c] = x.y;
+    b[2 * c] = x.z;
+    b[3 * c] = x.w;
+}
+
+template <int NW>
+__device__ __forceinline__ uint4 unstash_block(const Stack<NW>& q, int slot) {
+    const volatile uint32_t* b = q.w + slot;
+    const int c = q.cap;
+    return make_uint4(b[0], b[c], b[2 * c], b[3 * c]);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -686,7 +713,14 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                 e.s += 1u;
                 ++events;
                 const int k = lin_index(A.g, e.ix, e.iy, e.iz);
-                const bool air = TWO && particle_is_air(A, e, k);
+                const int slot = ev_n - 1 - (int)lane;
+                uint4 xb = make_uint4(0u, 0u, 0u, 0u);  // two species: the event's Philox block
+                bool air = false;
+                if constexpr (TWO) {
+                    const uint4 x = draw_bits(A.key, e.id, e.s);
+                    air = particle_is_air(A, x, k);
+                    stash_block(evq, slot, x);
+                }
                 if (air) air_events.add();
                 const float wgt = (air ? A.albedo_air : A.albedo) * e.I;
                 if (!REPLAY) {
@@ -695,7 +729,8 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                         store_event(A, ev_base + lane, e, wgt, air);
                     if (MODE == 0) le_voxel(A, e, wgt, k, air);
                     else le_classic<DT, 0>(A, e, wgt, nullptr, air);
-                    term = after_event(A, e, t, air);
+                    if constexpr (TWO) xb = unstash_block(evq, slot);
+                    term = after_event<TWO>(A, e, t, air, xb);
                     if (term) finish_photon(A, e, term);
                 } else {
                     float we;
@@ -704,19 +739,21 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                     else we = le_adjoint(A, e, wgt, k, air);
                     if (PASS1) {
                         eacc += (double)we;
-                        term = after_event(A, e, t, air);
+                        if constexpr (TWO) xb = unstash_block(evq, slot);
+                        term = after_event<TWO>(A, e, t, air, xb);
                         if (term) {
                             A.wbuf[e.idx - A.out_base] = eacc;
                             A.nevbuf[e.idx - A.out_base] = e.s;
                         }
                     } else {
                         const float S = (float)eacc;  // the score weight of the flight that ended here
-                        if (TWO && !air && S != 0.f) {  // two species: aerosol collision, S / beta_aer
-                            atomicAdd(A.gacc + k, S / __ldg(A.beta_aer + k));
+                        if (TWO && S != 0.f) {  // two species: the collision voxel's term (see flight_step)
+                            atomicAdd(A.gacc + k, S * ((air ? 0.f : 1.f / __ldg(A.beta_aer + k)) - e.tau));
                             ++scatters;
                         }
                         eacc -= (double)we;
-                        term = e.s == enev ? 1 : after_event(A, e, t, air);  // stop at pass 1's last event
+                        if constexpr (TWO) xb = unstash_block(evq, slot);
+                        term = e.s == enev ? 1 : after_event<TWO>(A, e, t, air, xb);  // stop at pass 1's last event
                     }
                 }
             }

@@ -48,6 +48,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(mst_params, n_photons), offsetof(mst_params, seed),
          offsetof(mst_params, max_order), offsetof(mst_params, reg_eta));
   printf("%zu %zu\n", offsetof(mst_camera, width), offsetof(mst_camera, fov_x_rad));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(mst_channel), offsetof(mst_channel, beta_air_dev),
+         offsetof(mst_channel, sigma_ratio), offsetof(mst_channel, images_meas_dev), offsetof(mst_channel, images_dev));
   return 0;
 }
 """
@@ -64,6 +66,9 @@ int main(void) {
     P = pkg.Params
     assert offs == [P.n_photons.offset, P.seed.offset, P.max_order.offset, P.reg_eta.offset]
     assert coffs == [pkg.Camera.width.offset, pkg.Camera.fov_x_rad.offset]
+    ch = [int(x) for x in lines[3].split()]
+    C = pkg.Channel
+    assert ch == [ctypes.sizeof(C), C.beta_air.offset, C.sigma_ratio.offset, C.images_meas.offset, C.images.offset]
 
 
 def test_defaults_and_version(pkg):
@@ -89,6 +94,11 @@ def test_create_grid_validates_before_touching_a_device(pkg):
         (good, 17, 10),
         (good, 1, 0),
         (good, 1, 65),
+        # past the packed voxel index (11 + 11 + 10 bits) or 2^30 voxels
+        (pkg.GridDesc(2049, 4, 4, 10.0, 10.0, 10.0, (ctypes.c_double * 3)(0, 0, 0)), 1, 10),
+        (pkg.GridDesc(4, 2049, 4, 10.0, 10.0, 10.0, (ctypes.c_double * 3)(0, 0, 0)), 1, 10),
+        (pkg.GridDesc(4, 4, 1025, 10.0, 10.0, 10.0, (ctypes.c_double * 3)(0, 0, 0)), 1, 10),
+        (pkg.GridDesc(2048, 2048, 257, 10.0, 10.0, 10.0, (ctypes.c_double * 3)(0, 0, 0)), 1, 10),
     ]
     for desc, nc, nr in bad_cases:
         assert L.mst_create_grid(ctypes.byref(desc), nc, cam, nr, ctypes.byref(h)) == -1
@@ -99,6 +109,9 @@ def test_create_grid_validates_before_touching_a_device(pkg):
     L.mst_destroy(None)  # NULL-safe
     assert L.mst_render(None, None, None, None, None, None) == -1
     assert L.mst_sync(None) == -1
+    assert L.mst_set_air(None, None, 1.0) == -1
+    assert L.mst_sun_mask(None, 0.0, 0.0, 0.1, None, None) == -1
+    assert L.mst_render_grad_channels(None, None, 1, None, None, 0.0, None, None, None) == -1
 
 
 def test_package_refuses_without_library(tmp_path):

@@ -648,6 +648,26 @@ def test_rayleigh_phase_and_sampler(orc):
     assert abs(cs.mean()) < 1e-9 and abs((cs ** 2).mean() - 0.4) < 1e-6
 
 
+def test_particle_uniform_is_uniform_and_independent_of_the_event_draws(orc):
+    """The particle's uniform (the low bits the event's four 23-bit uniforms leave unused) is
+    uniform on (0, 1), its bits are those of the Philox block the same counter gives, and it is
+    uncorrelated with the event's other draws (HG cosine, azimuth, roulette, free path)."""
+    from scipy import stats
+    seed, n = 0x1234_5678_9ABC, 200_000
+    us, draws = np.empty(n), np.empty((n, 4))
+    for t in range(n):
+        photon, event = 7919 * t + 13, 1 + t % 37
+        us[t] = orc.particle_uniform(seed, photon, event)
+        x = orc.philox4x32_10([photon & 0xFFFFFFFF, photon >> 32, event, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        draws[t] = [orc.u01(w) for w in x]
+        if t < 64:
+            m = (x[0] & 511) | ((x[1] & 511) << 9) | ((x[2] & 31) << 18)
+            assert us[t] == (2 * m + 1) / 2 ** 24
+    assert stats.kstest(us, "uniform").pvalue > 1e-3
+    for c in range(4):
+        assert abs(np.corrcoef(us, draws[:, c])[0, 1]) < 5.0 / math.sqrt(n)
+
+
 def _slab_two_species(F, alb_air, alb_aer, g, b_air, b_aer, H, mu0, sun, d):
     """Single scattering by a homogeneous two-species slab: the one-species closed form with
     the scattering phase replaced by the species-weighted sum (b_air alb_air P_Ray + b_aer alb_aer
