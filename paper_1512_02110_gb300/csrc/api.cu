@@ -188,6 +188,9 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
         a.evrec = g->evrec;
         a.ev_cap = g->ev_cap;
         a.ev_count = g->ev_count;
+        a.ch_next = g->ch_next;
+        a.warp_head = g->warp_head;
+        g->ev_warps = (uint32_t)b_fwd * kTransportWarps;
         MST_CK(cudaMemsetAsync(g->ev_count, 0, sizeof(unsigned long long), st));
     }
     for (int l = 0; l < nl; ++l) {
@@ -244,14 +247,18 @@ int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
     a.ev_count = g->ev_count;
     a.wseq = g->wseq;
     a.evoff = g->evoff;
+    a.ch_next = g->ch_next;
+    a.warp_head = g->warp_head;
+    a.n_warps = g->ev_warps;
     a.first_id = p->photon_offset;
     a.out_base = 0;
     a.n = (uint32_t)n;
-    MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * 2, st));
+    MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * 3, st));
     MST_CK(cudaMemsetAsync(g->wbuf, 0, sizeof(double) * n, st));
     {
         Phase ph(g, MST_PH_EVENT_ADJOINT, st);
         MST_CK(launch_event_offsets(g, a.n, st));
+        a.ticket = g->tickets + 2;  // the adjoint's blocks take the forward warps' lists from it
         MST_CK(launch_event_adjoint(g, a, p->grid_dtype, st));
     }
     const bool two = g->air != nullptr;
@@ -312,7 +319,7 @@ int ensure_replay(mst_grid* g, uint64_t n) {
 // storing call offered (read without a wait once its copy has landed), within the budget. Never
 // fails the call: too many photons, no budget, a failed allocation or a call inside a stream
 // capture (no allocation there) all mean W by replay.
-bool ensure_records(mst_grid* g, uint64_t n) {
+bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
     const uint64_t rec_bytes = (uint64_t)kEventBytes;
     if (g->capturing || n > kRecordMaxPhotons || g->rec_budget < rec_bytes * 1024) return false;
     if (!g->ev_count) {
@@ -334,19 +341,38 @@ bool ensure_records(mst_grid* g, uint64_t n) {
         }
     }
     const uint64_t max_ev = std::min<uint64_t>(g->rec_budget / rec_bytes, 0xFFFFFFFFull);  // 32-bit w_s slots
-    uint64_t want = g->ev_last ? g->ev_last + g->ev_last / 4 : 6 * n;
+    // the forward reserves slots in per-warp chunks: one chunk per resident warp of headroom
+    const uint64_t tails = (uint64_t)g->sm_count * transport_blocks_per_sm(dtype, 0, g->air != nullptr) *
+                           kTransportWarps * kEventChunk;
+    uint64_t want = (g->ev_last ? g->ev_last + g->ev_last / 4 : 6 * n) + tails;
     want = std::min<uint64_t>(std::max<uint64_t>(want, 1024), max_ev);
+    if (!g->warp_head) {  // the forward's warps: at most kMaxWarpsPerSm per SM
+        if (cudaMalloc(&g->warp_head, sizeof(uint32_t) * (size_t)g->sm_count * kMaxWarpsPerSm) != cudaSuccess) {
+            cudaGetLastError();
+            g->warp_head = nullptr;
+            return false;
+        }
+    }
+    if ((uint64_t)g->sm_count * transport_blocks_per_sm(dtype, 0, g->air != nullptr) * kTransportWarps >
+        (uint64_t)g->sm_count * kMaxWarpsPerSm)
+        return false;
     if (g->evrec && g->ev_cap >= want) return true;
     cudaFree(g->evrec);
     cudaFree(g->wseq);
+    cudaFree(g->ch_next);
     g->evrec = nullptr;
     g->wseq = nullptr;
+    g->ch_next = nullptr;
     g->ev_cap = 0;
-    if (cudaMalloc(&g->evrec, want * kEventWords * 4) != cudaSuccess || cudaMalloc(&g->wseq, want * 4) != cudaSuccess) {
+    if (cudaMalloc(&g->evrec, want * kEventWords * 4) != cudaSuccess || cudaMalloc(&g->wseq, want * 4) != cudaSuccess ||
+        cudaMalloc(&g->ch_next, sizeof(uint32_t) * (want / kEventChunk + 1)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(g->evrec);
+        cudaFree(g->wseq);
+        cudaFree(g->ch_next);
         g->evrec = nullptr;
         g->wseq = nullptr;
+        g->ch_next = nullptr;
         return false;
     }
     g->ev_cap = want;
@@ -385,6 +411,8 @@ void free_all(mst_grid* g) {
         if (p) cudaFree(p);
     cudaFree(g->evrec);
     cudaFree(g->wseq);
+    cudaFree(g->ch_next);
+    cudaFree(g->warp_head);
     cudaFree(g->evoff);
     cudaFree(g->reg_wz);
     cudaFree(g->ch_beta);
@@ -730,7 +758,7 @@ int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const 
     // full gradient: the forward stores its events when they can be held (W without pass 1)
     bool stored = false;
     if (p->grad_mode == MST_GRAD_FULL) {
-        stored = ensure_records(g, p->n_photons);
+        stored = ensure_records(g, p->n_photons, p->grid_dtype);
         if (stored && ensure_replay(g, p->n_photons) != MST_OK) {
             stored = false;
             g->err.clear();
@@ -1056,8 +1084,10 @@ int mst_set_replay_memory(mst_grid* g, uint64_t bytes) {
         MST_CK(cudaDeviceSynchronize());
         cudaFree(g->evrec);
         cudaFree(g->wseq);
+        cudaFree(g->ch_next);
         g->evrec = nullptr;
         g->wseq = nullptr;
+        g->ch_next = nullptr;
         g->ev_cap = 0;
     }
     return MST_OK;

@@ -25,6 +25,10 @@ constexpr uint64_t kReplayChunk = 1ull << 24;    // photons per replay pass-1 / 
 constexpr uint64_t kRecordMaxPhotons = 1ull << 27;
 constexpr int kEventWords = 10;  // packed voxel, offset (3), incoming direction (3), albedo * weight, photon, event number
 constexpr int kEventBytes = kEventWords * 4 + 4;  // the record and its w_s
+constexpr unsigned kEventChunk = 256;  // record slots a warp of the forward reserves at a time
+constexpr int kTransportWarps = 8;     // warps per transport block (256 threads)
+constexpr uint32_t kEndChunk = 0xFFFFFFFFu;  // end of a warp's chunk list
+constexpr int kMaxWarpsPerSm = 64;     // warp_head entries per SM (the forward runs 24)
 constexpr uint64_t kDefaultRecordBytes = 24ull << 30;
 constexpr uint64_t kFoldSweep = 1ull << 21;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
@@ -67,6 +71,9 @@ struct TransportArgs {
     unsigned long long ev_cap;     // capacity of evrec in events (0: no events stored)
     unsigned long long* ev_count;  // events offered for storage; > ev_cap: they did not fit
     float* wseq;               // [ev_cap] w_s of the stored events, photon after photon (event order)
+    uint32_t* ch_next;         // [ev_cap / kEventChunk] next chunk of the same forward warp (kEndChunk: none)
+    uint32_t* warp_head;       // [warps of the forward launch] each warp's first chunk (kEndChunk: none)
+    uint32_t n_warps;          // warps of the forward launch that stored the events
     const uint32_t* evoff;     // [photons of the call] each photon's first slot in wseq
     const ScoreRec* plist;     // [kReplayChunk] photons with W != 0 (replay pass 2)
     const unsigned int* plist_n;  // entries in plist
@@ -127,6 +134,9 @@ struct mst_grid {
     const float* air = nullptr;   // [nvox] air extinction (borrowed, mst_set_air), NULL: one species
     double albedo_air = 1.0;      // single-scattering albedo of air
     const float* beta_in = nullptr;  // the running call's beta (the aerosol field with air)
+    uint32_t* ch_next = nullptr;  // [ev_cap / kEventChunk] chunk lists of the stored events
+    uint32_t* warp_head = nullptr;  // [sm_count * kMaxWarpsPerSm] first chunk of each forward warp
+    uint32_t ev_warps = 0;        // warps of the last storing forward launch
     float* btot = nullptr;        // [nvox] two species: beta + beta_air in FP32, written by the staging
     float* btot_ref = nullptr;    // [nvox] two species: beta_ref + beta_air (mst_surrogate_grad)
     float* ch_beta = nullptr;     // [nvox] mst_render_grad_channels: the channel's aerosol field

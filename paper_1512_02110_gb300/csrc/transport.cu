@@ -373,6 +373,14 @@ __device__ __forceinline__ void store_event(const TransportArgs& A, unsigned lon
 // neither stack can overflow.
 
 constexpr int kScoreTile = 4096;   // photons per block in the list kernels
+// Stored events are written in per-warp chunks of kEvChunk slots (one reservation on the global
+// counter per chunk). A warp's photons come from its own ticket batches, so a chunk holds the
+// events of a few dozen photons, and the adjoint that walks a chunk finds their W and w_s slots
+// together in cache instead of scattered over all photons in flight. The buffer keeps one chunk
+// per resident warp of headroom for the chunks' unused tails.
+constexpr unsigned kEvChunk = kEventChunk;
+static_assert(kTB / 32 == kTransportWarps, "transport block size");
+constexpr uint32_t kNoPhoton = 0xFFFFFFFFu;  // photon word of a chunk's unused tail slots
 constexpr int kEvCap = 64;
 constexpr int kRdCap = 64;
 // Voxels a flying lane advances per loop trip, and minimum resident blocks per SM (register
@@ -596,6 +604,9 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
     const Stack<NW> evq{smem + warp * NW * (kEvCap + kRdCap), kEvCap};
     const Stack<NW> rdq{smem + warp * NW * (kEvCap + kRdCap) + NW * kEvCap, kRdCap};
     int ev_n = 0, rd_n = 0;  // warp-uniform stack heights
+    unsigned long long ch_base = ~0ull;  // forward storing events: the warp's current chunk (none yet) ...
+    unsigned ch_fill = kEvChunk;         // ... and its slots in use
+    const uint32_t gwarp = blockIdx.x * (kTB / 32) + warp;  // the warp's chunk list
 
     // photon tallies: forward render only, one shared-memory slot per thread after the stacks
     typename std::conditional<REPLAY, NoTally, LaneTally>::type t;
@@ -703,10 +714,27 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
             uint32_t enev = 0u;
             double eacc = 0.0;
             int term = -1;  // -1 idle lane, 0 goes on, > 0 ended
-            unsigned long long ev_base = 0ull;  // forward storing events: this round's first slot
+            unsigned long long ev_slot = 0ull;  // forward storing events: this lane's record slot
             if (MODE == kFwdVoxel && A.ev_cap) {
-                if (lane == 0u) ev_base = atomicAdd(A.ev_count, (unsigned long long)n);
-                ev_base = __shfl_sync(kFull, ev_base, 0);
+                // the round's slots continue the warp's chunk and spill into a new one
+                unsigned long long nb = 0ull;
+                if (ch_fill + (unsigned)n > kEvChunk) {  // a new chunk, linked after the warp's last one
+                    if (lane == 0u) {
+                        nb = atomicAdd(A.ev_count, (unsigned long long)kEvChunk);
+                        const uint32_t nc = (uint32_t)(nb / kEvChunk);
+                        if (ch_base == ~0ull) A.warp_head[gwarp] = nc;
+                        else if (ch_base + kEvChunk <= A.ev_cap) A.ch_next[ch_base / kEvChunk] = nc;
+                    }
+                    nb = __shfl_sync(kFull, nb, 0);
+                }
+                const unsigned f = ch_fill + lane;
+                ev_slot = f < kEvChunk ? ch_base + f : nb + (f - kEvChunk);
+                if (ch_fill + (unsigned)n > kEvChunk) {
+                    ch_base = nb;
+                    ch_fill = ch_fill + (unsigned)n - kEvChunk;
+                } else {
+                    ch_fill += (unsigned)n;
+                }
             }
             if ((int)lane < n) {
                 get(evq, ev_n - 1 - (int)lane, A, e, enev, eacc);
@@ -725,8 +753,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                 const float wgt = (air ? A.albedo_air : A.albedo) * e.I;
                 if (!REPLAY) {
                     e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
-                    if (MODE == kFwdVoxel && A.ev_cap && ev_base + lane < A.ev_cap)
-                        store_event(A, ev_base + lane, e, wgt, air);
+                    if (MODE == kFwdVoxel && A.ev_cap && ev_slot < A.ev_cap) store_event(A, ev_slot, e, wgt, air);
                     if (MODE == 0) le_voxel(A, e, wgt, k, air);
                     else le_classic<DT, 0>(A, e, wgt, nullptr, air);
                     if constexpr (TWO) xb = unstash_block(evq, slot);
@@ -775,6 +802,15 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
     } else {
         flush_tally(A, t.load(), segments, events, lane);
         air_events.flush(A.stats + MST_ST_AIR_EVENTS, lane);
+        if (MODE == kFwdVoxel && A.ev_cap) {  // close the warp's list; its last chunk's tail holds no event
+            if (ch_base == ~0ull) {
+                if (lane == 0u) A.warp_head[gwarp] = kEndChunk;
+            } else {
+                if (lane == 0u && ch_base + kEvChunk <= A.ev_cap) A.ch_next[ch_base / kEvChunk] = kEndChunk;
+                for (unsigned f = ch_fill + lane; f < kEvChunk; f += 32u)
+                    if (ch_base + f < A.ev_cap) A.evrec[8ull * A.ev_cap + ch_base + f] = kNoPhoton;
+            }
+        }
     }
 }
 
@@ -783,27 +819,43 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
 // added to W in FP64. Does nothing when the events did not fit (pass 1 then walks the paths).
 template <bool TWO>
 __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
-    const unsigned long long cnt = *A.ev_count;
+    const unsigned long long cnt = *A.ev_count;  // reserved slots: whole chunks
     if (cnt > A.ev_cap) return;
     const unsigned long long C = A.ev_cap;
-    const unsigned long long stride = (unsigned long long)gridDim.x * kTB;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * kTB + threadIdx.x; i < cnt; i += stride) {
-        const uint32_t* r = A.evrec + i;
-        const uint32_t v = r[0];
-        Photon e;
-        e.ix = (int)(v & 2047u);
-        e.iy = (int)((v >> 11) & 2047u);
-        e.iz = (int)(v >> 22);
-        e.p = make_float3(__uint_as_float(r[C]), __uint_as_float(r[2 * C]), __uint_as_float(r[3 * C]));
-        e.d = make_float3(__uint_as_float(r[4 * C]), __uint_as_float(r[5 * C]), __uint_as_float(r[6 * C]));
-        const uint32_t sw = r[9 * C];  // event number, particle in bit 31
-        const float w = le_adjoint(A, e, __uint_as_float(r[7 * C]), lin_index(A.g, e.ix, e.iy, e.iz),
-                                   TWO && (sw >> 31) != 0u);
-        const uint32_t j = r[8 * C];
-        A.wseq[A.evoff[j] + (sw & 0x7FFFFFFFu) - 1u] = w;  // event s of photon j: slot evoff[j] + s - 1
-        if (w != 0.f) atomicAdd(A.wbuf + j, (double)w);
+    unsigned long long stored = 0ull;
+    // A block follows one forward warp's chunks in the order the warp wrote them (lists taken
+    // from a ticket): a photon's events lie in one or two neighbouring chunks of its warp, so its
+    // W, offset and w_s slots are used while they are still cached.
+    __shared__ uint32_t list;
+    for (;;) {
+        if (threadIdx.x == 0) list = atomicAdd(A.ticket, 1u);
+        __syncthreads();
+        const uint32_t gw = list;
+        __syncthreads();
+        if (gw >= A.n_warps) break;
+        for (uint32_t ch = A.warp_head[gw]; ch != kEndChunk; ch = A.ch_next[ch]) {
+            for (unsigned q = threadIdx.x; q < kEvChunk; q += kTB) {
+                const uint32_t* r = A.evrec + (unsigned long long)ch * kEvChunk + q;
+                const uint32_t j = r[8 * C];
+                if (j == kNoPhoton) continue;
+                ++stored;
+                const uint32_t v = r[0];
+                Photon e;
+                e.ix = (int)(v & 2047u);
+                e.iy = (int)((v >> 11) & 2047u);
+                e.iz = (int)(v >> 22);
+                e.p = make_float3(__uint_as_float(r[C]), __uint_as_float(r[2 * C]), __uint_as_float(r[3 * C]));
+                e.d = make_float3(__uint_as_float(r[4 * C]), __uint_as_float(r[5 * C]), __uint_as_float(r[6 * C]));
+                const uint32_t sw = r[9 * C];  // event number, particle in bit 31
+                const float w = le_adjoint(A, e, __uint_as_float(r[7 * C]), lin_index(A.g, e.ix, e.iy, e.iz),
+                                           TWO && (sw >> 31) != 0u);
+                A.wseq[A.evoff[j] + (sw & 0x7FFFFFFFu) - 1u] = w;  // event s of photon j: slot evoff[j] + s - 1
+                if (w != 0.f) atomicAdd(A.wbuf + j, (double)w);
+            }
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.stats + MST_ST_EVENTS_STORED, (double)cnt);
+    stored = warp_sumu(stored);
+    if ((threadIdx.x & 31u) == 0u && stored) atomicAdd(A.stats + MST_ST_EVENTS_STORED, (double)stored);
 }
 
 // Exclusive prefix sum of the photons' event counts (three passes over tiles of kScanTile):
