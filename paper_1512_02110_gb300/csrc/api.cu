@@ -258,6 +258,8 @@ int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
     {
         Phase ph(g, MST_PH_EVENT_ADJOINT, st);
         MST_CK(launch_event_offsets(g, a.n, st));
+        // the counts are spent: the adjoint leaves in them each photon's last event with w_s != 0
+        MST_CK(cudaMemsetAsync(g->nevbuf, 0, sizeof(uint32_t) * n, st));
         a.ticket = g->tickets + 2;  // the adjoint's blocks take the forward warps' lists from it
         MST_CK(launch_event_adjoint(g, a, p->grid_dtype, st));
     }

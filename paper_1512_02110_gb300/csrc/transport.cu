@@ -816,7 +816,8 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
 
 // w_s of every event the forward stored, instead of replay pass 1: the same arithmetic
 // (le_adjoint) on the same event state, written to the photon's slot in wseq for pass 2 and
-// added to W in FP64. Does nothing when the events did not fit (pass 1 then walks the paths).
+// added to W in FP64; nevbuf (zeroed after the slot scan) receives each photon's last event with
+// w_s != 0. Does nothing when the events did not fit (pass 1 then walks the paths).
 template <bool TWO>
 __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
     const unsigned long long cnt = *A.ev_count;  // reserved slots: whole chunks
@@ -849,8 +850,14 @@ __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
                 const uint32_t sw = r[9 * C];  // event number, particle in bit 31
                 const float w = le_adjoint(A, e, __uint_as_float(r[7 * C]), lin_index(A.g, e.ix, e.iy, e.iz),
                                            TWO && (sw >> 31) != 0u);
-                A.wseq[A.evoff[j] + (sw & 0x7FFFFFFFu) - 1u] = w;  // event s of photon j: slot evoff[j] + s - 1
-                if (w != 0.f) atomicAdd(A.wbuf + j, (double)w);
+                const uint32_t s = sw & 0x7FFFFFFFu;
+                A.wseq[A.evoff[j] + s - 1u] = w;  // event s of photon j: slot evoff[j] + s - 1
+                if (w != 0.f) {
+                    atomicAdd(A.wbuf + j, (double)w);
+                    // S_j = sum_{s >= j} w_s vanishes past the photon's last event with w_s != 0,
+                    // so pass 2 stops there (its list and its walks use this in place of the count)
+                    atomicMax(A.nevbuf + j, s);
+                }
             }
         }
     }
