@@ -7,6 +7,7 @@
 // time and advances it one free flight plus one event per loop trip; lanes whose photon has
 // ended take a new photon id from a warp-local pool that lane 0 refills from a global ticket,
 // so the warp stays full until the chunk runs dry.
+#include <algorithm>
 #include <type_traits>
 
 #include "mst_internal.h"
@@ -367,10 +368,13 @@ __device__ __forceinline__ void store_event(const TransportArgs& A, unsigned lon
 // ------------------------------------------------------------------------------------------
 // Per-warp photon stacks in shared memory (structure of arrays: lane i touches word i, so
 // pushes and pops are free of bank conflicts). A warp holds at most 32 flying photons, fewer
-// than kEvCap queued events (events are processed 32 at a time as soon as 32 are queued) and
-// a ready stack: new photons are launched only when the ready stack is empty, so right after a
-// launch a warp holds 32 flying + at most 31 queued photons and never more than 63 in total;
-// neither stack can overflow.
+// than 32 queued events once a round of events is done (events are processed 32 at a time as
+// soon as 32 are queued) and a ready stack: new photons are launched only when the ready stack
+// is empty, so right after a launch a warp holds 32 flying + at most 31 queued photons and never
+// more than 63 in total. The event and ready stacks therefore share one array of kSlots = 64
+// slots, the events growing up from slot 0 and the ready photons down from slot 63: together
+// they never hold more than 63. (Two separate 64-slot stacks took 49 KB of shared memory per
+// block of the forward, which the SM's L1 gives up to hold the extinction grid.)
 
 constexpr int kScoreTile = 4096;   // photons per block in the list kernels
 // Stored events are written in per-warp chunks of kEvChunk slots (one reservation on the global
@@ -381,8 +385,7 @@ constexpr int kScoreTile = 4096;   // photons per block in the list kernels
 constexpr unsigned kEvChunk = kEventChunk;
 static_assert(kTB / 32 == kTransportWarps, "transport block size");
 constexpr uint32_t kNoPhoton = 0xFFFFFFFFu;  // photon word of a chunk's unused tail slots
-constexpr int kEvCap = 64;
-constexpr int kRdCap = 64;
+constexpr int kSlots = 64;
 // Voxels a flying lane advances per loop trip, and minimum resident blocks per SM (register
 // budget), per kernel mode; set from sweeps on the 64^3 cumulus workload.
 constexpr int kStepsForward = 8;
@@ -601,8 +604,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
     extern __shared__ uint32_t smem[];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned warp = threadIdx.x >> 5;
-    const Stack<NW> evq{smem + warp * NW * (kEvCap + kRdCap), kEvCap};
-    const Stack<NW> rdq{smem + warp * NW * (kEvCap + kRdCap) + NW * kEvCap, kRdCap};
+    const Stack<NW> stk{smem + warp * NW * kSlots, kSlots};  // events at slot i, ready photons at kSlots-1-i
     int ev_n = 0, rd_n = 0;  // warp-uniform stack heights
     unsigned long long ch_base = ~0ull;  // forward storing events: the warp's current chunk (none yet) ...
     unsigned ch_fill = kEvChunk;         // ... and its slots in use
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
     // photon tallies: forward render only, one shared-memory slot per thread after the stacks
     typename std::conditional<REPLAY, NoTally, LaneTally>::type t;
     if constexpr (!REPLAY) {
-        float* tb = reinterpret_cast<float*>(smem + (kTB / 32) * NW * (kEvCap + kRdCap));
+        float* tb = reinterpret_cast<float*>(smem + (kTB / 32) * NW * kSlots);
         t.f = tb + threadIdx.x;
         t.u = reinterpret_cast<unsigned*>(tb + 11 * kTB) + threadIdx.x;
     }
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
             const int rank = __popc(empty & lanemask_lt());
             const int take = min(__popc(empty), rd_n);
             if (!fly && rank < take) {
-                get(rdq, rd_n - 1 - rank, A, ph, nev, acc);
+                get(stk, kSlots - rd_n + rank, A, ph, nev, acc);
                 walk_init<true>(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
                 tau = ph.tau;
                 fly = true;
@@ -689,7 +691,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
         const bool collided = fly && r == kCollided;
         const unsigned cmask = __ballot_sync(kFull, collided);
         if (collided) {
-            put(evq, ev_n + __popc(cmask & lanemask_lt()), ph, nev, acc);
+            put(stk, ev_n + __popc(cmask & lanemask_lt()), ph, nev, acc);
             fly = false;
         } else if (fly && r >= 0) {
             if (REPLAY) {
@@ -737,7 +739,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                 }
             }
             if ((int)lane < n) {
-                get(evq, ev_n - 1 - (int)lane, A, e, enev, eacc);
+                get(stk, ev_n - 1 - (int)lane, A, e, enev, eacc);
                 e.s += 1u;
                 ++events;
                 const int k = lin_index(A.g, e.ix, e.iy, e.iz);
@@ -747,7 +749,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                 if constexpr (TWO) {
                     const uint4 x = draw_bits(A.key, e.id, e.s);
                     air = particle_is_air(A, x, k);
-                    stash_block(evq, slot, x);
+                    stash_block(stk, slot, x);
                 }
                 if (air) air_events.add();
                 const float wgt = (air ? A.albedo_air : A.albedo) * e.I;
@@ -756,7 +758,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                     if (MODE == kFwdVoxel && A.ev_cap && ev_slot < A.ev_cap) store_event(A, ev_slot, e, wgt, air);
                     if (MODE == 0) le_voxel(A, e, wgt, k, air);
                     else le_classic<DT, 0>(A, e, wgt, nullptr, air);
-                    if constexpr (TWO) xb = unstash_block(evq, slot);
+                    if constexpr (TWO) xb = unstash_block(stk, slot);
                     term = after_event<TWO>(A, e, t, air, xb);
                     if (term) finish_photon(A, e, term);
                 } else {
@@ -766,7 +768,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                     else we = le_adjoint(A, e, wgt, k, air);
                     if (PASS1) {
                         eacc += (double)we;
-                        if constexpr (TWO) xb = unstash_block(evq, slot);
+                        if constexpr (TWO) xb = unstash_block(stk, slot);
                         term = after_event<TWO>(A, e, t, air, xb);
                         if (term) {
                             A.wbuf[e.idx - A.out_base] = eacc;
@@ -779,7 +781,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                             ++scatters;
                         }
                         eacc -= (double)we;
-                        if constexpr (TWO) xb = unstash_block(evq, slot);
+                        if constexpr (TWO) xb = unstash_block(stk, slot);
                         term = e.s == enev ? 1 : after_event<TWO>(A, e, t, air, xb);  // stop at pass 1's last event
                     }
                 }
@@ -787,7 +789,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
             ev_n -= n;
             __syncwarp();
             const unsigned gmask = __ballot_sync(kFull, term == 0);
-            if (term == 0) put(rdq, rd_n + __popc(gmask & lanemask_lt()), e, enev, eacc);
+            if (term == 0) put(stk, kSlots - 1 - (rd_n + __popc(gmask & lanemask_lt())), e, enev, eacc);
             rd_n += __popc(gmask);
             __syncwarp();
         }
@@ -1055,7 +1057,7 @@ __global__ void k_fold_grad(float* __restrict__ gacc, double* __restrict__ g64, 
 
 template <bool REPLAY>
 constexpr size_t smem_bytes() {
-    return (size_t)(kTB / 32) * Rec<REPLAY>::NW * (kEvCap + kRdCap) * sizeof(uint32_t) +
+    return (size_t)(kTB / 32) * Rec<REPLAY>::NW * kSlots * sizeof(uint32_t) +
            (REPLAY ? 0 : (size_t)kTB * 15 * sizeof(uint32_t));
 }
 
@@ -1063,6 +1065,12 @@ template <typename K>
 int occupancy(K kern, size_t smem) {
     int n = 0;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {   // shared-memory carveout: enough for three blocks (the register budget allows no more), the
+        // rest of the SM's 256 KB to L1, which caches the extinction grid the walks fetch
+        const size_t need = 3 * (smem + 1024);
+        const int pct = (int)std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    }
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kTB, smem) != cudaSuccess || n < 1) n = 1;
     return n;
 }
