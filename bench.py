@@ -425,6 +425,7 @@ def run_batch(args):
     batch = m.Batch(grids)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ms_batch, all_b = _timed(lambda: batch.render_grad(betas, params, meas), args.steps, args.warmup, flush)
+    stored_in_graph = sum(1 for g in grids if g.stats()["events_stored"] > 0)
 
     def sequential():
         for g, b, q, mm in zip(grids, betas, params, meas):
@@ -440,7 +441,8 @@ def run_batch(args):
                       "value": segs / (ms_batch * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
                       "sequential_ms_per_step": ms_seq, "sequential_value": segs / (ms_seq * 1e-3),
-                      "photons_per_step": photons, "segments_per_step": segs, "dtype": "f32", "data": "synthetic",
+                      "photons_per_step": photons, "segments_per_step": segs, "scenes_storing_events_in_graph":
+                      stored_in_graph, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "batch16: 16 scenes 24^3-96^3 x 20 m, blob/fractal fields, albedo "
                                              "0.99-0.999, g 0.75-0.9, sun 0-60 deg, 3-12 cams of 64/128 px, "
                                              f"{args.photons / 10:.0e}-{args.photons:.0e} photons each",

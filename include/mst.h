@@ -343,9 +343,12 @@ int mst_transmittance_noalloc(const mst_grid_desc *grid, int n_cams, const mst_c
  * A batch owns one CUDA graph holding the mst_render_grad sequences of n distinct handles, each
  * on its own branch, so scenes of uneven size overlap on the GPU and the whole batch is one
  * graph launch. The graph is captured on the first call (work is enqueued on internal
- * streams; the handles' conditioning weights are prepared on `stream` first) and replayed
- * while every pointer and parameter is unchanged; any change re-captures it. Results are
- * those of n mst_render_grad calls with the same arguments.
+ * streams; the handles' conditioning weights are prepared on `stream` first, and each
+ * full-gradient handle's event and per-photon buffers are sized for its photons, so that the
+ * graph's forwards store their events as mst_render_grad's do) and replayed while every
+ * pointer, parameter and handle buffer is unchanged; any change, including a buffer a direct
+ * call on one of the handles reallocated, re-captures it. Results are those of n
+ * mst_render_grad calls with the same arguments.
  *   grids: n distinct handles on one device (1 <= n <= MST_MAX_BATCH); the batch does not own
  *          them and must be destroyed before them.
  *   betas[i], params[i], meas[i], masks[i] (masks may be NULL, entries may be NULL),

@@ -229,8 +229,10 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
     }
     if (store_events) {  // the count reaches the host for the next call's sizing, without a wait
         MST_CK(cudaMemcpyAsync(g->ev_seen, g->ev_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        MST_CK(cudaEventRecord(g->ev_seen_ready, st));
-        g->ev_seen_pending = true;
+        if (!g->capturing) {  // a batch graph instead records one event after each launch
+            MST_CK(cudaEventRecord(g->ev_seen_ready, st));
+            g->ev_seen_pending = true;
+        }
     }
     return MST_OK;
 }
@@ -760,10 +762,14 @@ int render_grad_impl(mst_grid* g, const float* beta, const mst_params* p, const 
     // full gradient: the forward stores its events when they can be held (W without pass 1)
     bool stored = false;
     if (p->grad_mode == MST_GRAD_FULL) {
-        stored = ensure_records(g, p->n_photons, p->grid_dtype);
-        if (stored && ensure_replay(g, p->n_photons) != MST_OK) {
-            stored = false;
-            g->err.clear();
+        if (g->capturing) {  // a batch graph: the buffers were sized before the capture
+            stored = g->batch_stored;
+        } else {
+            stored = ensure_records(g, p->n_photons, p->grid_dtype);
+            if (stored && ensure_replay(g, p->n_photons) != MST_OK) {
+                stored = false;
+                g->err.clear();
+            }
         }
     }
     rc = run_photons(g, p, false, nullptr, st, stored);
@@ -1123,6 +1129,8 @@ struct mst_batch {
     std::vector<cudaEvent_t> join;
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> key;
+    cudaEvent_t done = nullptr;  // after the last graph launch: the handles' event counts have landed
+    bool launched = false;
     std::string err;
 };
 
@@ -1135,6 +1143,7 @@ void batch_free(mst_batch* b) {
     for (cudaEvent_t e : b->join)
         if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
     if (b->cap) cudaStreamDestroy(b->cap);
 }
 
@@ -1163,7 +1172,8 @@ int mst_batch_create(int n, mst_grid* const* grids, mst_batch** out) {
     b->grids.assign(grids, grids + n);
     DeviceGuard dg(b->device);
     bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
     b->branch.assign(n, nullptr);
     b->join.assign(n, nullptr);
     for (int i = 0; ok && i < n; ++i)
@@ -1206,20 +1216,47 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
     }
     DeviceGuard dg(b->device);
     cudaStream_t st = as_stream(stream);
-    std::vector<unsigned char> key;
-    for (int i = 0; i < b->n; ++i) {
-        key_add(key, betas[i]);
-        key_add(key, params[i]);
-        key_add(key, meas[i]);
-        key_add(key, masks ? masks[i] : nullptr);
-        key_add(key, images ? images[i] : nullptr);
-        key_add(key, grads[i]);
-        key_add(key, b->grids[i]->dbg_hash);
-        key_add(key, b->grids[i]->dbg_skip);
-        key_add(key, b->grids[i]->air);
-        key_add(key, b->grids[i]->albedo_air);
+    // The graph bakes in the call's pointers and each handle's scratch buffers; any change
+    // (including a buffer a direct call on the handle reallocated) re-captures it.
+    auto make_key = [&]() {
+        std::vector<unsigned char> k;
+        for (int i = 0; i < b->n; ++i) {
+            const mst_grid* g = b->grids[i];
+            key_add(k, betas[i]);
+            key_add(k, params[i]);
+            key_add(k, meas[i]);
+            key_add(k, masks ? masks[i] : nullptr);
+            key_add(k, images ? images[i] : nullptr);
+            key_add(k, grads[i]);
+            key_add(k, g->dbg_hash);
+            key_add(k, g->dbg_skip);
+            key_add(k, g->air);
+            key_add(k, g->albedo_air);
+            key_add(k, g->reg_wz);
+            const void* bufs[] = {g->wbuf, g->nevbuf, g->plist, g->evoff, g->evrec, g->wseq, g->ch_next,
+                                  g->warp_head, g->Qw, g->btot, g->btot_ref};
+            for (const void* q : bufs) key_add(k, q);
+            key_add(k, g->ev_cap);
+            key_add(k, g->batch_stored);
+        }
+        key_add(k, losses);
+        return k;
+    };
+    // A handle whose events overflowed its buffer in the last launch (W then came from replay
+    // pass 1 on the device) gets a buffer for the count it saw; the new buffer re-captures.
+    if (b->launched && cudaEventQuery(b->done) == cudaSuccess) {
+        for (int i = 0; i < b->n; ++i) {
+            mst_grid* g = b->grids[i];
+            if (g->batch_stored && *g->ev_seen > g->ev_cap) {
+                g->ev_last = *g->ev_seen;
+                g->batch_stored = ensure_records(g, params[i].n_photons, params[i].grid_dtype);
+                g->err.clear();
+            }
+        }
+        b->launched = false;
     }
-    key_add(key, losses);
+    cudaGetLastError();  // a query that found the launch still running
+    std::vector<unsigned char> key = make_key();
     if (!b->exec || key != b->key) {
         if (b->exec) {
             cudaGraphExecDestroy(b->exec);
@@ -1236,9 +1273,15 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
                 b->err = g->err;
                 return rc;
             }
+            // full gradient: the forward stores its events in buffers sized here (W without pass 1)
+            g->batch_stored = params[i].grad_mode == MST_GRAD_FULL &&
+                              ensure_records(g, params[i].n_photons, params[i].grid_dtype) &&
+                              ensure_replay(g, params[i].n_photons) == MST_OK;
+            g->err.clear();
             for (int mode = 0; mode < 7; ++mode)
                 transport_blocks_per_sm(params[i].grid_dtype, mode, g->air != nullptr);
         }
+        key = make_key();  // with the buffers as the graph will use them
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             b->err = "stream error before capture";
             return MST_ERR_CUDA;
@@ -1249,7 +1292,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
             return MST_ERR_CUDA;
         }
         int rc = MST_OK;
-        for (int i = 0; i < b->n; ++i) b->grids[i]->capturing = true;  // graph branches replay W
+        for (int i = 0; i < b->n; ++i) b->grids[i]->capturing = true;  // no allocation in the branches
         cudaEventRecord(b->fork, b->cap);
         for (int i = 0; i < b->n && rc == MST_OK; ++i) {
             cudaStreamWaitEvent(b->branch[i], b->fork, 0);
@@ -1279,6 +1322,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
         b->err = "cudaGraphLaunch failed";
         return MST_ERR_CUDA;
     }
+    if (!b->launched && cudaEventRecord(b->done, st) == cudaSuccess) b->launched = true;
     return MST_OK;
 }
 

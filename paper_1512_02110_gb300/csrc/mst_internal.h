@@ -124,6 +124,7 @@ struct mst_grid {
     bool ev_seen_pending = false;
     unsigned long long ev_last = 0;          // events offered by the last storing call whose count arrived
     bool capturing = false;                  // inside a stream capture: no allocation, no event query
+    bool batch_stored = false;               // the batch allocated this handle's event buffers before capture
     uint64_t rec_budget = mst::kDefaultRecordBytes;
     unsigned int* score_cnt = nullptr;  // [2 kScoreBins + 1] list bin counts, bin fill, list length
     double* g64 = nullptr;        // [nvox]

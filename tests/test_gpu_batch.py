@@ -58,6 +58,34 @@ def test_batch_matches_individual_calls(m):
     batch.close()
 
 
+def test_batch_recaptures_when_a_direct_call_reallocates(m):
+    """A direct call with more photons on one of the batch's handles grows its event and
+    per-photon buffers; the next batch call must re-capture (the graph held the old buffers)
+    and still equal the direct calls."""
+    import torch
+    cases = _scenes()[:2]
+    grids = [m.Grid.from_scene(sc) for sc, _ in cases]
+    betas = [dev(synth.smoothed(sc.beta, sc.shape, 0.3), np.float32) for sc, _ in cases]
+    meas = [g.render(dev(sc.beta, np.float32), m.make_params(p, seed=p.seed + 100))["images"]
+            for g, (sc, p) in zip(grids, cases)]
+    params = [m.make_params(p, grad_mode="full") for _, p in cases]
+    batch = m.Batch(grids)
+    batch.render_grad(betas, params, meas)
+    torch.cuda.synchronize()
+    st = grids[0].stats()
+    assert st["events_stored"] == st["events"] > 0  # the graph's forward stored its events
+    big = m.make_params(cases[0][1], grad_mode="full", n_photons=8 * cases[0][1].n_photons)
+    grids[0].render_grad(betas[0], big, meas[0])  # grows scene 0's buffers
+    out = batch.render_grad(betas, params, meas)
+    torch.cuda.synchronize()
+    for i, g in enumerate(grids):
+        ref = g.render_grad(betas[i], params[i], meas[i])
+        eg = rel_l2(out["grad"][i].cpu().numpy(), ref["grad"].cpu().numpy())
+        record(f"batch_recapture[{i}]", grad_rel_l2=eg)
+        assert eg < 1e-5, (i, eg)
+    batch.close()
+
+
 def test_batch_rejects_shared_handles(m):
     sc, _ = synth.cfg_blobs16()
     g = m.Grid.from_scene(f32_scene(sc))
