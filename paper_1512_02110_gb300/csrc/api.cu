@@ -5,6 +5,8 @@
 #include <cstring>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mst_internal.h"
 
 using namespace mst;
@@ -52,15 +54,23 @@ cudaEvent_t prof_event(mst_grid* g) {
     return g->ev_pool[g->ev_next++];
 }
 
+// NVTX range names of the phases (MST_PH_*), for profilers that attach (ncu --nvtx)
+const char* const kPhaseNames[MST_NPHASES] = {"mst:stage",   "mst:transport", "mst:fold",     "mst:los",
+                                              "mst:images",  "mst:backproject", "mst:los_adjoint",
+                                              "mst:replay",  "mst:combine",   "mst:replay2",  "mst:replay_list",
+                                              "mst:event_adjoint", "mst:bmc"};
+
 struct Phase {
     mst_grid* g;
     int phase;
     cudaStream_t st;
     cudaEvent_t a = nullptr;
     Phase(mst_grid* g_, int ph, cudaStream_t s) : g(g_), phase(ph), st(s) {
+        nvtxRangePushA(kPhaseNames[ph]);
         if (g->prof && (a = prof_event(g)) != nullptr) cudaEventRecord(a, st);
     }
     ~Phase() {
+        nvtxRangePop();
         if (!a) return;
         cudaEvent_t b = prof_event(g);
         if (!b) return;
