@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--recon-iters", type=int, default=50, help="iterations of --study recon")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default wavefront shape")
     ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
     ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
     ap.add_argument("--study", default=None, choices=["precision", "recon", "bmc", "classic", "species"],
@@ -219,6 +220,9 @@ def run_ours(args):
     meas = grid.render(beta, m.make_params(p, seed=4), images=True)["images"]
     params = m.make_params(p, grad_mode=args.grad, grid_dtype=args.grid_dtype)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    # wavefront shape picked by the autotuner on this scene (2^24-photon calls), before the warm-up
+    wavefront = None if args.no_autotune else grid.autotune(beta, m.make_params(p, grid_dtype=args.grid_dtype),
+                                                            n_sample=1 << 24)
 
     for _ in range(args.warmup):
         grid.render_grad(beta, params, meas, images=False)
@@ -351,7 +355,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_job, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "photons_per_gpu": n, "grad_mode": args.grad,
+                "config": {"workload": WORKLOAD, "photons_per_gpu": n, "grad_mode": args.grad, "wavefront": wavefront,
                            "grid_dtype": args.grid_dtype, "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"photon-id shards x{world}" if world > 1 else "1 GPU"},
                 "segments_per_step": {"forward": segs, "replay": st["replay_segments"],

@@ -286,6 +286,28 @@ typedef struct {
 int mst_render_grad_channels(mst_grid *g, const float *beta_aer_dev, int n_channels, const mst_channel *channels,
                              const uint8_t *mask_dev, double eta, double *grad_dev, double *loss_dev, void *stream);
 
+/* Wavefront shape of the persistent transport kernels on this handle: the voxels a flying lane
+ * advances per loop trip, and the resident blocks per SM, for the forward render (voxel
+ * estimator) and for replay pass 2. 0 keeps the built-in default (8 and 5 voxels; the
+ * register budget's occupancy, 3 blocks). The trip is a compile-time constant of the kernels:
+ * forward trips 6, 8, 10, 12 and pass-2 trips 4, 5, 6, 8 are built, for the FP32 grid (the
+ * FP16 / BF16 grids use the defaults). Results do not depend on the shape beyond the order of
+ * floating-point additions: each photon's path is fixed by its Philox key. Blocks per SM in
+ * 0..8 (more than the occupancy runs at the occupancy); other trips return MST_ERR_INVALID_ARG. */
+int mst_set_wavefront(mst_grid *g, int forward_trip, int forward_blocks_per_sm, int replay_trip,
+                      int replay_blocks_per_sm);
+
+/* Autotuner of the wavefront shape. Times full-gradient calls of the voxel estimator on this
+ * scene (beta_dev; p's optics, sun, seed and grid_dtype; zero measured images) with n_sample
+ * photons for each candidate (forward trips 6, 8, 10, 12 and pass-2 trips 4, 5, 6, 8, each at
+ * the register budget's occupancy and one block per SM less), sets the fastest forward and
+ * pass-2 shapes on the handle (as mst_set_wavefront) and writes them to
+ * choice_host[4] = {forward trip, forward blocks per SM, pass-2 trip, pass-2 blocks per SM}.
+ * Synchronises the stream, allocates and frees its own scratch, leaves the handle's statistics
+ * those of its last call. n_sample in [2^16, 2^27]; on failure the shape is left unchanged. */
+int mst_autotune(mst_grid *g, const float *beta_dev, const mst_params *p, uint64_t n_sample, int *choice_host,
+                 void *stream);
+
 /* Device memory the handle may hold for the events a full-gradient forward render stores
  * (44 B per scattering event: voxel, position, incoming direction, weight, photon index, event
  * number, and its w_s), for

@@ -40,7 +40,8 @@ EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy"
            "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
            "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
            "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory", "mst_render_bmc",
-           "mst_set_reg_weights", "mst_set_air", "mst_render_grad_channels", "mst_sun_mask"]
+           "mst_set_reg_weights", "mst_set_air", "mst_render_grad_channels", "mst_sun_mask",
+           "mst_set_wavefront", "mst_autotune"]
 PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine", "replay2",
           "replay_list", "event_adjoint", "bmc"]
 
@@ -97,6 +98,8 @@ def _load():
     L.mst_set_reg_weights.argtypes = [P, P]
     L.mst_set_air.argtypes = [P, P, ctypes.c_double]
     L.mst_sun_mask.argtypes = [P, D, D, D, P, P]
+    L.mst_set_wavefront.argtypes = [P, I, I, I, I]
+    L.mst_autotune.argtypes = [P, P, P, ctypes.c_uint64, P, P]
     L.mst_render_grad_channels.argtypes = [P, P, I, P, P, D, P, P, P]
     L.mst_render_bmc.argtypes = [P, P, P, ctypes.c_uint32, P, P, P]
     L.mst_get_stats.argtypes = [P, P]
@@ -348,6 +351,19 @@ class Grid:
         self._check(lib.mst_render_grad_channels(self._h, _ptr(beta), n, arr, _ptr(mask), float(eta), _ptr(grad),
                                                  _ptr(loss), _stream(stream)), "mst_render_grad_channels")
         return dict(loss=loss, grad=grad, images=imgs if images else None)
+
+    def set_wavefront(self, forward_trip=0, forward_blocks=0, replay_trip=0, replay_blocks=0):
+        """Voxels per loop trip and blocks per SM of the forward and pass-2 kernels (0: default)."""
+        self._check(lib.mst_set_wavefront(self._h, int(forward_trip), int(forward_blocks), int(replay_trip),
+                                          int(replay_blocks)), "mst_set_wavefront")
+
+    def autotune(self, beta, params: Params, n_sample: int = 1 << 24, stream=None) -> dict:
+        """Times candidate wavefront shapes on this scene and keeps the fastest (mst_autotune)."""
+        beta = self._t(beta, self.nvox, torch.float32, "beta")
+        c = (ctypes.c_int * 4)()
+        self._check(lib.mst_autotune(self._h, _ptr(beta), ctypes.byref(params), int(n_sample), c, _stream(stream)),
+                    "mst_autotune")
+        return dict(forward_trip=c[0], forward_blocks_per_sm=c[1], replay_trip=c[2], replay_blocks_per_sm=c[3])
 
     def set_replay_memory(self, nbytes: int):
         """Budget for the events a full-gradient forward render stores (0: W by replay)."""

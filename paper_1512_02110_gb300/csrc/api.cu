@@ -189,9 +189,9 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
     const bool classic_adj = replay && p->estimator == MST_EST_CLASSIC;
     const int m_p1 = classic_adj ? 5 : 3, m_p2 = classic_adj ? 6 : 2;
     if (classic_adj) a.cres = g->resid;
-    const int b_fwd = g->sm_count * transport_blocks_per_sm(p->grid_dtype, est, g->air != nullptr);
-    const int b_p1 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, m_p1, g->air != nullptr);
-    const int b_p2 = g->sm_count * transport_blocks_per_sm(p->grid_dtype, m_p2, g->air != nullptr);
+    const int b_fwd = transport_blocks(g, p->grid_dtype, est);
+    const int b_p1 = transport_blocks(g, p->grid_dtype, m_p1);
+    const int b_p2 = transport_blocks(g, p->grid_dtype, m_p2);
     if (replay) set_fold(a, (uint64_t)g->geo.nvox);
     else if (est == MST_EST_VOXEL) set_fold(a, (uint64_t)g->geo.nvox * g->cp);
     if (store_events) {
@@ -275,8 +275,7 @@ int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
         a.ticket = g->tickets + 2;  // the adjoint's blocks take the forward warps' lists from it
         MST_CK(launch_event_adjoint(g, a, p->grid_dtype, st));
     }
-    const bool two = g->air != nullptr;
-    auto blocks = [&](int mode) { return g->sm_count * transport_blocks_per_sm(p->grid_dtype, mode, two); };
+    auto blocks = [&](int mode) { return transport_blocks(g, p->grid_dtype, mode); };
     a.ticket = g->tickets;
     {
         Phase ph(g, MST_PH_REPLAY, st);  // returns at once when the events fitted
@@ -358,8 +357,11 @@ bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
     // the forward reserves slots in per-warp chunks: one chunk per resident warp of headroom
     const uint64_t tails = (uint64_t)g->sm_count * transport_blocks_per_sm(dtype, 0, g->air != nullptr) *
                            kTransportWarps * kEventChunk;
-    uint64_t want = (g->ev_last ? g->ev_last + g->ev_last / 4 : 6 * n) + tails;
-    want = std::min<uint64_t>(std::max<uint64_t>(want, 1024), max_ev);
+    // need: the last count this handle's forward reserved (6 per photon before any), plus the
+    // tails; a buffer below it is replaced by one 1.25 x the need, so that counts that drift by a
+    // few chunks from call to call do not reallocate it every time
+    const uint64_t need = std::min<uint64_t>(std::max<uint64_t>((g->ev_last ? g->ev_last : 6 * n) + tails, 1024), max_ev);
+    const uint64_t want = std::min<uint64_t>(need + need / 4, max_ev);
     if (!g->warp_head) {  // the forward's warps: at most kMaxWarpsPerSm per SM
         if (cudaMalloc(&g->warp_head, sizeof(uint32_t) * (size_t)g->sm_count * kMaxWarpsPerSm) != cudaSuccess) {
             cudaGetLastError();
@@ -370,7 +372,7 @@ bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
     if ((uint64_t)g->sm_count * transport_blocks_per_sm(dtype, 0, g->air != nullptr) * kTransportWarps >
         (uint64_t)g->sm_count * kMaxWarpsPerSm)
         return false;
-    if (g->evrec && g->ev_cap >= want) return true;
+    if (g->evrec && g->ev_cap >= need) return true;
     cudaFree(g->evrec);
     cudaFree(g->wseq);
     cudaFree(g->ch_next);
@@ -1092,6 +1094,114 @@ int mst_render_grad_channels(mst_grid* g, const float* beta, int n, const mst_ch
         MST_CK(launch_regularizer(g, beta, eta, g->lap, g->stats + MST_NSTATS + 1, lossp, grad, st));
     }
     return MST_OK;
+}
+
+int mst_set_wavefront(mst_grid* g, int forward_trip, int forward_blocks, int replay_trip, int replay_blocks) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    const bool ft = forward_trip == 0 || forward_trip == 6 || forward_trip == 8 || forward_trip == 10 ||
+                    forward_trip == 12;
+    const bool rt = replay_trip == 0 || replay_trip == 4 || replay_trip == 5 || replay_trip == 6 || replay_trip == 8;
+    if (!ft || !rt || forward_blocks < 0 || forward_blocks > 8 || replay_blocks < 0 || replay_blocks > 8)
+        return fail(g, MST_ERR_INVALID_ARG,
+                    "forward trip in {0, 6, 8, 10, 12}, pass-2 trip in {0, 4, 5, 6, 8}, blocks per SM in 0..8");
+    g->wf_trip[0] = forward_trip;  // forward, voxel estimator (the classic one keeps its defaults)
+    g->wf_blocks[0] = forward_blocks;
+    for (int m : {2, 4}) {  // replay pass 2, recomputing or reading the stored w_s
+        g->wf_trip[m] = replay_trip;
+        g->wf_blocks[m] = replay_blocks;
+    }
+    return MST_OK;
+}
+
+int mst_autotune(mst_grid* g, const float* beta, const mst_params* p, uint64_t n_sample, int* choice, void* stream) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    if (!beta || !choice) return fail(g, MST_ERR_INVALID_ARG, "beta and choice are required");
+    int rc = check_params(g, p, false);
+    if (rc) return rc;
+    if (n_sample < 65536 || n_sample > kRecordMaxPhotons)
+        return fail(g, MST_ERR_INVALID_ARG, "n_sample must be in [2^16, 2^27]");
+    DeviceGuard dg(g->device);
+    cudaStream_t st = as_stream(stream);
+    mst_params q = *p;  // a full-gradient call of the voxel estimator on the sample, against zero images
+    q.n_photons = n_sample;
+    q.n_photons_total = 0;
+    q.photon_offset = 0;
+    q.estimator = MST_EST_VOXEL;
+    q.grad_mode = MST_GRAD_FULL;
+    q.reg_eta = 0.0;
+    double *meas = nullptr, *grad = nullptr, *loss = nullptr;
+    if (cudaMalloc(&meas, sizeof(double) * g->total_pix) != cudaSuccess ||
+        cudaMalloc(&grad, sizeof(double) * g->geo.nvox) != cudaSuccess || cudaMalloc(&loss, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(meas);
+        cudaFree(grad);
+        return fail(g, MST_ERR_OOM, "autotune buffers: out of device memory");
+    }
+    MST_CK(cudaMemsetAsync(meas, 0, sizeof(double) * g->total_pix, st));
+    const bool prof0 = g->prof;
+    // the sample's event counts must not size the buffers of the handle's real calls
+    const unsigned long long ev_last0 = g->ev_last;
+    const int saved_trip[7] = {g->wf_trip[0], 0, g->wf_trip[2], 0, g->wf_trip[4], 0, 0};
+    const int saved_blocks[7] = {g->wf_blocks[0], 0, g->wf_blocks[2], 0, g->wf_blocks[4], 0, 0};
+    const int occ_f = transport_blocks_per_sm(q.grid_dtype, 0, g->air != nullptr);
+    const int occ_r = transport_blocks_per_sm(q.grid_dtype, 4, g->air != nullptr);
+    // candidates: voxels per trip around the defaults, at full occupancy and one block less
+    std::vector<std::pair<int, int>> cf, cr;
+    for (int t : {6, 8, 10, 12})
+        for (int b = occ_f; b >= std::max(1, occ_f - 1); --b) cf.push_back({t, b});
+    for (int t : {4, 5, 6, 8})
+        for (int b = occ_r; b >= std::max(1, occ_r - 1); --b) cr.push_back({t, b});
+    std::vector<double> tf(cf.size(), 1e30), tr(cr.size(), 1e30);
+    g->prof = true;
+    auto run = [&](double& ms_f, double& ms_r) -> int {  // one timed call: forward and pass-2 phases
+        prof_reset(g);
+        int e = render_grad_impl(g, beta, &q, meas, nullptr, nullptr, grad, loss, st);
+        if (e) return e;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return fail(g, MST_ERR_CUDA, "autotune: stream error");
+        ms_f = ms_r = 0.0;
+        for (const auto& pr : g->prof_recs) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, pr.a, pr.b);
+            if (pr.phase == MST_PH_TRANSPORT) ms_f += t;
+            if (pr.phase == MST_PH_REPLAY2) ms_r += t;
+        }
+        return MST_OK;
+    };
+    double wf = 0.0, wr = 0.0;
+    rc = run(wf, wr);  // warm-up (buffers sized, kernels loaded)
+    const size_t n = std::max(cf.size(), cr.size());
+    for (size_t i = 0; i < n && rc == MST_OK; ++i) {  // forward and pass-2 candidates paired in one call
+        const size_t jf = i % cf.size(), jr = i % cr.size();
+        rc = mst_set_wavefront(g, cf[jf].first, cf[jf].second, cr[jr].first, cr[jr].second);
+        for (int rep = 0; rep < 2 && rc == MST_OK; ++rep) {
+            double ms_f = 0.0, ms_r = 0.0;
+            rc = run(ms_f, ms_r);
+            tf[jf] = std::min(tf[jf], ms_f);
+            tr[jr] = std::min(tr[jr], ms_r);
+        }
+    }
+    g->prof = prof0;
+    prof_reset(g);
+    g->ev_last = ev_last0;
+    g->ev_seen_pending = false;  // a count pending from before was overwritten by the sample's
+    cudaFree(meas);
+    cudaFree(grad);
+    cudaFree(loss);
+    if (rc) {  // keep the setting the handle had
+        for (int m : {0, 2, 4}) {
+            g->wf_trip[m] = saved_trip[m];
+            g->wf_blocks[m] = saved_blocks[m];
+        }
+        return rc;
+    }
+    const size_t bf = std::min_element(tf.begin(), tf.end()) - tf.begin();
+    const size_t br = std::min_element(tr.begin(), tr.end()) - tr.begin();
+    rc = mst_set_wavefront(g, cf[bf].first, cf[bf].second, cr[br].first, cr[br].second);
+    choice[0] = cf[bf].first;
+    choice[1] = cf[bf].second;
+    choice[2] = cr[br].first;
+    choice[3] = cr[br].second;
+    return rc;
 }
 
 int mst_set_replay_memory(mst_grid* g, uint64_t bytes) {

@@ -125,6 +125,8 @@ struct mst_grid {
     unsigned long long ev_last = 0;          // events offered by the last storing call whose count arrived
     bool capturing = false;                  // inside a stream capture: no allocation, no event query
     bool batch_stored = false;               // the batch allocated this handle's event buffers before capture
+    int wf_trip[7] = {0, 0, 0, 0, 0, 0, 0};    // per kernel mode: voxels per trip (0: kernel default) ...
+    int wf_blocks[7] = {0, 0, 0, 0, 0, 0, 0};  // ... and blocks per SM (0: the register budget's occupancy)
     uint64_t rec_budget = mst::kDefaultRecordBytes;
     unsigned int* score_cnt = nullptr;  // [2 kScoreBins + 1] list bin counts, bin fill, list length
     double* g64 = nullptr;        // [nvox]
@@ -206,5 +208,11 @@ cudaError_t launch_classic_residual(const mst_grid* g, const double* img, const 
 cudaError_t launch_regularizer(const mst_grid* g, const float* beta, double eta, double* lap, double* psi,
                                double* loss, double* grad, cudaStream_t st);
 int transport_blocks_per_sm(int dtype, int mode, bool two);
+// blocks of a persistent transport launch of this mode on the handle (its wavefront setting)
+inline int transport_blocks(const mst_grid* g, int dtype, int mode) {
+    const int occ = transport_blocks_per_sm(dtype, mode, g->air != nullptr);
+    const int b = g->wf_blocks[mode];
+    return g->sm_count * (b > 0 && b < occ ? b : occ);
+}
 
 }  // namespace mst

@@ -587,8 +587,9 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
 // scatters the score of every flight that ends in an event; it stops at pass 1's last event.
 // Both passes run the same flight and event arithmetic, so they see the same path.
 // TWO: two-species medium (the launch has an air field); one-species kernels carry none of its
-// code.
-template <int DT, int MODE, bool TWO>
+// code. TRIP: voxels a flying lane advances per loop trip (0: the mode's default), a compile-time
+// constant (a run-time bound cost the forward 2 %); the autotuner picks among the instantiated ones.
+template <int DT, int MODE, bool TWO, int TRIP = 0>
 __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMinBlocksPass2
                                                        : (MODE == kPass1 ? kMinBlocksPass1
                                                           : ((MODE == kFwdClassic || MODE == kPass1C || MODE == kPass2C)
@@ -599,7 +600,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
     constexpr bool PASS2 = MODE == kPass2 || MODE == kPass2W || MODE == kPass2C;
     constexpr bool CLASSIC_ADJ = MODE == kPass1C || MODE == kPass2C;
     constexpr bool REPLAY = PASS1 || PASS2;
-    constexpr int kStepsPerTrip = PASS2 ? kStepsPass2 : (PASS1 ? kStepsPass1 : kStepsForward);
+    constexpr int kStepsPerTrip = TRIP > 0 ? TRIP : (PASS2 ? kStepsPass2 : (PASS1 ? kStepsPass1 : kStepsForward));
     constexpr int NW = Rec<REPLAY>::NW;
     extern __shared__ uint32_t smem[];
     const unsigned lane = threadIdx.x & 31u;
@@ -1075,10 +1076,35 @@ int occupancy(K kern, size_t smem) {
     return n;
 }
 
-template <int DT, int MODE, bool TWO>
+template <int DT, int MODE, bool TWO, int TRIP = 0>
 cudaError_t launch_mode(const TransportArgs& a, int blocks, cudaStream_t st) {
-    k_transport<DT, MODE, TWO><<<blocks, kTB, smem_bytes<(MODE >= 2)>(), st>>>(a);
+    if constexpr (TRIP != 0) {  // a variant of the autotuner: the default's carveout (set by occupancy())
+        static const int once = occupancy(k_transport<DT, MODE, TWO, TRIP>, smem_bytes<(MODE >= 2)>());
+        (void)once;
+    }
+    k_transport<DT, MODE, TWO, TRIP><<<blocks, kTB, smem_bytes<(MODE >= 2)>(), st>>>(a);
     return cudaGetLastError();
+}
+
+// Trip-length variants of the FP32-grid forward and pass-2 kernels, for the autotuner
+// (kForwardTrips / kReplayTrips; the defaults are the un-suffixed kernels).
+template <int MODE, bool TWO>
+cudaError_t launch_trip(const TransportArgs& a, int trip, int blocks, cudaStream_t st) {
+    if constexpr (MODE == kFwdVoxel) {
+        switch (trip) {
+            case 6: return launch_mode<0, MODE, TWO, 6>(a, blocks, st);
+            case 10: return launch_mode<0, MODE, TWO, 10>(a, blocks, st);
+            case 12: return launch_mode<0, MODE, TWO, 12>(a, blocks, st);
+            default: return launch_mode<0, MODE, TWO>(a, blocks, st);
+        }
+    } else {
+        switch (trip) {
+            case 4: return launch_mode<0, MODE, TWO, 4>(a, blocks, st);
+            case 6: return launch_mode<0, MODE, TWO, 6>(a, blocks, st);
+            case 8: return launch_mode<0, MODE, TWO, 8>(a, blocks, st);
+            default: return launch_mode<0, MODE, TWO>(a, blocks, st);
+        }
+    }
 }
 
 template <int DT, bool TWO>
@@ -1095,7 +1121,12 @@ int occupancy_mode(int mode) {
 }
 
 template <int DT, bool TWO>
-cudaError_t launch_dt(const TransportArgs& a, int mode, int blocks, cudaStream_t st) {
+cudaError_t launch_dt(const TransportArgs& a, int mode, int trip, int blocks, cudaStream_t st) {
+    if constexpr (DT == 0) {
+        if (trip > 0 && mode == kFwdVoxel) return launch_trip<kFwdVoxel, TWO>(a, trip, blocks, st);
+        if (trip > 0 && mode == kPass2W) return launch_trip<kPass2W, TWO>(a, trip, blocks, st);
+        if (trip > 0 && mode == kPass2) return launch_trip<kPass2, TWO>(a, trip, blocks, st);
+    }
     switch (mode) {
         case kFwdVoxel: return launch_mode<DT, kFwdVoxel, TWO>(a, blocks, st);
         case kFwdClassic: return launch_mode<DT, kFwdClassic, TWO>(a, blocks, st);
@@ -1108,9 +1139,10 @@ cudaError_t launch_dt(const TransportArgs& a, int mode, int blocks, cudaStream_t
 }
 
 template <bool TWO>
-cudaError_t launch_species(const TransportArgs& a, int dtype, int mode, int blocks, cudaStream_t st) {
-    return dtype == 0 ? launch_dt<0, TWO>(a, mode, blocks, st)
-                      : (dtype == 1 ? launch_dt<1, TWO>(a, mode, blocks, st) : launch_dt<2, TWO>(a, mode, blocks, st));
+cudaError_t launch_species(const TransportArgs& a, int dtype, int mode, int trip, int blocks, cudaStream_t st) {
+    return dtype == 0 ? launch_dt<0, TWO>(a, mode, trip, blocks, st)
+                      : (dtype == 1 ? launch_dt<1, TWO>(a, mode, trip, blocks, st)
+                                    : launch_dt<2, TWO>(a, mode, trip, blocks, st));
 }
 
 }  // namespace
@@ -1130,9 +1162,9 @@ int transport_blocks_per_sm(int dtype, int mode, bool two) {
 
 cudaError_t launch_transport(const mst_grid* g, const TransportArgs& a, int dtype, int mode, int blocks,
                              cudaStream_t st) {
-    (void)g;
-    return a.beta_air ? launch_species<true>(a, dtype, mode, blocks, st)
-                      : launch_species<false>(a, dtype, mode, blocks, st);
+    const int trip = g->wf_trip[mode];  // the handle's wavefront setting (0: the kernel's default)
+    return a.beta_air ? launch_species<true>(a, dtype, mode, trip, blocks, st)
+                      : launch_species<false>(a, dtype, mode, trip, blocks, st);
 }
 
 cudaError_t launch_score_list(const mst_grid* g, uint32_t n, cudaStream_t st) {

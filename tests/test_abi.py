@@ -112,6 +112,8 @@ def test_create_grid_validates_before_touching_a_device(pkg):
     assert L.mst_set_air(None, None, 1.0) == -1
     assert L.mst_sun_mask(None, 0.0, 0.0, 0.1, None, None) == -1
     assert L.mst_render_grad_channels(None, None, 1, None, None, 0.0, None, None, None) == -1
+    assert L.mst_set_wavefront(None, 8, 3, 5, 3) == -1
+    assert L.mst_autotune(None, None, None, 1 << 20, None, None) == -1
 
 
 def test_package_refuses_without_library(tmp_path):
