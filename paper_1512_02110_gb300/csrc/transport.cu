@@ -837,7 +837,8 @@ __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
         const uint32_t gw = list;
         __syncthreads();
         if (gw >= A.n_warps) break;
-        for (uint32_t ch = A.warp_head[gw]; ch != kEndChunk; ch = A.ch_next[ch]) {
+        for (uint32_t ch = A.warp_head[gw], next; ch != kEndChunk; ch = next) {
+            next = A.ch_next[ch];  // issued first, so its latency overlaps the chunk's work
             for (unsigned q = threadIdx.x; q < kEvChunk; q += kTB) {
                 const uint32_t* r = A.evrec + (unsigned long long)ch * kEvChunk + q;
                 const uint32_t j = r[8 * C];
