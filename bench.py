@@ -47,13 +47,14 @@ def parse():
     ap.add_argument("--grad", default="full", choices=["full", "surrogate"])
     ap.add_argument("--grid-dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--ref-photons", type=float, default=2e4, help="photons per oracle step (bounded sample)")
-    ap.add_argument("--recon-iters", type=int, default=50, help="iterations of --study recon")
+    ap.add_argument("--recon-iters", type=int, default=50, help="iterations of --study recon; --study haze runs 2x for L-BFGS")
+    ap.add_argument("--render-photons", type=float, default=1e8, help="photons per render of --study haze")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default wavefront shape")
     ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
     ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
-    ap.add_argument("--study", default=None, choices=["precision", "recon", "bmc", "classic", "species"],
+    ap.add_argument("--study", default=None, choices=["precision", "recon", "haze", "bmc", "classic", "species"],
                     help="FP16/BF16 brick forms against FP32 at equal photon count (prints one JSON line)")
     return ap.parse_args()
 
@@ -651,6 +652,79 @@ def run_recon_study(args):
     return 0
 
 
+def run_haze_study(args):
+    """Reconstruction in the paper's own setting (Sec. 7; synth.cfg_haze80): aerosol haze over
+    air on 80 x 80 x 120 voxels, 36 ground cameras, the unknowns the values of the paper's 20 x
+    20 x 40 grid (blocks of 4 x 4 x 3 voxels, 16000 unknowns against 147456 pixels). Measured
+    images: the true field rendered with 10x the photons of one reconstruction render, seed 4;
+    pixels within 10 deg of the sun masked (M_c). Runs: projected L-BFGS on the full gradient
+    from beta_aerosol = 0.001 1/km (the score of the aerosol collisions needs a nonzero aerosol
+    density) with the Laplacian prior (Eq. Cost, eta = 3000: eta Psi of the true field equals
+    the loss's noise floor at 1e8 photons) and without it; the paper's surrogate loop (Eq. GD,
+    N_GD = 5) from beta_aerosol = 0, its null initialisation, with Q = I and Q = 1 / ray count.
+    Prints one JSON line: epsilon = |b - b_true|_1 / |b_true|_1 and delta_mass along each run
+    (aerosol only; air is known), its renders and GPU+host time, and the loss of the true field
+    (the noise floor)."""
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(0)
+    n = int(args.render_photons)
+    eta = 3000.0
+    sc, p, coarse, block = synth.cfg_haze80(n)
+    grid = m.Grid.from_scene(sc)
+    grid.set_air(torch.from_numpy(sc.beta_air.astype(np.float32)).cuda(), p.albedo_air)
+    b_true = sc.beta.astype(np.float64)
+    t1 = np.abs(b_true).sum()
+    bt = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
+    t0 = time.perf_counter()
+    meas = grid.render(bt, m.make_params(p, seed=4, n_photons=10 * n))["images"]
+    mask = grid.sun_mask(p.sun_zenith, p.sun_azimuth, math.radians(10.0))
+    torch.cuda.synchronize()
+
+    def errs(b):
+        return {"epsilon": float(np.abs(b - b_true).sum() / t1), "delta_mass": float((np.abs(b).sum() - t1) / t1)}
+
+    out = {"study": "haze", "scene": "80x80x120 voxels of 625x625x83.3 m, haze blobs on 20x20x40, air at 550 nm, "
+           "36 ground cameras 64x64 (150 deg pinholes), sun zenith 45 deg", "photons_per_render": n, "eta": eta,
+           "measured": {"photons": 10 * n, "seed": 4, "s": time.perf_counter() - t0,
+                        "masked_pixels": int((mask == 0).sum().item()), "pixels": sc.n_pix},
+           "unknowns": int(np.prod(coarse)),
+           "true_field": {"loss": grid.render_grad(bt, m.make_params(p, grad_mode="full"), meas, mask,
+                                                   images=False)["loss"].item(),
+                          "psi": grid.regularizer(bt, 1.0).item()}}
+    beta0 = np.full(sc.nvox, 0.001 * synth.KM)
+    for name, e in (("lbfgs_full_prior", eta), ("lbfgs_full_no_prior", 0.0)):
+        trace = []
+        t0 = time.perf_counter()
+        prm = m.make_params(p, grad_mode="full", reg_eta=e)
+        st = m.reconstruct(grid, meas, beta0, prm, iters=2 * args.recon_iters, method="lbfgs", mask=mask, block=block,
+                           callback=lambda s: trace.append({"it": s.it, "loss": s.losses[-1], **errs(s.beta)}))
+        torch.cuda.synchronize()
+        out[name] = {"initial": errs(beta0), "iterations": st.it, "renders": st.n_renders,
+                     "s": time.perf_counter() - t0, "loss0": st.losses[0], "final": errs(st.beta),
+                     "trace": trace[::10] + trace[-1:]}
+    P = m.Blocks(sc.shape, block)
+    for cond in ("none", "inv_count"):
+        prm = m.make_params(p, grad_mode="surrogate", conditioning=cond, reg_eta=eta)
+        b0 = torch.zeros(sc.nvox, dtype=torch.float32, device="cuda")
+        L0 = grid.render(b0, prm, images=False, L=True)["L"]
+        g0 = P.reduce(grid.surrogate_grad(b0, L0, b0, prm, meas, mask)["grad"].cpu().numpy())
+        step = 0.02 * synth.KM / max(np.abs(g0).max(), 1e-300)  # first step: at most 0.02 1/km per block
+        trace = []
+        t0 = time.perf_counter()
+        st = m.reconstruct(grid, meas, np.zeros(sc.nvox), prm, iters=args.recon_iters, method="gd", step=step,
+                           n_gd=5, mask=mask, block=block,
+                           callback=lambda s: trace.append({"outer": s.it, "loss": s.losses[-1], **errs(s.beta)}))
+        torch.cuda.synchronize()
+        out[f"gd_null_init_{cond}"] = {"initial": errs(np.zeros(sc.nvox)), "outer_iterations": st.it, "n_gd": 5,
+                                       "step": step, "renders": st.n_renders, "s": time.perf_counter() - t0,
+                                       "loss0": st.losses[0], "final": errs(st.beta),
+                                       "trace": trace[::10] + trace[-1:]}
+    print(json.dumps(out))
+    return 0
+
 def run_precision_study(args):
     """Image and gradient error of the FP32 / FP16 / BF16 brick forms at N photons against a
     10 N-photon FP32 reference (relative L2), and their step times."""
@@ -692,6 +766,8 @@ def main():
         return run_precision_study(args)
     if args.study == "recon":
         return run_recon_study(args)
+    if args.study == "haze":
+        return run_haze_study(args)
     if args.study == "bmc":
         return run_bmc_study(args)
     if args.study == "classic":

@@ -42,7 +42,7 @@ extern "C" {
 #define MST_ERR_UNSUPPORTED (-5) /* combination of options not implemented */
 #define MST_ERR_TOO_LARGE (-6)   /* grid exceeds the fixed scratch of mst_transmittance_noalloc */
 
-#define MST_MAX_CAMERAS 16
+#define MST_MAX_CAMERAS 64
 #define MST_MAX_SUBPIXEL_RAYS 64
 #define MST_NSTATS 32
 #define MST_NOALLOC_MAX_VOXELS (1 << 21) /* largest grid (nx ny nz) of mst_transmittance_noalloc */

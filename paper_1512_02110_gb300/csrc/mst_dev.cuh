@@ -12,7 +12,7 @@
 
 namespace mst {
 
-constexpr int kMaxCams = 16;
+constexpr int kMaxCams = 64;
 constexpr int kMaxRays = 64;
 
 struct Geo {

@@ -297,6 +297,61 @@ def cfg_cumulus64(n_photons: int = 100_000_000):
     return scene, params
 
 
+def haze_field(coarse_shape, coarse_h, seed: int, n_blobs: int = 4, max_ext: float = 0.2 * KM,
+               background: float = 0.005 * KM, sigma_xy=(4000.0, 9000.0), sigma_z=(500.0, 1200.0),
+               top: float = 3000.0, inner: float = 0.6) -> np.ndarray:
+    """Aerosol haze blobs of the kind the paper reconstructs (Sec. 7): Gaussian blobs wide
+    across and shallow in altitude (horizontal sigma in sigma_xy, vertical in sigma_z),
+    centres uniform over the inner fraction of the box across and below `top` in altitude,
+    scaled so the maximum is max_ext over a uniform background. Evaluated at the centres of
+    the coarse cells; returns 1/m, flat, x fastest, on the coarse grid."""
+    rng = np.random.default_rng(seed)
+    X, Y, Z = _centres(coarse_shape, coarse_h)
+    ext = np.array(coarse_shape, dtype=np.float64) * np.array(coarse_h)
+    f = np.zeros(X.shape)
+    for _ in range(n_blobs):
+        cx, cy = ext[:2] * (0.5 - inner / 2 + inner * rng.random(2))
+        cz = top * rng.random()
+        sx, sy = rng.uniform(*sigma_xy, size=2)
+        sz = rng.uniform(*sigma_z)
+        f += np.exp(-0.5 * (((X - cx) / sx) ** 2 + ((Y - cy) / sy) ** 2 + ((Z - cz) / sz) ** 2))
+    f = f / f.max() * (max_ext - background) + background
+    return _flat(f)
+
+
+def refine(coarse: np.ndarray, coarse_shape, factor) -> np.ndarray:
+    """A coarse field (flat, x fastest) held constant over blocks of factor = (fx, fy, fz)
+    fine voxels: the fine field, flat, x fastest."""
+    cx, cy, cz = (int(v) for v in coarse_shape)
+    f3 = np.asarray(coarse, dtype=np.float64).reshape(cz, cy, cx)
+    f3 = np.repeat(np.repeat(np.repeat(f3, factor[2], 0), factor[1], 1), factor[0], 2)
+    return np.ascontiguousarray(f3).ravel()
+
+
+def cfg_haze80(n_photons: int = 100_000_000, seed: int = 1, fov_deg: float = 150.0):
+    """The paper's reconstruction setting (Sec. 7), synthetic: a 50 x 50 x 10 km atmosphere on
+    80 x 80 x 120 voxels (625 x 625 x 83.3 m); aerosol haze blobs defined on the coarse 20 x 20
+    x 40 grid (blocks of 4 x 4 x 3 voxels) over air at 550 nm (0.0116 1/km at the ground, 8 km
+    scale height); sun at 45 deg zenith; 36 ground cameras 7 km apart on a 6 x 6 lattice,
+    looking up, 64 x 64 pixels. The paper's cameras are hemispherical; these are pinholes of
+    fov_deg horizontal field of view (150 deg: the image corners see 79 deg from the zenith).
+    Aerosol albedo 0.9 and g 0.7 (the paper leaves both to its haze model). Returns (scene with
+    beta = aerosol and beta_air = air, params, coarse shape, block)."""
+    coarse, block = (20, 20, 40), (4, 4, 3)
+    shape = tuple(c * b for c, b in zip(coarse, block))
+    h = (625.0, 625.0, 10000.0 / 120)
+    ch = tuple(v * b for v, b in zip(h, block))
+    aer = refine(haze_field(coarse, ch, seed), coarse, block)
+    air = air_profile(shape, h, 0.0116 * KM)
+    xs = 25000.0 + 7000.0 * (np.arange(6) - 2.5) + 100.0  # off the voxel faces
+    pos = [(x, y, 1.0) for y in xs for x in xs]
+    scene = make_scene(shape, h, aer, make_cameras(pos, 64, 64, fov_deg))
+    scene = dataclasses.replace(scene, beta_air=air)
+    params = Params(albedo=0.9, g=0.7, sun_zenith=math.radians(45.0), n_photons=n_photons, seed=3,
+                    albedo_air=1.0)
+    return scene, params, coarse, block
+
+
 def smoothed(beta: np.ndarray, shape, frac: float = 0.3) -> np.ndarray:
     """A nearby but different field: (1-frac)*beta + frac*mean(beta)."""
     return (1.0 - frac) * beta + frac * float(beta.mean())

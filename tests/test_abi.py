@@ -91,7 +91,7 @@ def test_create_grid_validates_before_touching_a_device(pkg):
         (pkg.GridDesc(0, 4, 4, 10.0, 10.0, 10.0, (ctypes.c_double * 3)(0, 0, 0)), 1, 10),
         (pkg.GridDesc(4, 4, 4, -1.0, 10.0, 10.0, (ctypes.c_double * 3)(0, 0, 0)), 1, 10),
         (good, 0, 10),
-        (good, 17, 10),
+        (good, 65, 10),
         (good, 1, 0),
         (good, 1, 65),
         # past the packed voxel index (11 + 11 + 10 bits) or 2^30 voxels

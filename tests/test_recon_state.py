@@ -114,3 +114,28 @@ def test_block_reconstruction_reaches_the_block_optimum(tmp_path):
     g = reconstruct(grid, None, np.full(24, 0.5), None, iters=10, method="gd", step=0.5 / np.linalg.norm(A @ B, 2) ** 2,
                     n_gd=5, block=(2, 2, 1))
     assert all(b2 <= b1 + 1e-12 for b1, b2 in zip(g.losses, g.losses[1:])) and np.allclose(g.beta, B @ g.x)
+
+
+def test_haze_scene_is_the_coarse_field_on_blocks():
+    """The paper-shaped haze scene: its aerosol field is the coarse 20 x 20 x 40 field held
+    constant over 4 x 4 x 3 voxel blocks (synth.refine agrees with Blocks.expand), the 36
+    cameras sit inside the domain and within the library's camera limit, and the optical depths
+    are those of haze (aerosol column 0.05-0.5, air 0.07)."""
+    import re
+
+    import synth
+    from paper_1512_02110_gb300.autograd import Blocks
+    sc, p, coarse, block = synth.cfg_haze80(1000)
+    P = Blocks(sc.shape, block)
+    assert P.n == int(np.prod(coarse))
+    assert np.allclose(P.expand(P.restrict(sc.beta)), sc.beta, rtol=1e-14, atol=0)
+    th = np.random.default_rng(1).random(P.n)
+    assert np.array_equal(synth.refine(th, coarse, block), P.expand(th))
+    hdr = open(__import__("os").path.join(__import__("os").path.dirname(__file__), "..", "include", "mst.h")).read()
+    assert sc.n_cams == 36 <= int(re.search(r"#define MST_MAX_CAMERAS (\d+)", hdr).group(1))
+    ext = sc.extent()
+    assert np.all(sc.cam_pos > 0) and np.all(sc.cam_pos < ext)
+    dz = sc.h[2]
+    col = sc.beta.reshape(sc.shape[::-1]).sum(0) * dz
+    assert 0.04 < col.min() and col.max() < 0.5
+    assert abs(sc.beta_air.reshape(sc.shape[::-1]).sum(0).mean() * dz - 0.066) < 0.002
