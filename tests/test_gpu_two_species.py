@@ -266,3 +266,58 @@ def test_two_species_in_a_batch(m):
     assert rel_l2(out["grad"][0].cpu().numpy(), ref0["grad"].cpu().numpy()) < 1e-5
     assert abs(out["loss"][0].item() - refs[0]["loss"].item()) > 1e-3 * refs[0]["loss"].item()
     batch.close()
+
+
+def _haze_small(n_photons=100_000):
+    """The haze reconstruction setting at a size the oracle runs in seconds: aerosol blobs on
+    a coarse 5 x 5 x 10 grid held over 4 x 4 x 3 voxel blocks (20 x 20 x 30 voxels of 625 x 625 x
+    83.3 m) over air at 550 nm, 36 ground cameras of 8 x 8 pixels and 150 deg field of view
+    (rays up to 79 deg from the zenith), sun at 45 deg."""
+    coarse, block = (5, 5, 10), (4, 4, 3)
+    shape = tuple(c * b for c, b in zip(coarse, block))
+    h = (625.0, 625.0, 10000.0 / 120)
+    ch = tuple(v * b for v, b in zip(h, block))
+    aer = synth.refine(synth.haze_field(coarse, ch, seed=5, sigma_xy=(1500.0, 3000.0), sigma_z=(300.0, 800.0),
+                                        top=1500.0), coarse, block)
+    air = synth.air_profile(shape, h, 0.0116 * synth.KM).astype(np.float32).astype(np.float64)
+    xs = 12500.0 * (np.arange(6) + 0.5) / 6 + 100.0
+    cams = synth.make_cameras([(x, y, 1.0) for y in xs for x in xs], 8, 8, 150.0)
+    sc = f32_scene(synth.make_scene(shape, h, aer, cams))
+    sc = dataclasses.replace(sc, beta_air=air)
+    p = synth.Params(albedo=0.9, g=0.7, sun_zenith=np.radians(45.0), n_photons=n_photons, seed=3, albedo_air=1.0)
+    return sc, p
+
+
+def test_haze_setting_forward_and_full_gradient(m):
+    """The configuration of the haze reconstruction (wide pinholes, 36 cameras, thin aerosol
+    over air, a block-constant field) through the forward render and the full gradient, against
+    the oracle on the photons whose paths agree."""
+    sc, p = _haze_small()
+    grid = _grid(m, sc, p)
+    beta = dev(sc.beta, np.float32)
+    skip = _skip(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render(beta, m.make_params(p), images=True, L=True)
+    st = grid.stats()
+    ref = oracle.render(sc, p, skip=skip)
+    _, T = oracle.transmittance(sc)
+    img_ref = oracle.images(sc, ref["L"], T)
+    eL2 = rel_l2(out["L"].cpu().numpy(), ref["L"])
+    eI = max_rel(out["images"].cpu().numpy(), img_ref, 1e-3 * np.abs(img_ref).max())
+    for k in ["events", "traced", "escaped_n"]:
+        assert st[k] == ref["stats"][k], (k, st[k], ref["stats"][k])
+    meas = oracle.forward_images(sc, p.replace(seed=4, n_photons=20_000))[0] * 0.8 + 1e-9
+    mask = oracle.sun_mask(sc, p.sun_zenith, p.sun_azimuth, np.radians(25.0))  # 8 x 8 pixels of ~20 deg
+    assert 0 < (mask == 0).sum() < mask.size
+    g = grid.render_grad(beta, m.make_params(p, grad_mode="full", reg_eta=3000.0), dev(meas, np.float64),
+                         dev(mask, np.uint8))
+    gst = grid.stats()
+    grid.set_debug(None, None)
+    gr = oracle.full_grad(sc, p, meas, mask, eta=3000.0, skip=skip)
+    el = abs(g["loss"].item() - gr["loss"]) / gr["loss"]
+    eg = rel_l2(g["grad"].cpu().numpy(), gr["grad"])
+    record("haze_setting", diverged_frac=skip.mean(), L_rel_l2=eL2, images_max_rel=eI, loss_rel=el, grad_rel_l2=eg,
+           events=st["events"], air_events=st["air_events"], masked=int((mask == 0).sum()))
+    assert st["events"] > 0 and 0 < st["air_events"] < st["events"]
+    assert gst["events_stored"] == gst["events"]
+    assert eL2 < 1e-4 and eI < 1e-4 and el < 1e-4 and eg < 1e-3, (eL2, eI, el, eg)
