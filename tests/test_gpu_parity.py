@@ -326,6 +326,31 @@ def test_full_gradient(m, torch):
     assert ei < 1e-4 and el < 1e-4 and eg < 1e-3
 
 
+@pytest.mark.parametrize("order", [1, 3])
+def test_full_gradient_max_order(m, torch, order):
+    """The model truncated at `order` scatterings (order 1: the single-scattering model the
+    reconstruction study fits as the paper's baseline): paths end at that event in the forward,
+    the stored-event adjoint and replay pass 2 alike."""
+    sc, p, meas, mask = _grad_case()
+    p = p.replace(max_order=order)
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    skip, _, _ = _diverged(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render_grad(beta, m.make_params(p, grad_mode="full", reg_eta=0.05), dev(meas, np.float64),
+                           dev(mask, np.uint8))
+    st = grid.stats()
+    grid.set_debug(None, None)
+    ref = oracle.full_grad(sc, p, meas, mask, eta=0.05, skip=skip)
+    ei = max_rel(out["images"].cpu().numpy(), ref["images"], 1e-3 * np.abs(ref["images"]).max())
+    el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
+    eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    record(f"full_gradient[max_order={order}]", diverged_frac=skip.mean(), images_max_rel=ei, loss_rel=el,
+           grad_rel_l2=eg, events_per_photon=st["events"] / p.n_photons)
+    assert st["events_stored"] == st["events"] <= order * p.n_photons
+    assert ei < 1e-4 and el < 1e-4 and eg < 1e-3, (ei, el, eg)
+
+
 def test_full_gradient_classic_estimator(m, torch):
     """Full gradient of the classic local estimate (path score plus shadow-ray terms) against
     the oracle's, photons that FP32 and FP64 send apart excluded from both."""
