@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--grad", default="full", choices=["full", "surrogate"])
     ap.add_argument("--grid-dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--ref-photons", type=float, default=2e4, help="photons per oracle step (bounded sample)")
-    ap.add_argument("--recon-iters", type=int, default=50, help="iterations of --study recon; --study haze runs 2x for L-BFGS")
+    ap.add_argument("--recon-iters", type=int, default=50,
+                    help="iterations of --study recon; --study haze runs 2x for L-BFGS")
     ap.add_argument("--render-photons", type=float, default=1e8, help="photons per render of --study haze")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -662,8 +663,9 @@ def run_haze_study(args):
     density) with the Laplacian prior (Eq. Cost, eta = 3000: eta Psi of the true field equals
     the loss's noise floor at 1e8 photons) and without it; the same with a single-scattering
     model (max order 1, the paper's Table 1 baseline), and the full model started from that
-    result (the table's third column); the paper's surrogate loop (Eq. GD, N_GD = 5) from
-    beta_aerosol = 0, its null initialisation, with Q = I and Q = 1 / ray count.
+    result (the table's third column); the full model with the altitude-weighted prior (Sec. 6,
+    W = 1 + z / 2 km); the paper's surrogate loop (Eq. GD, N_GD = 5) from beta_aerosol = 0, its
+    null initialisation, with Q = I and Q = 1 / ray count.
     Prints one JSON line: epsilon = |b - b_true|_1 / |b_true|_1 and delta_mass along each run
     (aerosol only; air is known), its renders and GPU+host time, and the loss of the true field
     (the noise floor)."""
@@ -716,6 +718,23 @@ def run_haze_study(args):
         out[name] = {"initial": errs(b_start), "max_order": order, "iterations": st.it, "renders": st.n_renders,
                      "s": time.perf_counter() - t0, "loss0": st.losses[0], "final": errs(st.beta),
                      "trace": trace[::10] + trace[-1:]}
+    # the altitude-weighted prior of Sec. 6 (Psi = |W Lap beta|^2, W diagonal in altitude), W = 1 + z / 2 km:
+    # smoother aloft, where fewer and more oblique rays see each voxel; eta scaled so that eta Psi_W of the
+    # true field again equals the noise floor
+    z = (np.arange(sc.shape[2]) + 0.5) * sc.h[2]
+    grid.set_reg_weights(1.0 + z / 2000.0)
+    eta_w = out["true_field"]["loss"] / grid.regularizer(bt, 1.0).item()
+    trace = []
+    t0 = time.perf_counter()
+    st = m.reconstruct(grid, meas, beta0, m.make_params(p, grad_mode="full", reg_eta=eta_w),
+                       iters=2 * args.recon_iters, method="lbfgs", mask=mask, block=block,
+                       callback=lambda s: trace.append({"it": s.it, "loss": s.losses[-1], **errs(s.beta)}))
+    torch.cuda.synchronize()
+    grid.set_reg_weights(None)
+    out["lbfgs_full_altitude_prior"] = {"initial": errs(beta0), "W": "1 + z / 2 km", "eta": eta_w,
+                                        "iterations": st.it, "renders": st.n_renders, "s": time.perf_counter() - t0,
+                                        "loss0": st.losses[0], "final": errs(st.beta),
+                                        "trace": trace[::10] + trace[-1:]}
     P = m.Blocks(sc.shape, block)
     for cond in ("none", "inv_count"):
         prm = m.make_params(p, grad_mode="surrogate", conditioning=cond, reg_eta=eta)
