@@ -227,6 +227,29 @@ def test_pixel_chords_sum(orc):
         off += W * H
 
 
+def test_pixel_chords_sum_wide_field(orc):
+    """The same identity for wide pinholes on a flat, wide box (the haze reconstruction's
+    cameras: 150 deg, rays up to 79 deg from the axis, chords of up to ~10 km through voxels of
+    625 x 625 x 83 m), including a camera looking sideways from inside the box."""
+    shape, h = (20, 20, 30), (625.0, 625.0, 10000.0 / 120)
+    pos = [(3100.0, 4700.0, 1.0), (9350.0, 6300.0, 1.0), (6300.0, 6300.0, 1200.0)]
+    rots = [synth.look_up_rot(), synth.look_up_rot(), synth.look_at_rot([0.3, 1.0, 0.05])]
+    sc = synth.make_scene(shape, h, np.zeros(int(np.prod(shape))), synth.make_cameras(pos, 8, 6, 150.0, rots=rots))
+    V = float(np.prod(sc.h))
+    one = np.ones((sc.n_cams, sc.nvox))
+    img = orc.images(sc, one * V, one)
+    lo, hi = rg.box(sc)
+    off = 0
+    for c in range(sc.n_cams):
+        W, H = sc.cam_w[c], sc.cam_h[c]
+        for p in range(W * H):
+            i, j = p % W, p // W
+            ref = np.mean([rg.chord(sc.cam_pos[c], d, lo, hi) for d in rg.subpixel_dirs(sc, c, i, j)])
+            assert abs(img[off + p] - ref) < 1e-9 * max(ref, 1.0), (c, p, img[off + p], ref)
+        off += W * H
+    assert img.max() > 8000.0  # oblique rays cross the 2.5 km high box over ~10 km
+
+
 def test_pixel_integral_brute_force(orc):
     """Per-voxel chord attribution: image of an arbitrary field equals the dense line integral."""
     sc, _ = synth.cfg_blobs16()
