@@ -329,8 +329,8 @@ def refine(coarse: np.ndarray, coarse_shape, factor) -> np.ndarray:
 
 
 def cfg_haze80(n_photons: int = 100_000_000, seed: int = 1, fov_deg: float = 150.0):
-    """The paper's reconstruction setting (Sec. 7), synthetic: a 50 x 50 x 10 km atmosphere on
-    80 x 80 x 120 voxels (625 x 625 x 83.3 m); aerosol haze blobs defined on the coarse 20 x 20
+    """The paper's rendering and reconstruction setting (Secs. 4 and 7), synthetic: a 50 x 50 x
+    10 km atmosphere on 80 x 80 x 120 voxels (625 x 625 x 83.3 m); aerosol haze blobs defined on the coarse 20 x 20
     x 40 grid (blocks of 4 x 4 x 3 voxels) over air at 550 nm (0.0116 1/km at the ground, 8 km
     scale height); sun at 45 deg zenith; 36 ground cameras 7 km apart on a 6 x 6 lattice,
     looking up, 64 x 64 pixels. The paper's cameras are hemispherical; these are pinholes of
