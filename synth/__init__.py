@@ -330,9 +330,9 @@ def refine(coarse: np.ndarray, coarse_shape, factor) -> np.ndarray:
 
 def cfg_haze80(n_photons: int = 100_000_000, seed: int = 1, fov_deg: float = 150.0):
     """The paper's rendering and reconstruction setting (Secs. 4 and 7), synthetic: a 50 x 50 x
-    10 km atmosphere on 80 x 80 x 120 voxels (625 x 625 x 83.3 m); aerosol haze blobs defined on the coarse 20 x 20
-    x 40 grid (blocks of 4 x 4 x 3 voxels) over air at 550 nm (0.0116 1/km at the ground, 8 km
-    scale height); sun at 45 deg zenith; 36 ground cameras 7 km apart on a 6 x 6 lattice,
+    10 km atmosphere on 80 x 80 x 120 voxels (625 x 625 x 83.3 m); aerosol haze blobs defined on
+    the coarse 20 x 20 x 40 grid (blocks of 4 x 4 x 3 voxels) over air at 550 nm (0.0116 1/km at
+    the ground, 8 km scale height); sun at 45 deg zenith; 36 ground cameras 7 km apart on a 6 x 6 lattice,
     looking up, 64 x 64 pixels. The paper's cameras are hemispherical; these are pinholes of
     fov_deg horizontal field of view (150 deg: the image corners see 79 deg from the zenith).
     Aerosol albedo 0.9 and g 0.7 (the paper leaves both to its haze model). Returns (scene with
