@@ -114,14 +114,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_record(kernel):
+def traffic_record(kernel, photons):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel source
-    has not changed since the capture (else None)."""
+    has not changed since the capture and the launch traces the captured photon count (else
+    None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             d = json.load(f)
         src = open(os.path.join(ROOT, "paper_1512_02110_gb300", "csrc", "transport.cu"), "rb").read()
-        if d.get("transport_cu_sha1") != hashlib.sha1(src).hexdigest():
+        if d.get("transport_cu_sha1") != hashlib.sha1(src).hexdigest() or int(d.get("photons", -1)) != int(photons):
             return None
         rec = d.get("kernels", {}).get(kernel)
         return None if rec is None else float(rec["dram_bytes_per_launch_full"])
@@ -312,7 +313,7 @@ def run_ours(args):
     achieved_ops = aops / calls_per_step / per_launch_s
     hbm_peak, peak_kind = peaks()
     hbm_achieved = abytes / calls_per_step / per_launch_s / 1e9
-    traffic = traffic_record(kern)
+    traffic = traffic_record(kern, n)
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                 "unit": "TOP/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz",
