@@ -614,6 +614,85 @@ def test_full_gradient_matches_fd_crn(orc):
     assert np.median(np.abs(tg)) > 5.0, tg
 
 
+def _voxel_chords(sc, d, o):
+    """Chord of the ray o + t d (t >= 0) in every voxel of the scene, by the slab method on each
+    voxel box (dense [nvox] array; no voxel walk)."""
+    nx, ny, nz = sc.shape
+    h = np.array(sc.h)
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lo = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1) * h
+    hi = lo + h
+    t0 = np.zeros(lo.shape[0])
+    t1 = np.full(lo.shape[0], np.inf)
+    for a in range(3):
+        if d[a] == 0.0:
+            out = (o[a] < lo[:, a]) | (o[a] > hi[:, a])
+            t1 = np.where(out, -np.inf, t1)
+            continue
+        ta, tb = (lo[:, a] - o[a]) / d[a], (hi[:, a] - o[a]) / d[a]
+        t0, t1 = np.maximum(t0, np.minimum(ta, tb)), np.minimum(t1, np.maximum(ta, tb))
+    return np.maximum(t1 - t0, 0.0)
+
+
+def _voxelised_slab_images(sc, beta, albedo, mu0, chords):
+    """Expectation of the voxelised first-order images (Eq. Lcupdate, Eq. Icpixel) of a homogeneous
+    slab with isotropic scattering, far from its lateral edges. Photons enter the top along the
+    sun (cosine mu0) with weight F mu0 A / N, so first collisions have density
+    (N / A) (beta / mu0) exp(-beta z' / mu0) per unit volume at depth z' below the top, and each adds
+    albedo I0 / (4 pi): E[L_c(k)] = albedo F beta / (4 pi) dx dy (mu0 / beta)
+    (exp(-beta (H - z1) / mu0) - exp(-beta (H - z0) / mu0)) over the voxel's layer [z0, z1], F = 1.
+    Then i_p = 1 / (N_rays V) sum_rho sum_k l^rho(k) T_c(k) E[L_c(k)] with T_c(k) from the voxel
+    centre to the camera (Eq. Tck)."""
+    nx, ny, nz = sc.shape
+    hx, hy, hz = sc.h
+    H, V = nz * hz, hx * hy * hz
+    z0 = np.repeat(np.arange(nz) * hz, nx * ny)
+    EL = albedo * beta / (4 * math.pi) * hx * hy * (mu0 / beta) * (
+        np.exp(-beta * (H - z0 - hz) / mu0) - np.exp(-beta * (H - z0) / mu0))
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cen = (np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1) + 0.5) * np.array(sc.h)
+    T = np.exp(-beta * np.linalg.norm(cen - sc.cam_pos[0], axis=1))
+    return np.array([sum(float(np.dot(l, T * EL)) for l in ls) for ls in chords]) / (sc.n_rays * V)
+
+
+@pytest.mark.slow
+def test_voxelised_gradient_along_beta_matches_the_slab_expectation(orc):
+    """The full gradient of the voxelised estimator (score of the free-flight density through L,
+    Sec. 5.1 Eq. divCost1 with Eq. beer-lambert, plus the W^T term through T), first order, in the
+    homogeneous slab with the camera on the floor: with a measured value M far above the images the
+    loss is linear in them, so beta . dE/dbeta / (-2M) estimates sum_p tau d i_p / d tau, the
+    derivative along beta of the voxelised model's expected images, which the closed form of the
+    first-collision density gives exactly (no voxelisation bias: the reference is the voxelised
+    model itself). The images are pinned against the same expectation. Planted in the oracle, a
+    20 % scale error in the suffix sums S_j moves the estimate by ~20 sigma, one in the chord term
+    of the score by ~7 sigma and one in the collision term 1 / beta by ~60 sigma."""
+    beta, albedo = 2.5e-3, 0.9
+    sc = slab_scene(beta)
+    p = synth.Params(albedo=albedo, g=0.0, sun_zenith=math.radians(30), n_photons=16_000_000, seed=25, max_order=1,
+                     rr_threshold=0.0)
+    M = 1e6
+    meas = np.full(sc.n_pix, M)
+
+    def one(q):
+        r = orc.full_grad(sc, q, meas)
+        return [float(np.dot(sc.beta, r["grad"])) / (-2.0 * M), float(r["images"].sum())]
+
+    nb = 32
+    out = batched(orc, sc, p, nb, one)
+    est, sig = out[:, 0].sum(), out[:, 0].std(ddof=1) * math.sqrt(nb)
+    img, isig = out[:, 1].sum(), out[:, 1].std(ddof=1) * math.sqrt(nb)
+    mu0 = math.cos(p.sun_zenith)
+    chords = [[_voxel_chords(sc, d, sc.cam_pos[0]) for d in rg.subpixel_dirs(sc, 0, pix % 4, pix // 4)]
+              for pix in range(16)]
+    ref_img = _voxelised_slab_images(sc, beta, albedo, mu0, chords).sum()
+    e = 1e-4
+    ref = (_voxelised_slab_images(sc, beta * (1 + e), albedo, mu0, chords).sum()
+           - _voxelised_slab_images(sc, beta * (1 - e), albedo, mu0, chords).sum()) / (2 * e)
+    assert abs(img - ref_img) < 3.5 * isig, (img, ref_img, isig)
+    assert abs(est - ref) < 3.5 * sig, (est, ref, sig)
+    assert abs(ref) > 30 * sig  # resolved
+
+
 @pytest.mark.slow
 def test_classic_gradient_along_beta_matches_the_slab_closed_form(orc):
     """Classic-estimator gradient (path score plus shadow-ray terms), first order in the
