@@ -73,7 +73,7 @@ def lib():
         L.or_rotate.argtypes = [P, ctypes.c_double, ctypes.c_double, P]
         L.or_radical_inverse.argtypes = [ctypes.c_int, ctypes.c_int]
         L.or_radical_inverse.restype = ctypes.c_double
-        L.or_render.argtypes = [P, P, P, P, P, P, P, ctypes.c_int]
+        L.or_render.argtypes = [P, P, P, P, P, P, P, ctypes.c_int, P]
         L.or_transmittance.argtypes = [P, P, P]
         L.or_los_adjoint.argtypes = [P, P, P]
         L.or_images.argtypes = [P, P, P, P]
@@ -191,8 +191,10 @@ def radical_inverse(base: int, i: int) -> float:
 # the method
 
 
-def render(scene, params, want_L=True, classic=False, hashes=False, skip=None, nthreads=0):
-    """Forward MC. Returns dict(L [C,nvox] or None, classic [npix] or None, stats, hash)."""
+def render(scene, params, want_L=True, classic=False, hashes=False, skip=None, nthreads=0, points=False):
+    """Forward MC. Returns dict(L [C,nvox] or None, classic [npix] or None, stats, hash, point):
+    point [n, 3] (points=True) is each photon's last event point in grid coordinates (metres
+    from the grid origin; the launch point for a photon without events)."""
     b = _Bound(scene)
     q = _params(params)
     L = np.zeros((scene.n_cams, scene.nvox)) if want_L else None
@@ -200,8 +202,9 @@ def render(scene, params, want_L=True, classic=False, hashes=False, skip=None, n
     st = np.zeros(16)
     h = np.zeros(params.n_photons, np.uint32) if hashes else None
     sk = None if skip is None else np.ascontiguousarray(skip, dtype=np.uint8)
-    lib().or_render(b.ref, ctypes.byref(q), _ptr(L), _ptr(ci), _ptr(st), _ptr(h), _ptr(sk), int(nthreads))
-    return dict(L=L, classic=ci, stats=dict(zip(ST_NAMES, st.tolist())), hash=h)
+    pt = np.zeros((params.n_photons, 3)) if points else None
+    lib().or_render(b.ref, ctypes.byref(q), _ptr(L), _ptr(ci), _ptr(st), _ptr(h), _ptr(sk), int(nthreads), _ptr(pt))
+    return dict(L=L, classic=ci, stats=dict(zip(ST_NAMES, st.tolist())), hash=h, point=pt)
 
 
 def transmittance(scene, beta=None):

@@ -419,6 +419,7 @@ typedef struct {
     const double *cres; /* dE/di per pixel [sum W*H] or NULL (classic-estimator gradient replay) */
     double *gsh;       /* [nvox] receives the shadow-ray terms of the classic-estimator gradient */
     path_rec *rec;     /* non-NULL in full-gradient replay */
+    double last[3];    /* the traced photon's last event point (its launch point before any) */
 } tctx;
 
 static void rec_seg(path_rec *r, long k, double len, int flight) {
@@ -494,6 +495,7 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
     double d[3] = {c->sun[0], c->sun[1], c->sun[2]};
     double I = c->I0;
     double tau = -log(1.0 - u[2]);
+    for (int q = 0; q < 3; ++q) c->last[q] = X[q];
     c->stats[ST_LAUNCHED] += I;
     c->stats[ST_TRACED] += 1.0;
     uint32_t hash = FNV_OFFSET;
@@ -509,6 +511,7 @@ static uint32_t trace_photon(tctx *c, uint64_t p) {
             break;
         }
         s_ev += 1;
+        for (int q = 0; q < 3; ++q) c->last[q] = Xn[q];
         long k = lin(s, vn);
         hash = (hash ^ (uint32_t)k) * FNV_PRIME;
         c->stats[ST_EVENTS] += 1.0;
@@ -605,6 +608,27 @@ static void tctx_init(tctx *c, const or_scene *s, const or_params *P) {
     c->nvox = nvox_of(s);
 }
 
+/* The deterministic stages run on the OpenMP default team; a call that asks for a thread count
+ * sets it for its whole duration (and restores it), so that every stage uses that many. */
+static int threads_begin(int req) {
+#ifdef _OPENMP
+    const int prev = omp_get_max_threads();
+    if (req > 0) omp_set_num_threads(req);
+    return prev;
+#else
+    (void)req;
+    return 1;
+#endif
+}
+
+static void threads_end(int prev) {
+#ifdef _OPENMP
+    omp_set_num_threads(prev);
+#else
+    (void)prev;
+#endif
+}
+
 static int nthreads_of(int req) {
 #ifdef _OPENMP
     return req > 0 ? req : omp_get_max_threads();
@@ -616,9 +640,11 @@ static int nthreads_of(int req) {
 
 /* Forward render: L [C][nvox] (may be NULL), classic images (may be NULL), stats [16],
  * per-photon hash (may be NULL), skip mask (may be NULL: photons with skip[p] != 0 are
- * not traced). Photon ids run from photon_offset to photon_offset + n_photons - 1. */
+ * not traced), per-photon last event point [n][3] in grid coordinates (may be NULL; the launch
+ * point for a photon without events). Photon ids run from photon_offset to
+ * photon_offset + n_photons - 1. */
 void or_render(const or_scene *s, const or_params *P, double *L, double *cimg, double *stats, uint32_t *hash,
-               const uint8_t *skip, int nthreads) {
+               const uint8_t *skip, int nthreads, double *last_pt) {
     const long nvox = nvox_of(s);
     const long nL = (long)s->n_cams * nvox, nI = total_pixels(s);
     int nt = nthreads_of(nthreads);
@@ -645,6 +671,8 @@ void or_render(const or_scene *s, const or_params *P, double *L, double *cimg, d
             }
             uint32_t h = trace_photon(&c, P->photon_offset + (uint64_t)i);
             if (hash) hash[i] = h;
+            if (last_pt)
+                for (int q = 0; q < 3; ++q) last_pt[3 * i + q] = c.last[q] - s->o[q];
         }
     }
     for (int t = 0; t < nt; ++t) {
@@ -686,6 +714,9 @@ static void scat_visit(void *cc, long k, double len) {
 void or_los_adjoint(const or_scene *s, const double *sv, double *gT) {
     const long nvox = nvox_of(s);
     memset(gT, 0, sizeof(double) * (size_t)s->n_cams * nvox);
+    /* one camera per thread: each camera's rows are summed by one thread in voxel order, so the
+     * result does not depend on the thread count */
+#pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < s->n_cams; ++c) {
         const double *Pc = s->cam_pos + 3 * c;
         for (long k = 0; k < nvox; ++k) {
@@ -742,6 +773,8 @@ void or_backproject(const or_scene *s, const double *rr, double *b) {
     const long nvox = nvox_of(s);
     const double V = s->h[0] * s->h[1] * s->h[2];
     memset(b, 0, sizeof(double) * (size_t)s->n_cams * nvox);
+    /* one camera per thread, its pixels in order: independent of the thread count */
+#pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < s->n_cams; ++c) {
         const int W = s->cam_w[c], H = s->cam_h[c];
         const long off = pix_offset(s, c);
@@ -1026,7 +1059,8 @@ void or_full_grad(const or_scene *s, const or_params *P, const double *meas, con
     double *gT = (double *)malloc(sizeof(double) * nL);
     double *rr = (double *)malloc(sizeof(double) * np);
     double st_local[ST_N];
-    or_render(s, P, L, NULL, stats ? stats : st_local, NULL, skip, nthreads);
+    const int prev_threads = threads_begin(nthreads);
+    or_render(s, P, L, NULL, stats ? stats : st_local, NULL, skip, nthreads, NULL);
     or_transmittance(s, NULL, T);
     or_images(s, L, T, img);
     double E = residual(s, img, meas, mask, rr);
@@ -1050,6 +1084,7 @@ void or_full_grad(const or_scene *s, const or_params *P, const double *meas, con
         free(gr);
     }
     *loss = E;
+    threads_end(prev_threads);
     free(adj);
     if (!L_out) free(L);
     free(T); free(b); free(sv); free(gT); free(rr);
@@ -1067,7 +1102,7 @@ void or_full_grad_classic(const or_scene *s, const or_params *P, const double *m
     double *rr = (double *)malloc(sizeof(double) * np);
     double st_local[ST_N];
     for (long p = 0; p < np; ++p) img[p] = 0.0;
-    or_render(s, P, NULL, img, stats ? stats : st_local, NULL, skip, nthreads);
+    or_render(s, P, NULL, img, stats ? stats : st_local, NULL, skip, nthreads, NULL);
     double E = residual(s, img, meas, mask, rr);
     for (long k = 0; k < nvox; ++k) grad[k] = 0.0;
     replay_score(s, P, nthreads, NULL, rr, skip, grad);
