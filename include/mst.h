@@ -325,6 +325,15 @@ int mst_set_replay_memory(mst_grid *g, uint64_t bytes);
  * Both are indexed by the call's photon index (0 .. n_photons-1). */
 int mst_set_debug(mst_grid *g, uint32_t *photon_hash_dev, const uint8_t *photon_skip_dev);
 
+/* Validation aid for the forward render, kept on the handle until replaced (NULL: off):
+ *   photon_point_dev [n_photons][4] float: each traced photon's last event point (its launch
+ *     point if it had no event) as the offset inside its voxel (x, y, z in metres, entries 0-2)
+ *     and the voxel packed as ix | iy << 11 | iz << 22 (entry 3, the bits of a uint32). With the
+ *     path checksum this tells whether FP32 carried the photon along the path of an FP64
+ *     reference: positions drift apart along long paths (Sec. 2.1.2 steps ii-iii) even where
+ *     the voxels agree. Indexed by the call's photon index; skipped photons are not written. */
+int mst_set_debug_points(mst_grid *g, float *photon_point_dev);
+
 /* Copies the statistics of the last render call (MST_NSTATS doubles: escaped weight per face,
  * absorbed, roulette, segment and event counts) to the host. Synchronises the device. */
 int mst_get_stats(mst_grid *g, double *stats_host);

@@ -37,7 +37,7 @@ STAT_NAMES = ["esc_xm", "esc_xp", "esc_ym", "esc_yp", "esc_zm", "esc_zp", "absor
               "air_events"]
 EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy", "mst_render", "mst_render_grad",
            "mst_transmittance", "mst_form_images", "mst_surrogate_grad", "mst_ray_counts", "mst_regularizer",
-           "mst_set_debug", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
+           "mst_set_debug", "mst_set_debug_points", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",
            "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
            "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory", "mst_render_bmc",
            "mst_set_reg_weights", "mst_set_air", "mst_render_grad_channels", "mst_sun_mask",
@@ -94,6 +94,7 @@ def _load():
     L.mst_ray_counts.argtypes = [P, P, P]
     L.mst_regularizer.argtypes = [P, P, D, P, P, P]
     L.mst_set_debug.argtypes = [P, P, P]
+    L.mst_set_debug_points.argtypes = [P, P]
     L.mst_set_replay_memory.argtypes = [P, ctypes.c_uint64]
     L.mst_set_reg_weights.argtypes = [P, P]
     L.mst_set_air.argtypes = [P, P, ctypes.c_double]
@@ -291,6 +292,12 @@ class Grid:
     def set_debug(self, photon_hash=None, photon_skip=None):
         self._check(lib.mst_set_debug(self._h, _ptr(photon_hash), _ptr(photon_skip)), "mst_set_debug")
         self._dbg = (photon_hash, photon_skip)  # keep alive while attached
+
+    def set_debug_points(self, points=None):
+        """points: float32 CUDA tensor [n_photons, 4] receiving each photon's last event point
+        (offset inside the voxel, then the packed voxel as uint32 bits), or None."""
+        self._check(lib.mst_set_debug_points(self._h, _ptr(points)), "mst_set_debug_points")
+        self._dbg_points = points  # keep alive while attached
 
     def stats(self) -> dict:
         out = np.zeros(NSTATS)

@@ -127,6 +127,7 @@ TransportArgs transport_args(mst_grid* g, const mst_params* p) {
     a.hg.tg = (float)(2.0 * gg);
     a.hg.iso = std::fabs(gg) < 1e-6;
     a.beta = g->ext;
+    a.beta_pad = g->ext_pad;
     a.beta_air = g->air;  // two species (Sec. 2): the particle of each event is drawn
     a.beta_aer = g->air ? g->beta_in : nullptr;
     a.albedo_air = (float)g->albedo_air;
@@ -157,6 +158,7 @@ TransportArgs transport_args(mst_grid* g, const mst_params* p) {
     a.stats = g->stats;
     a.hash = g->dbg_hash;
     a.skip = g->dbg_skip;
+    a.point = g->dbg_point;
     return a;
 }
 
@@ -192,7 +194,7 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
     const int b_fwd = transport_blocks(g, p->grid_dtype, est);
     const int b_p1 = transport_blocks(g, p->grid_dtype, m_p1);
     const int b_p2 = transport_blocks(g, p->grid_dtype, m_p2);
-    if (replay) set_fold(a, (uint64_t)g->geo.nvox);
+    if (replay) set_fold(a, (uint64_t)g->geo.npad);
     else if (est == MST_EST_VOXEL) set_fold(a, (uint64_t)g->geo.nvox * g->cp);
     if (store_events) {
         a.evrec = g->evrec;
@@ -253,7 +255,7 @@ int run_photons(mst_grid* g, const mst_params* p, bool replay, double* cimg, cud
 int run_replay_stored(mst_grid* g, const mst_params* p, cudaStream_t st) {
     TransportArgs a = transport_args(g, p);
     const uint64_t n = p->n_photons;
-    set_fold(a, (uint64_t)g->geo.nvox);
+    set_fold(a, (uint64_t)g->geo.npad);
     a.evrec = g->evrec;
     a.ev_cap = g->ev_cap;
     a.ev_count = g->ev_count;
@@ -421,7 +423,7 @@ double radical_inverse(int base, int i) {
 }
 
 void free_all(mst_grid* g) {
-    void* ptrs[] = {g->ext, g->Lacc, g->L64, g->T, g->R, g->bacc, g->gT, g->adj, g->gacc, g->g64,
+    void* ptrs[] = {g->ext, g->ext_pad, g->Lacc, g->L64, g->T, g->R, g->bacc, g->gT, g->adj, g->gacc, g->g64,
                     g->resid, g->cimg, g->lap, g->omega, g->Qw, g->stats, g->tickets, g->wbuf, g->nevbuf, g->plist, g->score_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -530,6 +532,11 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
     geo.ex = (float)(d->nx * d->dx); geo.ey = (float)(d->ny * d->dy); geo.ez = (float)(d->nz * d->dz);
     geo.nvox = d->nx * d->ny * d->nz;
     geo.max_steps = d->nx + d->ny + d->nz + 8;
+    geo.p0 = d->nx + 2;
+    geo.p01 = (d->nx + 2) * (d->ny + 2);
+    geo.inv_p0 = (float)(1.0 / geo.p0);
+    geo.inv_p01 = (float)(1.0 / geo.p01);
+    geo.npad = geo.p01 * (d->nz + 2);
     for (int a = 0; a < 3; ++a) g->origin[a] = d->origin[a];
     g->voxel_volume = d->dx * d->dy * d->dz;
     g->n_cams = n_cams;
@@ -586,6 +593,7 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
         size_t bytes;
     } allocs[] = {
         {&g->ext, nvox * 4},
+        {&g->ext_pad, (size_t)geo.npad * 4},
         {(void**)&g->Lacc, nvox * g->cp * 4},
         {(void**)&g->L64, C * nvox * 8},
         {(void**)&g->T, C * nvox * 4},
@@ -593,7 +601,7 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
         {(void**)&g->bacc, C * nvox * 4},
         {(void**)&g->gT, C * nvox * 4},
         {(void**)&g->adj, nvox * g->cp * 4},
-        {(void**)&g->gacc, nvox * 4},
+        {(void**)&g->gacc, (size_t)geo.npad * 4},
         {(void**)&g->score_cnt, (2 * kScoreBins + 1) * 4},
         {(void**)&g->g64, nvox * 8},
         {(void**)&g->resid, (size_t)off * 8},
@@ -626,7 +634,7 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
     cudaError_t e = cudaMemcpy(g->omega, om, sizeof(float) * off, cudaMemcpyHostToDevice);
     delete[] om;
     if (e == cudaSuccess) e = cudaMemset(g->Lacc, 0, nvox * g->cp * 4);
-    if (e == cudaSuccess) e = cudaMemset(g->gacc, 0, nvox * 4);
+    if (e == cudaSuccess) e = cudaMemset(g->gacc, 0, (size_t)geo.npad * 4);
     if (e == cudaSuccess) e = cudaMemset(g->stats, 0, MST_NSTATS * 8 + 64);
     if (e != cudaSuccess) {
         free_all(g);
@@ -968,6 +976,12 @@ int mst_set_debug(mst_grid* g, uint32_t* hash, const uint8_t* skip) {
     if (!g) return MST_ERR_INVALID_ARG;
     g->dbg_hash = hash;
     g->dbg_skip = skip;
+    return MST_OK;
+}
+
+int mst_set_debug_points(mst_grid* g, float* points) {
+    if (!g) return MST_ERR_INVALID_ARG;
+    g->dbg_point = reinterpret_cast<float4*>(points);
     return MST_OK;
 }
 

@@ -21,6 +21,12 @@ struct Geo {
     float ex, ey, ez;   // grid extent (m)
     int nvox;
     int max_steps;      // nx + ny + nz + 8: no straight walk crosses more voxels
+    // The photon flights walk a copy of the grid padded with one halo voxel on every side
+    // ([nz + 2][ny + 2][nx + 2], halo extinction +inf), so that leaving the grid needs no bounds
+    // test in the voxel step: the walk stops on the halo's extinction instead.
+    int p0, p01;        // nx + 2, (nx + 2)(ny + 2): strides of the padded grid
+    float inv_p0, inv_p01;
+    int npad;           // (nx + 2)(ny + 2)(nz + 2)
 };
 
 struct Cam {
@@ -154,6 +160,33 @@ __device__ __forceinline__ float3 rotate_dir(float3 d, float ct, float st, float
 // but cost the walk a wrap test and two selects per step.
 
 __device__ __forceinline__ int lin_index(const Geo& g, int ix, int iy, int iz) { return ix + g.nx * (iy + g.ny * iz); }
+
+// index of voxel (ix, iy, iz) in the padded grid (each index may be -1 or n: the halo)
+__device__ __forceinline__ int pad_index(const Geo& g, int ix, int iy, int iz) {
+    return (ix + 1) + g.p0 * (iy + 1) + g.p01 * (iz + 1);
+}
+
+// (ix, iy, iz) of padded index q, each in [-1, n]. The quotients come from FP32 reciprocals and
+// are corrected by one step: q < 2^31 and the quotients are below 2^12, so the FP32 estimate is
+// off by at most one.
+__device__ __forceinline__ void unpad(const Geo& g, int q, int& ix, int& iy, int& iz) {
+    int a = (int)((float)q * g.inv_p01);
+    int r = q - a * g.p01;
+    if (r < 0) { --a; r += g.p01; } else if (r >= g.p01) { ++a; r -= g.p01; }
+    int b = (int)((float)r * g.inv_p0);
+    int c = r - b * g.p0;
+    if (c < 0) { --b; c += g.p0; } else if (c >= g.p0) { ++b; c -= g.p0; }
+    ix = c - 1;
+    iy = b - 1;
+    iz = a - 1;
+}
+
+// linear voxel index of an interior padded index
+__device__ __forceinline__ int unpad_lin(const Geo& g, int q) {
+    int ix, iy, iz;
+    unpad(g, q, ix, iy, iz);
+    return lin_index(g, ix, iy, iz);
+}
 
 template <int DT>
 struct BetaFetch;

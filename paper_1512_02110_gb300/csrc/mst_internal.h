@@ -46,7 +46,8 @@ struct TransportArgs {
     Geo g;
     CamSet cams;
     HG hg;
-    const void* beta;          // staged extinction [nvox] in the compute dtype
+    const void* beta;          // staged extinction [nvox] in the compute dtype (camera and shadow rays)
+    const void* beta_pad;      // the same on the padded grid of the flights (halo +inf)
     const float* beta_air;     // two species: air extinction [nvox] (NULL: one species)
     const float* beta_aer;     // two species: aerosol extinction [nvox], the unknown
     float3 sun;                // photon direction at launch
@@ -63,7 +64,7 @@ struct TransportArgs {
     const float* omega;        // [total pix] pixel solid angles (classic estimator)
     const double* cres;        // [total pix] dE/di of the classic images (classic-estimator gradient)
     const float* adj;          // [nvox][cp] a_c(k) = T_c(k) b_c(k) (replay)
-    float* gacc;               // [nvox] FP32 gradient accumulator (replay)
+    float* gacc;               // [npad] FP32 gradient accumulator on the padded grid (replay)
     double* wbuf;              // [photons of the chunk] W per photon (replay pass 1, stored-event adjoint)
     uint32_t* nevbuf;          // [photons of the chunk] events per photon (replay pass 1, or the forward
                                // when it stores events)
@@ -84,6 +85,7 @@ struct TransportArgs {
     uint32_t fold_nslices;     // slices per sweep
     double* stats;             // [MST_NSTATS]
     uint32_t* hash;            // per-photon checksum or NULL
+    float4* point;             // per-photon last event point (offset, packed voxel) or NULL
     const uint8_t* skip;       // per-photon skip mask or NULL
     unsigned int* ticket;      // per-chunk photon ticket
 };
@@ -102,6 +104,7 @@ struct mst_grid {
 
     // device buffers owned by the handle
     void* ext = nullptr;          // staged extinction [nvox], up to 4 bytes per voxel
+    void* ext_pad = nullptr;      // staged extinction on the padded grid [npad] (photon flights)
     float* Lacc = nullptr;        // [nvox][cp]
     double* L64 = nullptr;        // [C][nvox]
     float* T = nullptr;           // [C][nvox]
@@ -109,7 +112,7 @@ struct mst_grid {
     float* bacc = nullptr;        // [C][nvox]  Pi_c^T (2 r_c)
     float* gT = nullptr;          // [C][nvox]  W_c^T (L T b)
     float* adj = nullptr;         // [nvox][cp] T_c b_c
-    float* gacc = nullptr;        // [nvox]
+    float* gacc = nullptr;        // [npad] gradient tile on the padded grid
     double* wbuf = nullptr;       // [replay_cap], allocated by the first full-gradient call
     uint32_t* nevbuf = nullptr;   // [replay_cap]
     mst::ScoreRec* plist = nullptr;     // [replay_cap]
@@ -162,6 +165,7 @@ struct mst_grid {
 
     uint32_t* dbg_hash = nullptr;
     const uint8_t* dbg_skip = nullptr;
+    float4* dbg_point = nullptr;
     std::string err;
 };
 

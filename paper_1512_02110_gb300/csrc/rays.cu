@@ -28,6 +28,24 @@ __global__ void k_stage(const float* __restrict__ beta, const float* __restrict_
     }
 }
 
+// The grid of the photon flights: the same values on [nz + 2][ny + 2][nx + 2] with a halo of
+// +inf extinction, where a flight stops (a free path never outlasts infinite optical depth).
+template <int DT>
+__global__ void k_stage_pad(const float* __restrict__ beta, const float* __restrict__ air, void* __restrict__ ext,
+                            const Geo g) {
+    typedef typename BetaFetch<DT>::T T;
+    T* out = static_cast<T*>(ext);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.npad; q += gridDim.x * blockDim.x) {
+        const int ix = q % g.p0 - 1, iy = (q / g.p0) % (g.ny + 2) - 1, iz = q / g.p01 - 1;
+        float b = CUDART_INF_F;
+        if (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny && iz >= 0 && iz < g.nz) {
+            const int k = lin_index(g, ix, iy, iz);
+            b = air ? beta[k] + air[k] : beta[k];
+        }
+        out[q] = BetaFetch<DT>::make(b);
+    }
+}
+
 // beta_ref + beta_air in FP32 (the surrogate's reference total)
 __global__ void k_add_air(const float* __restrict__ beta, const float* __restrict__ air, float* __restrict__ out,
                           int nvox) {
@@ -282,6 +300,12 @@ cudaError_t launch_stage(const mst_grid* g, const float* beta, const float* air,
     if (dtype == 0) k_stage<0><<<nb, kTB, 0, st>>>(beta, air, g->ext, tot, nvox);
     else if (dtype == 1) k_stage<1><<<nb, kTB, 0, st>>>(beta, air, g->ext, tot, nvox);
     else k_stage<2><<<nb, kTB, 0, st>>>(beta, air, g->ext, tot, nvox);
+    if (g->ext_pad) {
+        const int np = nblocks(g->geo.npad, kTB, 4096);
+        if (dtype == 0) k_stage_pad<0><<<np, kTB, 0, st>>>(beta, air, g->ext_pad, g->geo);
+        else if (dtype == 1) k_stage_pad<1><<<np, kTB, 0, st>>>(beta, air, g->ext_pad, g->geo);
+        else k_stage_pad<2><<<np, kTB, 0, st>>>(beta, air, g->ext_pad, g->geo);
+    }
     return cudaGetLastError();
 }
 

@@ -132,44 +132,115 @@ __device__ __forceinline__ void launch_photon(const TransportArgs& A, Photon& ph
     ph.hash = kFnvOffset;
 }
 
-// steps ii-iii, one voxel of a free flight (Eq. MCextinct). Returns -1 while the flight goes
-// on, kCollided on a collision (ph.p and the voxel updated) or the exit face 0..5
-// (kWalkOverflow if the walk was abandoned). With S != 0 it also scatters the score of the
-// flight into the gradient tile: -S * length in every voxel crossed and S * (1/beta - length)
-// in the collision voxel. With two species (TWO) the collision voxel's term waits for the
-// particle: the flight keeps its partial length there in ph.tau (spent once the flight has
-// collided) and the event adds S * ([aerosol] / beta_aer - length) in one atomic.
-constexpr int kCollided = -2;
+// A free flight (steps ii-iii) on the padded grid. Per axis: the distance along the ray from
+// the current point to the next face (t), the distance between faces (q = h / |d|), and the change
+// of the padded index when a face is crossed (+-1, +-(nx + 2), +-(nx + 2)(ny + 2); 0 for an axis
+// the ray does not move along, whose t stays +inf); `lin` is the current voxel's padded index.
+// A voxel step subtracts the step from two axes and resets the crossed one to q, so every
+// quantity stays of the size of one voxel and FP32 keeps ~1e-6 m resolution anywhere in the grid.
+// Ties go to x, then y, then z. Leaving the grid needs no test in the step: the first halo voxel
+// has extinction +inf, so its optical depth exceeds any free path and the flight stops there.
+struct Flight {
+    float tx, ty, tz;
+    float qx, qy, qz;
+    int dx, dy, dz;
+    int lin;
+    int left;  // voxel steps left before a flight is abandoned (only a non-finite direction gets there)
+};
 
-template <int DT, bool TWO>
-__device__ __forceinline__ int flight_step(const TransportArgs& A, Photon& ph, Walk& w, float& tau, float S,
-                                           unsigned& nsc) {
-    const float b = BetaFetch<DT>::get(A.beta, w.lin);
-    float seg;
-    const int a = walk_axis(w, seg);
-    const float bs = b * seg;
-    if (tau <= bs) {
-        const float l = tau / b;
-        ph.p = walk_local(w, A.g, l);
-        ph.ix = w.ix;
-        ph.iy = w.iy;
-        ph.iz = w.iz;
-        if (S != 0.f) {
-            if constexpr (TWO) {
-                ph.tau = l;
-            } else {
-                atomicAdd(A.gacc + w.lin, S * (1.f / b - l));
-                ++nsc;
-            }
-        }
-        return kCollided;
+// 1 / |d| by the hardware reciprocal (__fdividef, within 2 ulp)
+__device__ __forceinline__ void flight_axis(float p, float d, float h, int stride, float& t, float& q, int& dl) {
+    if (d > 0.f) {
+        const float inv = __fdividef(1.f, d);
+        t = (h - p) * inv;
+        q = h * inv;
+        dl = stride;
+    } else if (d < 0.f) {
+        const float inv = __fdividef(1.f, -d);
+        t = p * inv;
+        q = h * inv;
+        dl = -stride;
+    } else {
+        t = CUDART_INF_F;
+        q = CUDART_INF_F;
+        dl = 0;
     }
-    if (S != 0.f && seg > 0.f) {
-        atomicAdd(A.gacc + w.lin, -S * seg);
+}
+
+// the flight of photon ph from its point (voxel + offset) along its direction
+__device__ __forceinline__ void flight_init(Flight& f, const Geo& g, const Photon& ph) {
+    flight_axis(fminf(fmaxf(ph.p.x, 0.f), g.hx), ph.d.x, g.hx, 1, f.tx, f.qx, f.dx);
+    flight_axis(fminf(fmaxf(ph.p.y, 0.f), g.hy), ph.d.y, g.hy, g.p0, f.ty, f.qy, f.dy);
+    flight_axis(fminf(fmaxf(ph.p.z, 0.f), g.hz), ph.d.z, g.hz, g.p01, f.tz, f.qz, f.dz);
+    f.lin = pad_index(g, ph.ix, ph.iy, ph.iz);
+    f.left = g.max_steps;
+}
+
+// One voxel of a free flight (Eq. MCextinct): the free path tau runs out in this voxel when
+// tau <= beta * (distance to the next face). Returns true then, or when the voxel is the halo
+// (beta = +inf; the caller tells the two apart by b), with b and the face distance m of the voxel;
+// false after crossing into the next voxel. SCORE (replay pass 2): every voxel the flight crosses
+// receives -S * length in the gradient tile (padded like the grid).
+template <int DT, bool SCORE>
+__device__ __forceinline__ bool flight_step(const TransportArgs& A, Flight& f, float& tau, float& b, float& m, float S,
+                                            unsigned& nsc) {
+    b = BetaFetch<DT>::get(A.beta_pad, f.lin);
+    m = fminf(f.tx, fminf(f.ty, f.tz));
+    const float bs = b * m;
+    if (!(tau > bs)) return true;
+    tau -= bs;
+    if (SCORE && S != 0.f && m > 0.f) {
+        atomicAdd(A.gacc + f.lin, -S * m);
         ++nsc;
     }
-    tau -= bs;
-    return walk_step<false>(w, A.g, a, seg);  // the kernel bounds the crossings once per trip
+    const bool px = f.tx <= m;
+    const bool py = !px && f.ty <= m;
+    f.tx = px ? f.qx : f.tx - m;
+    f.ty = py ? f.qy : f.ty - m;
+    f.tz = (px || py) ? f.tz - m : f.qz;
+    f.lin += px ? f.dx : (py ? f.dy : f.dz);
+    return false;
+}
+
+// offset along one axis, inside the current voxel, of the point a distance l past the current
+// point (d: the direction component; p0: the flight's start offset, kept when d = 0)
+__device__ __forceinline__ float flight_offset(float t, float d, float h, float p0, float l) {
+    const float v = d > 0.f ? h - (t - l) * d : (d < 0.f ? (t - l) * -d : p0);
+    return fminf(fmaxf(v, 0.f), h);
+}
+
+// Exit face (0..5: x-, x+, y-, y+, z-, z+) of a flight that reached halo voxel `lin`.
+__device__ __forceinline__ int halo_face(const Geo& g, int lin) {
+    int ix, iy, iz;
+    unpad(g, lin, ix, iy, iz);
+    return ix < 0 ? 0 : (ix >= g.nx ? 1 : (iy < 0 ? 2 : (iy >= g.ny ? 3 : (iz < 0 ? 4 : 5))));
+}
+
+// A flight that stopped in voxel f.lin (flight_step returned true) with b, m its extinction and
+// face distance: a collision moves the photon to the collision point (offset inside the voxel
+// and the voxel's indices) and returns kCollided; the halo returns the exit face. With S != 0 the
+// collision voxel receives S * (1/beta - length) (one species) or, with two species (TWO), keeps
+// its partial length in ph.tau for the event, which adds S * ([aerosol] / beta_aer - length) once
+// the particle is known.
+constexpr int kCollided = -2;
+
+template <bool TWO>
+__device__ __forceinline__ int flight_end(const TransportArgs& A, Photon& ph, const Flight& f, float tau, float b,
+                                          float S, unsigned& nsc) {
+    if (isinf(b)) return halo_face(A.g, f.lin);
+    const float l = tau / b;
+    ph.p = make_float3(flight_offset(f.tx, ph.d.x, A.g.hx, ph.p.x, l), flight_offset(f.ty, ph.d.y, A.g.hy, ph.p.y, l),
+                       flight_offset(f.tz, ph.d.z, A.g.hz, ph.p.z, l));
+    unpad(A.g, f.lin, ph.ix, ph.iy, ph.iz);
+    if (S != 0.f) {
+        if constexpr (TWO) {
+            ph.tau = l;
+        } else {
+            atomicAdd(A.gacc + f.lin, S * (1.f / b - l));
+            ++nsc;
+        }
+    }
+    return kCollided;
 }
 
 // cosine between the photon direction and the direction from the photon to camera c, and the
@@ -297,7 +368,9 @@ __device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon
             if (OP == 2) {
                 const float sw = -cr * val;
                 walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p,
-                               [&](const Walk& wk, float len) { atomicAdd(gacc + wk.lin, sw * len); }, ns);
+                               [&](const Walk& wk, float len) {
+                                   atomicAdd(gacc + pad_index(A.g, wk.ix, wk.iy, wk.iz), sw * len);
+                               }, ns);
             }
         }
     }
@@ -344,6 +417,9 @@ __device__ __forceinline__ void finish_photon(const TransportArgs& A, const Phot
     uint32_t h = (ph.hash ^ ph.s) * kFnvPrime;
     h = (h ^ (uint32_t)term) * kFnvPrime;
     if (A.hash) A.hash[ph.idx] = h;
+    if (A.point)
+        A.point[ph.idx] = make_float4(ph.p.x, ph.p.y, ph.p.z,
+                                      __uint_as_float((uint32_t)ph.ix | ((uint32_t)ph.iy << 11) | ((uint32_t)ph.iz << 22)));
     if (A.ev_cap) A.nevbuf[ph.idx - A.out_base] = ph.s;  // forward storing events: the count pass 2 stops at
 }
 
@@ -505,8 +581,8 @@ __device__ __forceinline__ void fold_slice(const TransportArgs& A, uint32_t batc
                     if (v != 0.f) atomicAdd(A.L64 + (size_t)c * A.g.nvox + k, (double)v);
                 }
             } else {  // gradient tile [nvox] -> g64 [nvox]
-                const float v = atomicExch(A.gacc + i, 0.f);
-                if (v != 0.f) atomicAdd(A.g64 + i, (double)v);
+                const float v = atomicExch(A.gacc + i, 0.f);  // padded tile: the halo stays 0
+                if (v != 0.f) atomicAdd(A.g64 + unpad_lin(A.g, (int)i), (double)v);
             }
         }
     }
@@ -621,7 +697,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
     t.zero();
 
     Photon ph;
-    Walk w;
+    Flight w;
     float tau = 0.f;
     uint32_t nev = 0u;  // pass 2: events of pass 1
     double acc = 0.0;   // pass 1: W; pass 2: S
@@ -644,7 +720,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
             const int take = min(__popc(empty), rd_n);
             if (!fly && rank < take) {
                 get(stk, kSlots - rd_n + rank, A, ph, nev, acc);
-                walk_init<true>(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+                flight_init(w, A.g, ph);
                 tau = ph.tau;
                 fly = true;
             }
@@ -668,7 +744,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
             }
             launch_photon(A, ph, pid);
             if (MODE == kPass2W) ph.hash = A.evoff[pid];
-            walk_init<true>(w, A.g, ph.p, ph.d, ph.ix, ph.iy, ph.iz);
+            flight_init(w, A.g, ph);
             tau = ph.tau;
             t.add_launch(A.I0);
             return true;
@@ -676,16 +752,27 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
         const bool any_fly = __any_sync(kFull, fly);
         if (!any_fly && ev_n == 0 && rd_n == 0 && dry) break;
 
-        // (2) one voxel for every flying photon
+        // (2) up to kStepsPerTrip voxels for every flying photon
         int r = -1;
-        int nstep = 0;
         if (fly) {
             const float S = PASS2 ? (float)acc : 0.f;
+            int nstep = 0;
+            bool stop = false;
+            float b = 0.f, m = 0.f;
 #pragma unroll 1
-            for (; nstep < kStepsPerTrip && r == -1; ++nstep) r = flight_step<DT, TWO>(A, ph, w, tau, S, scatters);
-        }
-        if (fly) {  // a flight longer than any straight walk through the grid is abandoned
+            while (nstep < kStepsPerTrip) {
+                ++nstep;
+                if (flight_step<DT, PASS2>(A, w, tau, b, m, S, scatters)) {
+                    stop = true;
+                    break;
+                }
+            }
+            if (stop) {
+                r = flight_end<TWO>(A, ph, w, tau, b, S, scatters);
+                if (r >= 0) --nstep;  // the halo voxel is no segment of the path
+            }
             segments += nstep;
+            // a flight longer than any straight walk through the grid is abandoned
             w.left -= nstep;
             if (r == -1 && w.left < 0) r = kWalkOverflow;
         }
@@ -778,7 +865,8 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
                     } else {
                         const float S = (float)eacc;  // the score weight of the flight that ended here
                         if (TWO && S != 0.f) {  // two species: the collision voxel's term (see flight_step)
-                            atomicAdd(A.gacc + k, S * ((air ? 0.f : 1.f / __ldg(A.beta_aer + k)) - e.tau));
+                            atomicAdd(A.gacc + pad_index(A.g, e.ix, e.iy, e.iz),
+                                      S * ((air ? 0.f : 1.f / __ldg(A.beta_aer + k)) - e.tau));
                             ++scatters;
                         }
                         eacc -= (double)we;
@@ -1047,12 +1135,13 @@ __global__ void k_fold_L(float* __restrict__ Lacc, double* __restrict__ L64, int
     }
 }
 
-__global__ void k_fold_grad(float* __restrict__ gacc, double* __restrict__ g64, int nvox) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nvox; k += gridDim.x * blockDim.x) {
-        const float v = gacc[k];
+// the gradient tile is padded like the grid the flights walk; its halo is never written
+__global__ void k_fold_grad(float* __restrict__ gacc, double* __restrict__ g64, const Geo g) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.npad; q += gridDim.x * blockDim.x) {
+        const float v = gacc[q];
         if (v != 0.f) {
-            g64[k] += (double)v;
-            gacc[k] = 0.f;
+            g64[unpad_lin(g, q)] += (double)v;
+            gacc[q] = 0.f;
         }
     }
 }
@@ -1204,8 +1293,8 @@ cudaError_t launch_fold_L(const mst_grid* g, cudaStream_t st) {
 }
 
 cudaError_t launch_fold_grad(const mst_grid* g, cudaStream_t st) {
-    const int nb = (g->geo.nvox + 255) / 256;
-    k_fold_grad<<<nb < 4096 ? nb : 4096, 256, 0, st>>>(g->gacc, g->g64, g->geo.nvox);
+    const int nb = (g->geo.npad + 255) / 256;
+    k_fold_grad<<<nb < 4096 ? nb : 4096, 256, 0, st>>>(g->gacc, g->g64, g->geo);
     return cudaGetLastError();
 }
 
