@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default wavefront shape")
+    ap.add_argument("--no-replay-form", action="store_true",
+                    help="skip the timing of the replay form (W by replay pass 1, no stored events)")
+    ap.add_argument("--cpu-photons", type=float, default=1e6, help="photons of the CPU-baseline sample")
     ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
     ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
     ap.add_argument("--study", default=None, choices=["precision", "recon", "haze", "bmc", "classic", "species"],
@@ -142,17 +145,42 @@ def oracle_step(sc, p, meas, nthreads=0):
 
 
 def cpu_baseline(sc, p, meas, n_sample):
+    """The oracle on the host cores: n_sample photons on all cores, a tenth of them to fit the
+    per-call cost of the deterministic stages (LOS, images, back-projection, LOS adjoint) for the
+    linear extrapolation to the benchmark's 1e8 photons, and a fifth of them on one core."""
     import oracle
     oracle.build()
-    q = p.replace(n_photons=int(n_sample), n_photons_total=int(n_sample))
+    n = int(n_sample)
+    q = p.replace(n_photons=n, n_photons_total=n)
     dt, segs = oracle_step(sc, q, meas)
-    dt1, segs1 = oracle_step(sc, q, meas, nthreads=1)
+    n_small = max(1, n // 10)
+    dts, _ = oracle_step(sc, q.replace(n_photons=n_small, n_photons_total=n_small), meas)
+    n1 = max(1, n // 5)
+    dt1, segs1 = oracle_step(sc, q.replace(n_photons=n1, n_photons_total=n1), meas, nthreads=1)
+    per_photon = max(dt - dts, 0.0) / (n - n_small)
+    fixed = max(dt - per_photon * n, 0.0)
+    t_full = fixed + per_photon * 1e8
     cores = os.cpu_count()
     return {"value": segs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"cumulus64 scene, {int(n_sample)} photons forward + full gradient incl. all deterministic "
+            "sample": f"cumulus64 scene, {n} photons forward + full gradient incl. all deterministic "
                       f"stages in full (LOS, images, back-projection, LOS adjoint), FP64, OpenMP over {cores} "
-                      f"threads; {dt:.2f} s (1 thread: {dt1:.2f} s)",
-            "step_s": dt, "value_1_core": segs1 / dt1}
+                      f"threads; {dt:.2f} s ({n_small} photons: {dts:.2f} s; {n1} photons on 1 thread: {dt1:.2f} s)",
+            "step_s": dt, "value_1_core": segs1 / dt1,
+            "extrapolated_1e8_photons_s": t_full,
+            "extrapolation": f"linear in the photon count from the {n_small}- and {n}-photon runs: "
+                             f"{fixed:.2f} s per call + {per_photon * 1e6:.3f} s per 1e6 photons (extrapolated, "
+                             f"not measured)"}
+
+
+def device_bytes_of(fn):
+    """Runs fn() and returns (its result, device bytes it left allocated outside torch's cache)."""
+    import torch
+    torch.cuda.synchronize()
+    f0, r0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    out = fn()
+    torch.cuda.synchronize()
+    f1, r1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    return out, int((f0 - f1) - (r1 - r0))
 
 
 def run_reference(args):
@@ -215,6 +243,8 @@ def run_ours(args):
     sc, p = synth.cfg_cumulus64(int(args.photons))
     n = int(args.photons)
     p = p.replace(photon_offset=rank * n, n_photons_total=n)
+    torch.cuda.synchronize()
+    mem0 = (torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved())
     grid = m.Grid.from_scene(sc)
     beta_np = sc.beta.astype(np.float32)
     beta = torch.from_numpy(beta_np).cuda()
@@ -230,6 +260,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         grid.render_grad(beta, params, meas, images=False)
     torch.cuda.synchronize()
+    # device memory the handle holds in the timed steps (outside torch's caching allocator)
+    handle_bytes = int((mem0[0] - torch.cuda.mem_get_info()[0]) - (torch.cuda.memory_reserved() - mem0[1]))
 
     uuid = None
     try:
@@ -325,6 +357,40 @@ def run_ours(args):
                 "phase_ms_per_step": {k: v[0] / args.steps for k, v in phase_acc.items()}}
     launches = int(sum(v[1] for v in phase_acc.values()))
 
+    # The form whose device memory stays O(grid + images): W per photon by replay pass 1 (a second
+    # walk of every path) instead of from the events the forward stores, on a handle of its own
+    # with no event budget; same photons, same step.
+    replay_form = None
+    if not args.no_replay_form and args.grad == "full" and world == 1:
+        def make_replay():
+            g2 = m.Grid.from_scene(sc)
+            g2.set_replay_memory(0)
+            if wavefront:
+                g2.set_wavefront(wavefront["forward_trip"], wavefront["forward_blocks_per_sm"],
+                                 wavefront["replay_trip"], wavefront["replay_blocks_per_sm"])
+            for _ in range(2):
+                g2.render_grad(beta, params, meas, images=False)
+            return g2
+        g2, g2_bytes = device_bytes_of(make_replay)
+        g2.set_profiling(True)
+        r_ms, r_ph = [], {}
+        for i in range(3):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g2.render_grad(beta, params, meas, images=False)
+            b.record()
+            torch.cuda.synchronize()
+            r_ms.append(a.elapsed_time(b))
+            for k, (ms, _) in g2.phase_times().items():
+                r_ph[k] = r_ph.get(k, 0.0) + ms / 3
+        st2 = g2.stats()
+        g2.close()
+        replay_form = {"adjoint": "replay", "ms_per_step": sum(r_ms) / len(r_ms), "step_ms_all": r_ms,
+                       "value": st2["segments"] / (sum(r_ms) / len(r_ms) * 1e-3), "unit": UNIT,
+                       "device_bytes": g2_bytes, "events_stored": st2["events_stored"],
+                       "phase_ms_per_step": r_ph}
+
     # end to end through the public API, host buffers in pinned memory
     e2e = None
     if not args.no_e2e:
@@ -352,20 +418,23 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(sc.with_beta(beta_np.astype(np.float64)), p, meas.cpu().numpy(), args.ref_photons * 5)
+        cpu = cpu_baseline(sc.with_beta(beta_np.astype(np.float64)), p, meas.cpu().numpy(), args.cpu_photons)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_job, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "photons_per_gpu": n, "grad_mode": args.grad, "wavefront": wavefront,
+                           "adjoint": "stored_events" if st.get("events_stored", 0.0) > 0 else "replay",
+                           "device_bytes": handle_bytes,
                            "grid_dtype": args.grid_dtype, "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"photon-id shards x{world}" if world > 1 else "1 GPU"},
                 "segments_per_step": {"forward": segs, "replay": st["replay_segments"],
                                       "los": st["los_segments"], "pixel": st["pixel_segments"],
                                       "backproject": st["backproj_segments"], "los_adjoint": st["losadj_segments"]},
                 "events_per_step": st["events"], "step_ms_all": step_ms, "wall_s": wall,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "replay_form": replay_form}
         print(json.dumps(line), flush=True)
     grid.close()
     if dist is not None:
