@@ -532,11 +532,11 @@ int mst_create_grid(const mst_grid_desc* d, int n_cams, const mst_camera* cams, 
     geo.ex = (float)(d->nx * d->dx); geo.ey = (float)(d->ny * d->dy); geo.ez = (float)(d->nz * d->dz);
     geo.nvox = d->nx * d->ny * d->nz;
     geo.max_steps = d->nx + d->ny + d->nz + 8;
-    geo.p0 = d->nx + 2;
-    geo.p01 = (d->nx + 2) * (d->ny + 2);
+    geo.p0 = d->nx + 2 * kHalo;
+    geo.p01 = (d->nx + 2 * kHalo) * (d->ny + 2 * kHalo);
     geo.inv_p0 = (float)(1.0 / geo.p0);
     geo.inv_p01 = (float)(1.0 / geo.p01);
-    geo.npad = geo.p01 * (d->nz + 2);
+    geo.npad = geo.p01 * (d->nz + 2 * kHalo);
     for (int a = 0; a < 3; ++a) g->origin[a] = d->origin[a];
     g->voxel_volume = d->dx * d->dy * d->dz;
     g->n_cams = n_cams;

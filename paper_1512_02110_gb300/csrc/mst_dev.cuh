@@ -21,13 +21,16 @@ struct Geo {
     float ex, ey, ez;   // grid extent (m)
     int nvox;
     int max_steps;      // nx + ny + nz + 8: no straight walk crosses more voxels
-    // The photon flights walk a copy of the grid padded with one halo voxel on every side
-    // ([nz + 2][ny + 2][nx + 2], halo extinction +inf), so that leaving the grid needs no bounds
-    // test in the voxel step: the walk stops on the halo's extinction instead.
-    int p0, p01;        // nx + 2, (nx + 2)(ny + 2): strides of the padded grid
+    // The photon flights walk a copy of the grid padded with kHalo voxels on every side
+    // ([nz + 4][ny + 4][nx + 4], halo extinction +inf), so that leaving the grid needs no bounds
+    // test in the voxel step: the walk stops on the first halo layer's extinction, and the
+    // extinction of the voxel after it, loaded one step ahead, still lies inside the array.
+    int p0, p01;        // nx + 4, (nx + 4)(ny + 4): strides of the padded grid
     float inv_p0, inv_p01;
-    int npad;           // (nx + 2)(ny + 2)(nz + 2)
+    int npad;           // (nx + 4)(ny + 4)(nz + 4)
 };
+
+constexpr int kHalo = 2;  // halo layers of the padded grid
 
 struct Cam {
     float px, py, pz;              // centre of projection, grid-local metres
@@ -161,12 +164,12 @@ __device__ __forceinline__ float3 rotate_dir(float3 d, float ct, float st, float
 
 __device__ __forceinline__ int lin_index(const Geo& g, int ix, int iy, int iz) { return ix + g.nx * (iy + g.ny * iz); }
 
-// index of voxel (ix, iy, iz) in the padded grid (each index may be -1 or n: the halo)
+// index of voxel (ix, iy, iz) in the padded grid (each index may lie in the halo, -kHalo .. n + kHalo - 1)
 __device__ __forceinline__ int pad_index(const Geo& g, int ix, int iy, int iz) {
-    return (ix + 1) + g.p0 * (iy + 1) + g.p01 * (iz + 1);
+    return (ix + kHalo) + g.p0 * (iy + kHalo) + g.p01 * (iz + kHalo);
 }
 
-// (ix, iy, iz) of padded index q, each in [-1, n]. The quotients come from FP32 reciprocals and
+// (ix, iy, iz) of padded index q, each in [-kHalo, n + kHalo). The quotients come from FP32 reciprocals and
 // are corrected by one step: q < 2^31 and the quotients are below 2^12, so the FP32 estimate is
 // off by at most one.
 __device__ __forceinline__ void unpad(const Geo& g, int q, int& ix, int& iy, int& iz) {
@@ -176,9 +179,9 @@ __device__ __forceinline__ void unpad(const Geo& g, int q, int& ix, int& iy, int
     int b = (int)((float)r * g.inv_p0);
     int c = r - b * g.p0;
     if (c < 0) { --b; c += g.p0; } else if (c >= g.p0) { ++b; c -= g.p0; }
-    ix = c - 1;
-    iy = b - 1;
-    iz = a - 1;
+    ix = c - kHalo;
+    iy = b - kHalo;
+    iz = a - kHalo;
 }
 
 // linear voxel index of an interior padded index

@@ -28,7 +28,7 @@ __global__ void k_stage(const float* __restrict__ beta, const float* __restrict_
     }
 }
 
-// The grid of the photon flights: the same values on [nz + 2][ny + 2][nx + 2] with a halo of
+// The grid of the photon flights: the same values on [nz + 4][ny + 4][nx + 4] with a halo of
 // +inf extinction, where a flight stops (a free path never outlasts infinite optical depth).
 template <int DT>
 __global__ void k_stage_pad(const float* __restrict__ beta, const float* __restrict__ air, void* __restrict__ ext,
@@ -36,7 +36,7 @@ __global__ void k_stage_pad(const float* __restrict__ beta, const float* __restr
     typedef typename BetaFetch<DT>::T T;
     T* out = static_cast<T*>(ext);
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.npad; q += gridDim.x * blockDim.x) {
-        const int ix = q % g.p0 - 1, iy = (q / g.p0) % (g.ny + 2) - 1, iz = q / g.p01 - 1;
+        const int ix = q % g.p0 - kHalo, iy = (q / g.p0) % (g.ny + 2 * kHalo) - kHalo, iz = q / g.p01 - kHalo;
         float b = CUDART_INF_F;
         if (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny && iz >= 0 && iz < g.nz) {
             const int k = lin_index(g, ix, iy, iz);

@@ -140,11 +140,14 @@ __device__ __forceinline__ void launch_photon(const TransportArgs& A, Photon& ph
 // quantity stays of the size of one voxel and FP32 keeps ~1e-6 m resolution anywhere in the grid.
 // Ties go to x, then y, then z. Leaving the grid needs no test in the step: the first halo voxel
 // has extinction +inf, so its optical depth exceeds any free path and the flight stops there.
+// The extinction of the next voxel is loaded one step ahead (bn), so that its latency overlaps
+// the current step; the voxel after the first halo layer is the second, still in the array.
 struct Flight {
     float tx, ty, tz;
     float qx, qy, qz;
     int dx, dy, dz;
     int lin;
+    float bn;  // extinction of voxel lin, loaded ahead
     int left;  // voxel steps left before a flight is abandoned (only a non-finite direction gets there)
 };
 
@@ -168,11 +171,14 @@ __device__ __forceinline__ void flight_axis(float p, float d, float h, int strid
 }
 
 // the flight of photon ph from its point (voxel + offset) along its direction
-__device__ __forceinline__ void flight_init(Flight& f, const Geo& g, const Photon& ph) {
+template <int DT>
+__device__ __forceinline__ void flight_init(Flight& f, const TransportArgs& A, const Photon& ph) {
+    const Geo& g = A.g;
     flight_axis(fminf(fmaxf(ph.p.x, 0.f), g.hx), ph.d.x, g.hx, 1, f.tx, f.qx, f.dx);
     flight_axis(fminf(fmaxf(ph.p.y, 0.f), g.hy), ph.d.y, g.hy, g.p0, f.ty, f.qy, f.dy);
     flight_axis(fminf(fmaxf(ph.p.z, 0.f), g.hz), ph.d.z, g.hz, g.p01, f.tz, f.qz, f.dz);
     f.lin = pad_index(g, ph.ix, ph.iy, ph.iz);
+    f.bn = BetaFetch<DT>::get(A.beta_pad, f.lin);
     f.left = g.max_steps;
 }
 
@@ -184,8 +190,12 @@ __device__ __forceinline__ void flight_init(Flight& f, const Geo& g, const Photo
 template <int DT, bool SCORE>
 __device__ __forceinline__ bool flight_step(const TransportArgs& A, Flight& f, float& tau, float& b, float& m, float S,
                                             unsigned& nsc) {
-    b = BetaFetch<DT>::get(A.beta_pad, f.lin);
+    b = f.bn;
     m = fminf(f.tx, fminf(f.ty, f.tz));
+    const bool px = f.tx <= m;
+    const bool py = !px && f.ty <= m;
+    const int next = f.lin + (px ? f.dx : (py ? f.dy : f.dz));
+    f.bn = BetaFetch<DT>::get(A.beta_pad, next);
     const float bs = b * m;
     if (!(tau > bs)) return true;
     tau -= bs;
@@ -193,12 +203,10 @@ __device__ __forceinline__ bool flight_step(const TransportArgs& A, Flight& f, f
         atomicAdd(A.gacc + f.lin, -S * m);
         ++nsc;
     }
-    const bool px = f.tx <= m;
-    const bool py = !px && f.ty <= m;
     f.tx = px ? f.qx : f.tx - m;
     f.ty = py ? f.qy : f.ty - m;
     f.tz = (px || py) ? f.tz - m : f.qz;
-    f.lin += px ? f.dx : (py ? f.dy : f.dz);
+    f.lin = next;
     return false;
 }
 
@@ -720,7 +728,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
             const int take = min(__popc(empty), rd_n);
             if (!fly && rank < take) {
                 get(stk, kSlots - rd_n + rank, A, ph, nev, acc);
-                flight_init(w, A.g, ph);
+                flight_init<DT>(w, A, ph);
                 tau = ph.tau;
                 fly = true;
             }
@@ -744,7 +752,7 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
             }
             launch_photon(A, ph, pid);
             if (MODE == kPass2W) ph.hash = A.evoff[pid];
-            flight_init(w, A.g, ph);
+            flight_init<DT>(w, A, ph);
             tau = ph.tau;
             t.add_launch(A.I0);
             return true;
