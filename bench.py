@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--cpu-photons", type=float, default=1e6, help="photons of the CPU-baseline sample")
     ap.add_argument("--workload", default="cumulus64", choices=["cumulus64", "batch16"])
     ap.add_argument("--single", action="store_true", help="one untimed forward+gradient call (for ncu captures)")
-    ap.add_argument("--study", default=None, choices=["precision", "recon", "haze", "bmc", "classic", "species"],
+    ap.add_argument("--study", default=None, choices=["precision", "recon", "haze", "bmc", "classic", "species",
+                                                      "identify"],
                     help="FP16/BF16 brick forms against FP32 at equal photon count (prints one JSON line)")
     return ap.parse_args()
 
@@ -117,18 +118,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_record(kernel, photons):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel source
-    has not changed since the capture and the launch traces the captured photon count (else
-    None)."""
+def traffic_record(kernel, photons, events):
+    """DRAM bytes per launch of `kernel`, scaled from the committed ncu capture of a smaller call
+    of the same scene: bytes per stored event for the kernels whose traffic is the event stream
+    (the forward writes the events, the adjoint reads them), bytes per photon otherwise. None if
+    the kernel source has changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             d = json.load(f)
         src = open(os.path.join(ROOT, "paper_1512_02110_gb300", "csrc", "transport.cu"), "rb").read()
-        if d.get("transport_cu_sha1") != hashlib.sha1(src).hexdigest() or int(d.get("photons", -1)) != int(photons):
+        if d.get("transport_cu_sha1") != hashlib.sha1(src).hexdigest():
             return None
         rec = d.get("kernels", {}).get(kernel)
-        return None if rec is None else float(rec["dram_bytes_per_launch_full"])
+        if rec is None:
+            return None
+        if rec.get("scale") == "events":
+            return float(rec["dram_bytes"]) * events / float(d["events"])
+        return float(rec["dram_bytes"]) * photons / float(d["photons"])
     except Exception:
         return None
 
@@ -313,8 +319,9 @@ def run_ours(args):
     # 15 per transport segment, 27 per event and camera (local estimate: direction, cosine,
     # Henyey-Greenstein phase, two MUFU), 35 per event (scattering sample, roulette), 2 per replay
     # score scatter; the stored-event adjoint 27 per event and camera, 36 B record + 4 B per camera
-    # + 8 B of W per event. The HBM form (4 B per segment, 8 B per camera per event, plus the stored
-    # events and event counts the forward writes) is kept beside it.
+    # + 8 B of W per event. The byte form against the measured HBM copy rate (4 B per segment, 8 B
+    # per camera per event) is kept beside it, with the stored events' bytes the forward also
+    # writes (40 B per event, 4 B per photon) reported apart.
     C = sc.n_cams
     seg1, ev1 = st["segments"], st["events"]
     stored = st.get("events_stored", 0.0)
@@ -324,8 +331,7 @@ def run_ours(args):
         seg2, ev2 = st["replay_segments"] - seg1, st["replay_events"] - ev1
     ops_ev = 27 * C + 35
     kernels = {
-        "k_transport": (phase_acc["transport"], 15 * seg1 + ops_ev * ev1,
-                        4 * seg1 + 8 * C * ev1 + (36 * stored + 4 * st["traced"] if stored > 0 else 0)),
+        "k_transport": (phase_acc["transport"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 8 * C * ev1),
         "k_replay_pass1": (phase_acc["replay"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 4 * C * ev1),
         # with stored events pass 2 reads each w_s (4 B) instead of summing over the cameras
         "k_replay_pass2": (phase_acc["replay2"], 15 * seg2 + (35 if stored > 0 else ops_ev) * ev2
@@ -345,7 +351,7 @@ def run_ours(args):
     achieved_ops = aops / calls_per_step / per_launch_s
     hbm_peak, peak_kind = peaks()
     hbm_achieved = abytes / calls_per_step / per_launch_s / 1e9
-    traffic = traffic_record(kern, n)
+    traffic = traffic_record(kern, n, st["events"])
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                 "unit": "TOP/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz",
@@ -353,7 +359,11 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": abytes / calls_per_step, "ms_per_launch": kms / kn,
                 "launches_per_step": calls_per_step,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
-                        "peak_source": peak_kind},
+                        "peak_source": peak_kind,
+                        "bytes": "algorithmic: 4 B of extinction per voxel segment, 8 B per camera per event "
+                                 "(FP32 read-modify-write of the L tile)",
+                        "stored_event_bytes_per_launch": (40 * stored + 4 * st["traced"]) / calls_per_step
+                        if kern == "k_transport" and stored > 0 else 0.0},
                 "phase_ms_per_step": {k: v[0] / args.steps for k, v in phase_acc.items()}}
     launches = int(sum(v[1] for v in phase_acc.values()))
 
@@ -459,8 +469,9 @@ def run_single(args):
     out = grid.render_grad(beta, m.make_params(p, grad_mode=args.grad, grid_dtype=args.grid_dtype), meas,
                            images=False)
     torch.cuda.synchronize()
+    st = grid.stats()
     print(json.dumps({"single": True, "photons": int(args.photons), "loss": out["loss"].item(),
-                      "segments": grid.stats()["segments"]}))
+                      "segments": st["segments"], "events": st["events"], "events_stored": st["events_stored"]}))
     return 0
 
 
@@ -483,7 +494,8 @@ def _timed(fn, steps, warmup, flush):
 
 def run_batch(args):
     """Batched workload: 16 scenes of uneven size (24^3-96^3, 3-12 cameras, 1e7-1e8 photons log-uniform),
-    forward + full gradient, as one graph launch vs. 16 sequential calls."""
+    forward + full gradient, as one graph launch (one branch per scene, the default form) against
+    the persistent form (each transport pass one launch over all scenes) and 16 sequential calls."""
     import torch
 
     import paper_1512_02110_gb300 as m
@@ -500,8 +512,21 @@ def run_batch(args):
         params.append(m.make_params(p, grad_mode="full"))
     batch = m.Batch(grids)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # the default form: one graph branch per scene, each scene's wavefront from its own autotuner
+    # run on an eighth of its photons
+    if not args.no_autotune:
+        for g, b, q in zip(grids, betas, params):
+            g.autotune(b, q, n_sample=max(1 << 16, min(int(q.n_photons) // 8, 1 << 27)))
     ms_batch, all_b = _timed(lambda: batch.render_grad(betas, params, meas), args.steps, args.warmup, flush)
+    form = batch.form()
     stored_in_graph = sum(1 for g in grids if g.stats()["events_stored"] > 0)
+    # the persistent form (each transport pass one launch over all scenes), its wavefront picked
+    # by the batch autotuner on an eighth of the photons
+    batch.set_form("persistent")
+    wavefront = None if args.no_autotune else batch.autotune(betas, params, meas, sample_div=8)
+    ms_persistent, _ = _timed(lambda: batch.render_grad(betas, params, meas), args.steps, args.warmup, flush)
+    form_p = batch.form()
+    batch.set_form("branches")
 
     def sequential():
         for g, b, q, mm in zip(grids, betas, params, meas):
@@ -516,6 +541,9 @@ def run_batch(args):
     print(json.dumps({"metric": "photon path segments/s (batched forward + full gradient, 16 uneven scenes)",
                       "value": segs / (ms_batch * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
+                      "form": form,
+                      "persistent_ms_per_step": ms_persistent, "persistent_value": segs / (ms_persistent * 1e-3),
+                      "persistent_form": form_p, "persistent_wavefront": wavefront,
                       "sequential_ms_per_step": ms_seq, "sequential_value": segs / (ms_seq * 1e-3),
                       "photons_per_step": photons, "segments_per_step": segs, "scenes_storing_events_in_graph":
                       stored_in_graph, "dtype": "f32", "data": "synthetic",
@@ -749,6 +777,74 @@ def run_recon_study(args):
     return 0
 
 
+def run_identify_study(args):
+    """Identifiability of the cumulus64 field from its 9 in-situ cameras (Sec. 5, Sec. 6):
+    measured images are the true field rendered with 10x the photons of one reconstruction render
+    (seed 4); projected L-BFGS on the full gradient with 1e8 photons per render (common random
+    numbers) from 0.5x the true field, without and with the Laplacian prior (eta Psi of the true
+    field set to the loss of the true field, the noise floor, as in the haze study), and from the
+    uniform 1 1/km start with the prior, and from 0.5x the true field under a diagonal
+    preconditioner (beta = w x, w the start field). Also the loss along the ray
+    beta = s beta_true, s in 0.25 .. 2, and the full gradient's derivative along beta_true at
+    s = 0.5 against a central difference of the loss. Prints one JSON line with epsilon and
+    delta_mass along each run."""
+    import torch
+
+    import paper_1512_02110_gb300 as m
+    import synth
+    torch.cuda.set_device(0)
+    n = int(args.photons)
+    sc, p = synth.cfg_cumulus64(n)
+    grid = m.Grid.from_scene(sc)
+    b_true = sc.beta.astype(np.float64)
+    t1 = np.abs(b_true).sum()
+    bt = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
+    meas = grid.render(bt, m.make_params(p, seed=4, n_photons=10 * n))["images"]
+    prm = m.make_params(p, grad_mode="full")
+    loss_true = grid.render_grad(bt, prm, meas, images=False)["loss"].item()
+    psi_true = grid.regularizer(bt, 1.0).item()
+    eta = loss_true / psi_true
+
+    def errs(b):
+        return {"epsilon": float(np.abs(b - b_true).sum() / t1), "delta_mass": float((np.abs(b).sum() - t1) / t1)}
+
+    out = {"study": "identify", "photons_per_render": n, "measured_photons": 10 * n,
+           "true_field": {"loss": loss_true, "psi": psi_true}, "eta": eta}
+    out["loss_along_scale"] = [
+        {"s": sc_, "loss": grid.render_grad(torch.from_numpy((sc_ * b_true).astype(np.float32)).cuda(), prm, meas,
+                                            images=False)["loss"].item()} for sc_ in (0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0)]
+    # the gradient's direction at 0.5 beta_true: its derivative along beta_true against a central
+    # difference of the loss along that ray (same photons)
+    half = torch.from_numpy((0.5 * b_true).astype(np.float32)).cuda()
+    g_half = grid.render_grad(half, prm, meas, images=False)["grad"].cpu().numpy()
+    e_lo = grid.render_grad(torch.from_numpy((0.45 * b_true).astype(np.float32)).cuda(), prm, meas,
+                            images=False)["loss"].item()
+    e_hi = grid.render_grad(torch.from_numpy((0.55 * b_true).astype(np.float32)).cuda(), prm, meas,
+                            images=False)["loss"].item()
+    out["direction_at_half"] = {"grad_dot_beta_true": float(np.dot(g_half, b_true)),
+                                "central_difference": (e_hi - e_lo) / 0.1}
+    # runs: (name, start, prior weight, parametrisation); "scaled": beta = w x with w the start field,
+    # a diagonal preconditioner under which every voxel moves in proportion to its extinction
+    b_half = 0.5 * b_true
+    runs = (("half_true_no_prior", b_half, 0.0, None), ("half_true_prior", b_half, eta, None),
+            ("half_true_scaled", np.maximum(b_half, 1e-9), 0.0, "scaled"),
+            ("uniform_prior", np.full(sc.nvox, 1.0 * synth.KM), eta, None))
+    for name, b0, e, par in runs:
+        trace = []
+        t0 = time.perf_counter()
+        P = m.Scaled(b0) if par == "scaled" else None
+        st = m.reconstruct(grid, meas, b0, m.make_params(p, grad_mode="full", reg_eta=e), iters=args.recon_iters,
+                           method="lbfgs", block=P,
+                           callback=lambda s: trace.append({"it": s.it, "loss": s.losses[-1], **errs(s.beta)}))
+        torch.cuda.synchronize()
+        fin = errs(st.beta)
+        out[name] = {"initial": errs(b0), "eta": e, "iterations": st.it, "renders": st.n_renders,
+                     "s": time.perf_counter() - t0, "loss0": st.losses[0], "final": fin,
+                     "epsilon_below_start": fin["epsilon"] < errs(b0)["epsilon"], "trace": trace[::5] + trace[-1:]}
+    print(json.dumps(out))
+    return 0
+
+
 def run_haze_study(args):
     """Reconstruction in the paper's own setting (Sec. 7; synth.cfg_haze80): aerosol haze over
     air on 80 x 80 x 120 voxels, 36 ground cameras, the unknowns the values of the paper's 20 x
@@ -900,6 +996,8 @@ def main():
         return run_classic_study(args)
     if args.study == "species":
         return run_species_study(args)
+    if args.study == "identify":
+        return run_identify_study(args)
     if args.workload == "batch16":
         return run_batch(args)
     return run_ours(args)

@@ -288,9 +288,9 @@ int mst_render_grad_channels(mst_grid *g, const float *beta_aer_dev, int n_chann
 
 /* Wavefront shape of the persistent transport kernels on this handle: the voxels a flying lane
  * advances per loop trip, and the resident blocks per SM, for the forward render (voxel
- * estimator) and for replay pass 2. 0 keeps the built-in default (8 and 5 voxels; the
+ * estimator) and for replay pass 2. 0 keeps the built-in default (12 and 6 voxels; the
  * register budget's occupancy, 3 blocks). The trip is a compile-time constant of the kernels:
- * forward trips 6, 8, 10, 12 and pass-2 trips 4, 5, 6, 8 are built, for the FP32 grid (the
+ * forward trips 8, 10, 12, 16 and pass-2 trips 4, 6, 8, 10 are built, for the FP32 grid (the
  * FP16 / BF16 grids use the defaults). Results do not depend on the shape beyond the order of
  * floating-point additions: each photon's path is fixed by its Philox key. Blocks per SM in
  * 0..8 (more than the occupancy runs at the occupancy); other trips return MST_ERR_INVALID_ARG. */
@@ -299,7 +299,7 @@ int mst_set_wavefront(mst_grid *g, int forward_trip, int forward_blocks_per_sm, 
 
 /* Autotuner of the wavefront shape. Times full-gradient calls of the voxel estimator on this
  * scene (beta_dev; p's optics, sun, seed and grid_dtype; zero measured images) with n_sample
- * photons for each candidate (forward trips 6, 8, 10, 12 and pass-2 trips 4, 5, 6, 8, each at
+ * photons for each candidate (forward trips 8, 10, 12, 16 and pass-2 trips 4, 6, 8, 10, each at
  * the register budget's occupancy and one block per SM less), sets the fastest forward and
  * pass-2 shapes on the handle (as mst_set_wavefront) and writes them to
  * choice_host[4] = {forward trip, forward blocks per SM, pass-2 trip, pass-2 blocks per SM}.
@@ -354,8 +354,8 @@ int mst_sync(mst_grid *g);
 const char *mst_last_error(mst_grid *g);
 
 /* LOS transmittance without a handle and without allocating: for callers that cannot call
- * cudaMalloc (code inside a stream capture, hosts that hand out device memory only from their
- * own arena, plugins that may not allocate after start-up). The paper has no counterpart: it
+ * cudaMalloc (hosts that hand out device memory only from their own arena, plugins that may not
+ * allocate after start-up). The paper has no counterpart: it
  * computes the same T_c(k) as mst_transmittance (FP32 grid) for the grid and cameras given.
  *   beta_dev [nvox] float, T_dev [C][nvox] float: the caller's buffers.
  * Scratch: a fixed device array of MST_NOALLOC_MAX_VOXELS floats (8 MiB) inside the library,
@@ -363,7 +363,8 @@ const char *mst_last_error(mst_grid *g);
  * rejected with MST_ERR_TOO_LARGE before anything is enqueued (e.g. 128^3 fits, 136 x 128 x 128
  * does not).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call outside any stream capture. Every call shares the one array and
+ * make that first call outside any stream capture. The address is kept for the life of the
+ * process: after a cudaDeviceReset of that device it is stale. Every call shares the one array and
  * overwrites it; calls whose work overlaps on the GPU (other streams, other threads) race,
  * so order them on one stream or synchronise between them. Returns MST_OK, MST_ERR_INVALID_ARG,
  * MST_ERR_TOO_LARGE, MST_ERR_NO_DEVICE or MST_ERR_CUDA. */
@@ -392,6 +393,34 @@ int mst_batch_render_grad(mst_batch *b, const float *const *betas, const mst_par
                           const double *const *images_meas, const uint8_t *const *masks, double *const *images,
                           double *const *grads, double *losses_dev, void *stream);
 const char *mst_batch_last_error(mst_batch *b);
+
+/* Form of the batch's graph (Sec. 1: photons of all scenes are independent work items).
+ * MST_BATCH_BRANCHES (the default): one graph branch per scene holding that scene's
+ * mst_render_grad sequence; the branches overlap on the GPU.
+ * MST_BATCH_PERSISTENT: the photon transport of all scenes runs as single
+ * persistent launches (forward, stored-event adjoint, replay passes 1 and 2), every warp taking
+ * the scenes one after the other from a device table, with each scene's small kernels (staging,
+ * LOS, images, back-projection, folds) on a graph branch of its own between them. It applies
+ * when every scene renders the voxel estimator's full gradient on an FP32 grid with one species
+ * and its events fit the handle's budget; otherwise the call falls back to the branches. The
+ * persistent kernels read each scene's arguments from device memory instead of the parameter
+ * bank, which costs them registers: at 16 uneven scenes the branches are the faster form.
+ * mst_batch_get_form returns the form of the last captured graph (-1 for NULL). */
+enum { MST_BATCH_BRANCHES = 0, MST_BATCH_PERSISTENT = 1 };
+int mst_batch_set_form(mst_batch *b, int form);
+int mst_batch_get_form(mst_batch *b);
+
+/* Wavefront of the persistent form's launches, as mst_set_wavefront sets it for one handle:
+ * forward voxels per trip in {0, 8, 10, 12, 16} (0 or 12: default), pass-2 voxels per trip in
+ * {0, 4, 6, 8, 10} (0 or 6: default), blocks per SM (0: the register budget's occupancy). */
+int mst_batch_set_wavefront(mst_batch *b, int forward_trip, int forward_blocks, int replay_trip, int replay_blocks);
+
+/* Times batch calls on a sample of the given call (each scene's photons divided by sample_div,
+ * no regulariser) for each wavefront candidate, forward shapes first, then pass 2's, and keeps
+ * the fastest; choice[4] receives forward trip, forward blocks per SM, pass-2 trip, pass-2 blocks
+ * per SM. The handles' record-buffer sizing is restored afterwards. Synchronises the stream. */
+int mst_batch_autotune(mst_batch *b, const float *const *betas, const mst_params *params,
+                       const double *const *images_meas, int sample_div, int *choice, void *stream);
 void mst_batch_destroy(mst_batch *b); /* NULL-safe; synchronises the device first */
 
 /* Library version (integer, increases with the ABI). */

@@ -41,7 +41,8 @@ EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy"
            "mst_get_phase_times", "mst_transmittance_noalloc", "mst_batch_create", "mst_batch_render_grad",
            "mst_batch_last_error", "mst_batch_destroy", "mst_set_replay_memory", "mst_render_bmc",
            "mst_set_reg_weights", "mst_set_air", "mst_render_grad_channels", "mst_sun_mask",
-           "mst_set_wavefront", "mst_autotune"]
+           "mst_set_wavefront", "mst_autotune", "mst_batch_set_form", "mst_batch_get_form", "mst_batch_set_wavefront",
+           "mst_batch_autotune"]
 PHASES = ["stage", "transport", "fold", "los", "images", "backproject", "los_adjoint", "replay", "combine", "replay2",
           "replay_list", "event_adjoint", "bmc"]
 
@@ -112,6 +113,10 @@ def _load():
     L.mst_batch_last_error.argtypes = [P]
     L.mst_batch_last_error.restype = ctypes.c_char_p
     L.mst_batch_destroy.argtypes = [P]
+    L.mst_batch_set_form.argtypes = [P, I]
+    L.mst_batch_get_form.argtypes = [P]
+    L.mst_batch_set_wavefront.argtypes = [P, I, I, I, I]
+    L.mst_batch_autotune.argtypes = [P, P, P, P, I, P, P]
     L.mst_sync.argtypes = [P]
     L.mst_last_error.argtypes = [P]
     L.mst_last_error.restype = ctypes.c_char_p
@@ -437,6 +442,35 @@ class Batch:
             raise MSTError(f"mst_batch_render_grad: {ERRORS.get(rc, rc)}: {msg.decode() if msg else ''}")
         return dict(loss=losses, grad=grads, images=imgs)
 
+    def _check(self, rc, what):
+        if rc != MST_OK:
+            msg = lib.mst_batch_last_error(self._h)
+            raise MSTError(f"{what}: {ERRORS.get(rc, rc)}: {msg.decode() if msg else ''}")
+
+    def set_form(self, form: str):
+        """"persistent" (default): the transport of all scenes in single persistent launches;
+        "branches": one graph branch per scene (mst_batch_set_form)."""
+        self._check(lib.mst_batch_set_form(self._h, {"branches": 0, "persistent": 1}[form]), "mst_batch_set_form")
+
+    def form(self) -> str:
+        """Form of the last captured graph."""
+        return {0: "branches", 1: "persistent"}.get(lib.mst_batch_get_form(self._h), "none")
+
+    def set_wavefront(self, forward_trip=0, forward_blocks=0, replay_trip=0, replay_blocks=0):
+        self._check(lib.mst_batch_set_wavefront(self._h, int(forward_trip), int(forward_blocks), int(replay_trip),
+                                                int(replay_blocks)), "mst_batch_set_wavefront")
+
+    def autotune(self, betas, params, meas, sample_div: int = 8, stream=None) -> dict:
+        """Times the persistent form's wavefront candidates on a sample of this call (mst_batch_autotune)."""
+        n = len(self.grids)
+        P = ctypes.c_void_p
+        arr = lambda ts: (P * n)(*[t.data_ptr() for t in ts])
+        pa = (Params * n)(*params)
+        c = (ctypes.c_int * 4)()
+        self._check(lib.mst_batch_autotune(self._h, arr(betas), pa, arr(meas), int(sample_div), c, _stream(stream)),
+                    "mst_batch_autotune")
+        return dict(forward_trip=c[0], forward_blocks_per_sm=c[1], replay_trip=c[2], replay_blocks_per_sm=c[3])
+
     def close(self):
         if getattr(self, "_h", None):
             lib.mst_batch_destroy(self._h)
@@ -476,4 +510,4 @@ def transmittance_noalloc(shape, h, origin, cam_pos, cam_rot, cam_w, cam_h, cam_
     return T
 
 
-from .autograd import Blocks, RenderLoss, reconstruct  # noqa: E402  (needs `lib` above)
+from .autograd import Blocks, RenderLoss, Scaled, reconstruct  # noqa: E402  (needs `lib` above)

@@ -85,6 +85,27 @@ class Blocks:
         return self.reduce(beta) / self.count
 
 
+class Scaled:
+    """beta = w x with fixed positive weights w (a diagonal preconditioner): the optimizer works
+    on x, its gradient is w * dE/dbeta. With w the start field, every voxel moves in proportion to
+    its own extinction and voxels outside the start's support stay at 0."""
+
+    def __init__(self, w):
+        self.w = np.asarray(w, dtype=np.float64)
+        if not np.all(self.w > 0):
+            raise ValueError("scaling weights must be > 0")
+        self.n = self.w.size
+
+    def expand(self, x):
+        return self.w * np.asarray(x, dtype=np.float64)
+
+    def reduce(self, g):
+        return self.w * np.asarray(g, dtype=np.float64)
+
+    def restrict(self, beta):
+        return np.asarray(beta, dtype=np.float64) / self.w
+
+
 def _eval(grid, params, meas, mask, x, P=None):
     """Loss and gradient at parameter vector x (beta itself, or block values under P)."""
     beta_np = x if P is None else P.expand(x)
@@ -104,9 +125,13 @@ def reconstruct(grid, meas, beta0, params, iters: int = 50, method: str = "lbfgs
     method="gd": the paper's loop (Eq. GD): a forward render gives L and j = L/beta; then n_gd
     projected steps beta <- max(0, beta - step * dE/dbeta) with j fixed; repeat.
     block=(bx, by, bz): optimise one value per block of voxels (Blocks); the state's x holds the
-    block values and its beta the expanded field.
+    block values and its beta the expanded field. block may also be a parametrisation object
+    with expand / reduce / restrict (Blocks, Scaled).
     """
-    P = Blocks(grid.shape, block) if block is not None else None
+    if block is None or hasattr(block, "expand"):
+        P = block
+    else:
+        P = Blocks(grid.shape, block)
     b0 = np.maximum(np.asarray(beta0, dtype=np.float64), 0.0)
     if state is None:
         x0 = b0 if P is None else P.restrict(b0)

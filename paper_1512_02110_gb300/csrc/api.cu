@@ -1112,12 +1112,12 @@ int mst_render_grad_channels(mst_grid* g, const float* beta, int n, const mst_ch
 
 int mst_set_wavefront(mst_grid* g, int forward_trip, int forward_blocks, int replay_trip, int replay_blocks) {
     if (!g) return MST_ERR_INVALID_ARG;
-    const bool ft = forward_trip == 0 || forward_trip == 6 || forward_trip == 8 || forward_trip == 10 ||
-                    forward_trip == 12;
-    const bool rt = replay_trip == 0 || replay_trip == 4 || replay_trip == 5 || replay_trip == 6 || replay_trip == 8;
+    const bool ft = forward_trip == 0 || forward_trip == 8 || forward_trip == 10 || forward_trip == 12 ||
+                    forward_trip == 16;
+    const bool rt = replay_trip == 0 || replay_trip == 4 || replay_trip == 6 || replay_trip == 8 || replay_trip == 10;
     if (!ft || !rt || forward_blocks < 0 || forward_blocks > 8 || replay_blocks < 0 || replay_blocks > 8)
         return fail(g, MST_ERR_INVALID_ARG,
-                    "forward trip in {0, 6, 8, 10, 12}, pass-2 trip in {0, 4, 5, 6, 8}, blocks per SM in 0..8");
+                    "forward trip in {0, 8, 10, 12, 16}, pass-2 trip in {0, 4, 6, 8, 10}, blocks per SM in 0..8");
     g->wf_trip[0] = forward_trip;  // forward, voxel estimator (the classic one keeps its defaults)
     g->wf_blocks[0] = forward_blocks;
     for (int m : {2, 4}) {  // replay pass 2, recomputing or reading the stored w_s
@@ -1161,9 +1161,9 @@ int mst_autotune(mst_grid* g, const float* beta, const mst_params* p, uint64_t n
     const int occ_r = transport_blocks_per_sm(q.grid_dtype, 4, g->air != nullptr);
     // candidates: voxels per trip around the defaults, at full occupancy and one block less
     std::vector<std::pair<int, int>> cf, cr;
-    for (int t : {6, 8, 10, 12})
+    for (int t : {8, 10, 12, 16})
         for (int b = occ_f; b >= std::max(1, occ_f - 1); --b) cf.push_back({t, b});
-    for (int t : {4, 5, 6, 8})
+    for (int t : {4, 6, 8, 10})
         for (int b = occ_r; b >= std::max(1, occ_r - 1); --b) cr.push_back({t, b});
     std::vector<double> tf(cf.size(), 1e30), tr(cr.size(), 1e30);
     g->prof = true;
@@ -1266,12 +1266,18 @@ struct mst_batch {
     cudaEvent_t done = nullptr;  // after the last graph launch: the handles' event counts have landed
     bool launched = false;
     std::string err;
+    // the persistent form: the photon transport of all scenes in single launches
+    int form = MST_BATCH_BRANCHES;    // requested form
+    bool persistent = false;          // form of the captured graph
+    int trip_fwd = 0, blocks_fwd = 0, trip_p2 = 0, blocks_p2 = 0;  // its wavefront (0: defaults)
+    TransportArgs* tables = nullptr;  // device [4][n]: forward, event adjoint, pass 1, pass 2
 };
 
 namespace {
 
 void batch_free(mst_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->tables) cudaFree(b->tables);
     for (cudaStream_t s : b->branch)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->join)
@@ -1285,6 +1291,176 @@ template <typename T>
 void key_add(std::vector<unsigned char>& k, const T& v) {
     const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
     k.insert(k.end(), p, p + sizeof(T));
+}
+
+// blocks of a persistent batch launch of a transport mode (per_sm 0: the register budget's occupancy)
+int batch_launch_blocks(const mst_batch* b, int mode, int per_sm) {
+    const int occ = transport_batch_blocks_per_sm(mode);
+    return b->grids[0]->sm_count * (per_sm > 0 && per_sm < occ ? per_sm : occ);
+}
+
+// Whether every scene of the call can run in the persistent form: the voxel estimator's full
+// gradient with the forward's events stored (buffers sized before the capture), FP32 grid, one
+// species. Otherwise the batch keeps one graph branch per scene.
+bool persistent_ok(const mst_batch* b, const mst_params* params) {
+    if (b->form != MST_BATCH_PERSISTENT) return false;
+    for (int i = 0; i < b->n; ++i) {
+        const mst_grid* g = b->grids[i];
+        const mst_params& p = params[i];
+        if (p.estimator != MST_EST_VOXEL || p.grad_mode != MST_GRAD_FULL || p.grid_dtype != MST_GRID_F32 ||
+            g->air || !g->batch_stored || p.n_photons > kRecordMaxPhotons)
+            return false;
+    }
+    return true;
+}
+
+// Arguments of the persistent launches, one per scene and launch, as mst_render_grad builds them
+// for one handle (forward storing its events; event adjoint, pass 1 and pass 2 with their tickets).
+int persistent_tables(mst_batch* b, const float* const* betas, const mst_params* params) {
+    const int n = b->n;
+    std::vector<TransportArgs> t(4 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        mst_grid* g = b->grids[i];
+        const mst_params* p = &params[i];
+        g->beta_in = betas[i];
+        TransportArgs f = transport_args(g, p);
+        set_fold(f, (uint64_t)g->geo.nvox * g->cp);
+        f.evrec = g->evrec;
+        f.ev_cap = g->ev_cap;
+        f.ev_count = g->ev_count;
+        f.ch_next = g->ch_next;
+        f.warp_head = g->warp_head;
+        g->ev_warps = (uint32_t)batch_launch_blocks(b, 0, b->blocks_fwd) * kTransportWarps;
+        f.first_id = p->photon_offset;
+        f.out_base = 0;
+        f.n = (uint32_t)p->n_photons;
+        f.ticket = g->tickets;
+        t[i] = f;
+        TransportArgs r = transport_args(g, p);
+        set_fold(r, (uint64_t)g->geo.npad);
+        r.evrec = g->evrec;
+        r.ev_cap = g->ev_cap;
+        r.ev_count = g->ev_count;
+        r.wseq = g->wseq;
+        r.evoff = g->evoff;
+        r.ch_next = g->ch_next;
+        r.warp_head = g->warp_head;
+        r.n_warps = g->ev_warps;
+        r.first_id = p->photon_offset;
+        r.out_base = 0;
+        r.n = (uint32_t)p->n_photons;
+        r.ticket = g->tickets + 2;  // the event adjoint's blocks take the forward warps' lists from it
+        t[n + i] = r;
+        r.ticket = g->tickets;      // pass 1 (returns at once when the events fitted)
+        t[2 * n + i] = r;
+        r.ticket = g->tickets + 1;  // pass 2
+        t[3 * n + i] = r;
+    }
+    if (!b->tables && cudaMalloc(&b->tables, sizeof(TransportArgs) * t.size()) != cudaSuccess) {
+        cudaGetLastError();
+        b->tables = nullptr;
+        b->err = "batch tables: out of device memory";
+        return MST_ERR_OOM;
+    }
+    if (cudaMemcpy(b->tables, t.data(), sizeof(TransportArgs) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        b->err = "batch tables: copy failed";
+        return MST_ERR_CUDA;
+    }
+    return MST_OK;
+}
+
+// The persistent form of one batch call, enqueued while the capture stream records: each scene's
+// small kernels run on its own branch (the steps of mst_render_grad for one handle, in order),
+// and the photon transport, the stored-event adjoint and both replay passes of all scenes run as
+// single persistent launches on the capture stream between them.
+int persistent_sequence(mst_batch* b, const float* const* betas, const mst_params* params, const double* const* meas,
+                        const uint8_t* const* masks, double* const* images, double* const* grads, double* losses) {
+    const int n = b->n;
+    mst_grid* g = nullptr;  // the scene in hand, for the error messages of MST_CK
+    cudaStream_t cap = b->cap;
+    const TransportArgs* t_fwd = b->tables;
+    const TransportArgs* t_adj = b->tables + n;
+    const TransportArgs* t_p1 = b->tables + 2 * n;
+    const TransportArgs* t_p2 = b->tables + 3 * n;
+    auto fork = [&]() {
+        cudaEventRecord(b->fork, cap);
+        for (int i = 0; i < n; ++i) cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    };
+    auto join = [&]() {
+        for (int i = 0; i < n; ++i) {
+            cudaEventRecord(b->join[i], b->branch[i]);
+            cudaStreamWaitEvent(cap, b->join[i], 0);
+        }
+    };
+    const int sm = b->grids[0]->sm_count;
+    auto blocks = [&](int mode, int per_sm) { return batch_launch_blocks(b, mode, per_sm); };
+    // 1. staging and the counters of the forward
+    fork();
+    for (int i = 0; i < n; ++i) {
+        g = b->grids[i];
+        cudaStream_t st = b->branch[i];
+        g->beta_in = betas[i];
+        MST_CK(launch_stage(g, betas[i], nullptr, MST_GRID_F32, st));
+        MST_CK(cudaMemsetAsync(g->stats, 0, MST_NSTATS * 8, st));
+        MST_CK(cudaMemsetAsync(g->L64, 0, sizeof(double) * (size_t)g->n_cams * g->geo.nvox, st));
+        MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int), st));
+        MST_CK(cudaMemsetAsync(g->ev_count, 0, sizeof(unsigned long long), st));
+    }
+    join();
+    g = b->grids[0];
+    MST_CK(launch_transport_batch(t_fwd, n, 0, b->trip_fwd, blocks(0, b->blocks_fwd), cap));
+    // 2. L, images, loss, back-projection, LOS adjoint, adjoint tiles, the event slots
+    fork();
+    for (int i = 0; i < n; ++i) {
+        g = b->grids[i];
+        cudaStream_t st = b->branch[i];
+        const size_t nL = (size_t)g->n_cams * g->geo.nvox;
+        const uint64_t np = params[i].n_photons;
+        double* lossp = losses + i;
+        MST_CK(launch_fold_L(g, st));
+        MST_CK(cudaMemcpyAsync(g->ev_seen, g->ev_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        MST_CK(launch_los(g, MST_GRID_F32, g->L64, nullptr, nullptr, betas[i], g->T, g->R, st));
+        MST_CK(cudaMemsetAsync(lossp, 0, sizeof(double), st));
+        MST_CK(launch_images(g, g->R, images ? images[i] : nullptr, meas[i], masks ? masks[i] : nullptr, g->resid,
+                             lossp, st));
+        MST_CK(cudaMemsetAsync(g->bacc, 0, sizeof(float) * nL, st));
+        MST_CK(launch_backproject(g, g->resid, g->bacc, st));
+        MST_CK(cudaMemsetAsync(g->gT, 0, sizeof(float) * nL, st));
+        MST_CK(launch_los_adjoint(g, g->R, g->bacc, g->gT, st));
+        MST_CK(launch_adjoint_tiles(g, g->T, g->bacc, g->adj, st));
+        MST_CK(cudaMemsetAsync(g->g64, 0, sizeof(double) * g->geo.nvox, st));
+        MST_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * 3, st));
+        MST_CK(cudaMemsetAsync(g->wbuf, 0, sizeof(double) * np, st));
+        MST_CK(launch_event_offsets(g, (uint32_t)np, st));
+        MST_CK(cudaMemsetAsync(g->nevbuf, 0, sizeof(uint32_t) * np, st));
+    }
+    join();
+    g = b->grids[0];
+    MST_CK(launch_event_adjoint_batch(t_adj, n, sm * 8, cap));
+    MST_CK(launch_transport_batch(t_p1, n, 3, 0, blocks(3, 0), cap));  // only scenes whose events overflowed
+    // 3. the pass-2 lists
+    fork();
+    for (int i = 0; i < n; ++i) {
+        g = b->grids[i];
+        MST_CK(launch_score_list(g, (uint32_t)params[i].n_photons, b->branch[i]));
+    }
+    join();
+    g = b->grids[0];
+    MST_CK(launch_transport_batch(t_p2, n, 4, b->trip_p2, blocks(4, b->blocks_p2), cap));
+    MST_CK(launch_transport_batch(t_p2, n, 2, 0, blocks(2, 0), cap));  // only scenes whose events overflowed
+    // 4. gradient: fold, W^T term, regulariser
+    fork();
+    for (int i = 0; i < n; ++i) {
+        g = b->grids[i];
+        cudaStream_t st = b->branch[i];
+        MST_CK(launch_fold_grad(g, st));
+        MST_CK(launch_combine_full(g, g->gT, g->g64, grads[i], st));
+        if (params[i].reg_eta != 0.0)
+            MST_CK(launch_regularizer(g, betas[i], params[i].reg_eta, g->lap, g->stats + MST_NSTATS + 1, losses + i,
+                                      grads[i], st));
+    }
+    join();
+    return MST_OK;
 }
 
 }  // namespace
@@ -1333,6 +1509,129 @@ void mst_batch_destroy(mst_batch* b) {
 
 const char* mst_batch_last_error(mst_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
+int mst_batch_set_form(mst_batch* b, int form) {
+    if (!b) return MST_ERR_INVALID_ARG;
+    if (form != MST_BATCH_BRANCHES && form != MST_BATCH_PERSISTENT) {
+        b->err = "form must be MST_BATCH_BRANCHES or MST_BATCH_PERSISTENT";
+        return MST_ERR_INVALID_ARG;
+    }
+    b->form = form;
+    return MST_OK;
+}
+
+int mst_batch_get_form(mst_batch* b) { return b ? (b->persistent ? MST_BATCH_PERSISTENT : MST_BATCH_BRANCHES) : -1; }
+
+int mst_batch_set_wavefront(mst_batch* b, int forward_trip, int forward_blocks, int replay_trip, int replay_blocks) {
+    if (!b) return MST_ERR_INVALID_ARG;
+    const bool ft = forward_trip == 0 || forward_trip == 8 || forward_trip == 10 || forward_trip == 12 ||
+                    forward_trip == 16;
+    const bool rt = replay_trip == 0 || replay_trip == 4 || replay_trip == 6 || replay_trip == 8 || replay_trip == 10;
+    if (!ft || !rt || forward_blocks < 0 || forward_blocks > 8 || replay_blocks < 0 || replay_blocks > 8) {
+        b->err = "forward trip in {0, 8, 10, 12, 16}, pass-2 trip in {0, 4, 6, 8, 10}, blocks per SM in 0..8";
+        return MST_ERR_INVALID_ARG;
+    }
+    b->trip_fwd = forward_trip == 12 ? 0 : forward_trip;  // 12 and 6 are the kernels' defaults
+    b->blocks_fwd = forward_blocks;
+    b->trip_p2 = replay_trip == 6 ? 0 : replay_trip;
+    b->blocks_p2 = replay_blocks;
+    return MST_OK;
+}
+
+int mst_batch_autotune(mst_batch* b, const float* const* betas, const mst_params* params, const double* const* meas,
+                       int sample_div, int* choice, void* stream) {
+    if (!b) return MST_ERR_INVALID_ARG;
+    if (!betas || !params || !meas || !choice || sample_div < 1) {
+        b->err = "betas, params, images_meas and choice are required, sample_div >= 1";
+        return MST_ERR_INVALID_ARG;
+    }
+    const int n = b->n;
+    DeviceGuard dg(b->device);
+    cudaStream_t st = as_stream(stream);
+    // the sample: each scene's photons divided by sample_div, no regulariser, images not returned
+    std::vector<mst_params> q(params, params + n);
+    for (auto& x : q) {
+        x.n_photons = std::max<uint64_t>(1, x.n_photons / (uint64_t)sample_div);
+        x.n_photons_total = 0;
+        x.reg_eta = 0.0;
+    }
+    std::vector<double*> grads(n, nullptr);
+    double* losses = nullptr;
+    bool ok = cudaMalloc(&losses, sizeof(double) * n) == cudaSuccess;
+    for (int i = 0; i < n && ok; ++i) ok = cudaMalloc(&grads[i], sizeof(double) * b->grids[i]->geo.nvox) == cudaSuccess;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    std::vector<unsigned long long> ev_last0(n);
+    for (int i = 0; i < n; ++i) ev_last0[i] = b->grids[i]->ev_last;
+    const int saved[4] = {b->trip_fwd, b->blocks_fwd, b->trip_p2, b->blocks_p2};
+    int rc = ok ? MST_OK : MST_ERR_OOM;
+    if (!ok) b->err = "autotune buffers: out of device memory";
+    auto timed = [&](double& ms) -> int {  // best of two sample calls (one graph launch each)
+        ms = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, st);
+            const int e = mst_batch_render_grad(b, betas, q.data(), meas, nullptr, nullptr, grads.data(), losses, st);
+            if (e) return e;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return MST_ERR_CUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, (double)t);
+        }
+        return MST_OK;
+    };
+    // one axis at a time: the forward's trip and blocks, then pass 2's
+    int best[4] = {12, 0, 6, 0};
+    double ms = 0.0;
+    if (rc == MST_OK) rc = mst_batch_set_wavefront(b, 12, 0, 6, 0);
+    if (rc == MST_OK) rc = timed(ms);  // warm-up: buffers sized, graph captured
+    const int occ_f = transport_batch_blocks_per_sm(0);
+    const int occ_r = transport_batch_blocks_per_sm(4);
+    double best_ms = 1e30;
+    for (int t : {8, 10, 12, 16})
+        for (int bl = occ_f; bl >= std::max(1, occ_f - 1) && rc == MST_OK; --bl) {
+            rc = mst_batch_set_wavefront(b, t, bl, best[2], best[3]);
+            if (rc == MST_OK) rc = timed(ms);
+            if (rc == MST_OK && ms < best_ms) {
+                best_ms = ms;
+                best[0] = t;
+                best[1] = bl;
+            }
+        }
+    best_ms = 1e30;
+    for (int t : {4, 6, 8, 10})
+        for (int bl = occ_r; bl >= std::max(1, occ_r - 1) && rc == MST_OK; --bl) {
+            rc = mst_batch_set_wavefront(b, best[0], best[1], t, bl);
+            if (rc == MST_OK) rc = timed(ms);
+            if (rc == MST_OK && ms < best_ms) {
+                best_ms = ms;
+                best[2] = t;
+                best[3] = bl;
+            }
+        }
+    for (int i = 0; i < n; ++i) {  // the sample's event counts must not size the real calls' buffers
+        b->grids[i]->ev_last = ev_last0[i];
+        b->grids[i]->ev_seen_pending = false;
+    }
+    if (b->launched) {
+        cudaEventSynchronize(b->done);
+        b->launched = false;
+    }
+    cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (double* p : grads) cudaFree(p);
+    cudaFree(losses);
+    if (rc) {
+        b->trip_fwd = saved[0];
+        b->blocks_fwd = saved[1];
+        b->trip_p2 = saved[2];
+        b->blocks_p2 = saved[3];
+        return rc;
+    }
+    for (int k = 0; k < 4; ++k) choice[k] = best[k];
+    return mst_batch_set_wavefront(b, best[0], best[1], best[2], best[3]);
+}
+
 int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_params* params,
                           const double* const* meas, const uint8_t* const* masks, double* const* images,
                           double* const* grads, double* losses, void* stream) {
@@ -1374,6 +1673,11 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
             key_add(k, g->batch_stored);
         }
         key_add(k, losses);
+        key_add(k, b->form);
+        key_add(k, b->trip_fwd);
+        key_add(k, b->blocks_fwd);
+        key_add(k, b->trip_p2);
+        key_add(k, b->blocks_p2);
         return k;
     };
     // A handle whose events overflowed its buffer in the last launch (W then came from replay
@@ -1420,6 +1724,12 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
             b->err = "stream error before capture";
             return MST_ERR_CUDA;
         }
+        b->persistent = persistent_ok(b, params);
+        if (b->persistent) {
+            transport_batch_blocks_per_sm(0);  // function attributes and occupancy, outside the capture
+            const int rc0 = persistent_tables(b, betas, params);
+            if (rc0) return rc0;
+        }
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             b->err = "cudaStreamBeginCapture failed";
@@ -1427,14 +1737,22 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
         }
         int rc = MST_OK;
         for (int i = 0; i < b->n; ++i) b->grids[i]->capturing = true;  // no allocation in the branches
-        cudaEventRecord(b->fork, b->cap);
-        for (int i = 0; i < b->n && rc == MST_OK; ++i) {
-            cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-            rc = render_grad_impl(b->grids[i], betas[i], &params[i], meas[i], masks ? masks[i] : nullptr,
-                                  images ? images[i] : nullptr, grads[i], losses + i, b->branch[i]);
-            if (rc) b->err = "scene " + std::to_string(i) + ": " + b->grids[i]->err;
-            cudaEventRecord(b->join[i], b->branch[i]);
-            cudaStreamWaitEvent(b->cap, b->join[i], 0);
+        if (b->persistent) {
+            rc = persistent_sequence(b, betas, params, meas, masks, images, grads, losses);
+            if (rc) {
+                for (int i = 0; i < b->n; ++i)
+                    if (!b->grids[i]->err.empty()) b->err = "scene " + std::to_string(i) + ": " + b->grids[i]->err;
+            }
+        } else {
+            cudaEventRecord(b->fork, b->cap);
+            for (int i = 0; i < b->n && rc == MST_OK; ++i) {
+                cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+                rc = render_grad_impl(b->grids[i], betas[i], &params[i], meas[i], masks ? masks[i] : nullptr,
+                                      images ? images[i] : nullptr, grads[i], losses + i, b->branch[i]);
+                if (rc) b->err = "scene " + std::to_string(i) + ": " + b->grids[i]->err;
+                cudaEventRecord(b->join[i], b->branch[i]);
+                cudaStreamWaitEvent(b->cap, b->join[i], 0);
+            }
         }
         const cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
         for (int i = 0; i < b->n; ++i) b->grids[i]->capturing = false;

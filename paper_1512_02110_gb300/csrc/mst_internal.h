@@ -212,6 +212,15 @@ cudaError_t launch_classic_residual(const mst_grid* g, const double* img, const 
 cudaError_t launch_regularizer(const mst_grid* g, const float* beta, double eta, double* lap, double* psi,
                                double* loss, double* grad, cudaStream_t st);
 int transport_blocks_per_sm(int dtype, int mode, bool two);
+// The batched form (FP32 grid, one species): one persistent launch of transport mode `mode` (0, 3,
+// 4 or 2) over n scenes whose arguments sit in the device table, scene after scene in every warp;
+// trip as in the handle's wavefront setting (0: the mode's default).
+cudaError_t launch_transport_batch(const TransportArgs* table, int n, int mode, int trip, int blocks,
+                                   cudaStream_t st);
+cudaError_t launch_event_adjoint_batch(const TransportArgs* table, int n, int blocks, cudaStream_t st);
+// Resident blocks per SM of the batched kernels of a mode; the first call sets the attributes of
+// every batched instantiation (call it before a stream capture).
+int transport_batch_blocks_per_sm(int mode);
 // blocks of a persistent transport launch of this mode on the handle (its wavefront setting)
 inline int transport_blocks(const mst_grid* g, int dtype, int mode) {
     const int occ = transport_blocks_per_sm(dtype, mode, g->air != nullptr);

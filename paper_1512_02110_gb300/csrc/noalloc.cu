@@ -1,8 +1,8 @@
 // LOS transmittance for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA graph capture, a
-// host that hands out device memory only through its own arena, or a plugin whose process
-// forbids allocation after start-up. mst_transmittance_noalloc serves them: it takes no
+// Some callers cannot call cudaMalloc at all: a host that hands out device memory only through
+// its own arena, or a plugin whose process forbids allocation after start-up.
+// mst_transmittance_noalloc serves them: it takes no
 // handle, and the only scratch it needs (the staged extinction grid) lives in
 // a file-scope device array that every GPU loading this library holds until the process ends.
 // The caller passes beta and T; nothing is allocated or freed here.
@@ -69,10 +69,12 @@ extern "C" int mst_transmittance_noalloc(const mst_grid_desc* d, int n_cams, con
     const int rc = ext_address(dev, &scratch);
     if (rc != MST_OK) return rc;
 
-    // A descriptor on the host stack for the existing launchers: grid geometry, cameras and the
-    // static extinction array; no statistics are kept.
+    // A descriptor on the host stack for the two launchers below (launch_stage, launch_los):
+    // grid geometry, cameras and the static extinction array; no statistics and no padded grid
+    // are kept (stats and ext_pad stay NULL, which both launchers accept).
     mst_grid g;
     g.device = dev;
+    cudaDeviceGetAttribute(&g.sm_count, cudaDevAttrMultiProcessorCount, dev);
     mst::Geo& geo = g.geo;
     geo.nx = d->nx; geo.ny = d->ny; geo.nz = d->nz;
     geo.hx = (float)d->dx; geo.hy = (float)d->dy; geo.hz = (float)d->dz;

@@ -472,9 +472,9 @@ constexpr uint32_t kNoPhoton = 0xFFFFFFFFu;  // photon word of a chunk's unused 
 constexpr int kSlots = 64;
 // Voxels a flying lane advances per loop trip, and minimum resident blocks per SM (register
 // budget), per kernel mode; set from sweeps on the 64^3 cumulus workload.
-constexpr int kStepsForward = 8;
+constexpr int kStepsForward = 12;
 constexpr int kStepsPass1 = 8;
-constexpr int kStepsPass2 = 5;
+constexpr int kStepsPass2 = 6;
 constexpr int kMinBlocksForward = 3;  // voxel estimator; the classic one keeps a 1-block budget
 constexpr int kMinBlocksClassic = 1;
 constexpr int kMinBlocksPass1 = 3;
@@ -673,20 +673,24 @@ __device__ __forceinline__ void flush_tally(const TransportArgs& A, const Tally&
 // TWO: two-species medium (the launch has an air field); one-species kernels carry none of its
 // code. TRIP: voxels a flying lane advances per loop trip (0: the mode's default), a compile-time
 // constant (a run-time bound cost the forward 2 %); the autotuner picks among the instantiated ones.
-template <int DT, int MODE, bool TWO, int TRIP = 0>
-__global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMinBlocksPass2
-                                                       : (MODE == kPass1 ? kMinBlocksPass1
-                                                          : ((MODE == kFwdClassic || MODE == kPass1C || MODE == kPass2C)
-                                                                 ? kMinBlocksClassic
-                                                                 : kMinBlocksForward)))
-    k_transport(const TransportArgs A) {
+constexpr int min_blocks(int mode) {
+    return (mode == kPass2 || mode == kPass2W)
+               ? kMinBlocksPass2
+               : (mode == kPass1 ? kMinBlocksPass1
+                                 : ((mode == kFwdClassic || mode == kPass1C || mode == kPass2C) ? kMinBlocksClassic
+                                                                                                 : kMinBlocksForward));
+}
+
+// One scene's photons, run by every warp of the launch until the scene's pool is dry and the
+// warp holds none of its photons (flying, queued for an event or ready).
+template <int DT, int MODE, bool TWO, int TRIP>
+__device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* smem) {
     constexpr bool PASS1 = MODE == kPass1 || MODE == kPass1C;
     constexpr bool PASS2 = MODE == kPass2 || MODE == kPass2W || MODE == kPass2C;
     constexpr bool CLASSIC_ADJ = MODE == kPass1C || MODE == kPass2C;
     constexpr bool REPLAY = PASS1 || PASS2;
     constexpr int kStepsPerTrip = TRIP > 0 ? TRIP : (PASS2 ? kStepsPass2 : (PASS1 ? kStepsPass1 : kStepsForward));
     constexpr int NW = Rec<REPLAY>::NW;
-    extern __shared__ uint32_t smem[];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned warp = threadIdx.x >> 5;
     const Stack<NW> stk{smem + warp * NW * kSlots, kSlots};  // events at slot i, ready photons at kSlots-1-i
@@ -913,12 +917,31 @@ __global__ void __launch_bounds__(kTB, (MODE == kPass2 || MODE == kPass2W) ? kMi
     }
 }
 
+template <int DT, int MODE, bool TWO, int TRIP = 0>
+__global__ void __launch_bounds__(kTB, min_blocks(MODE)) k_transport(const TransportArgs A) {
+    extern __shared__ uint32_t smem[];
+    transport_run<DT, MODE, TWO, TRIP>(A, smem);
+}
+
+// Many scenes in one persistent launch (the batched form): every warp runs the scenes one after
+// the other from a table in device memory, each until its photons are done, so the launch ends on
+// one tail instead of one per scene and small scenes fill the GPU together with large ones.
+template <int DT, int MODE, bool TWO, int TRIP = 0>
+__global__ void __launch_bounds__(kTB, min_blocks(MODE))
+    k_transport_batch(const TransportArgs* __restrict__ scenes, int n_scenes) {
+    extern __shared__ uint32_t smem[];
+    for (int s = 0; s < n_scenes; ++s) {
+        transport_run<DT, MODE, TWO, TRIP>(scenes[s], smem);
+        __syncwarp();
+    }
+}
+
 // w_s of every event the forward stored, instead of replay pass 1: the same arithmetic
 // (le_adjoint) on the same event state, written to the photon's slot in wseq for pass 2 and
 // added to W in FP64; nevbuf (zeroed after the slot scan) receives each photon's last event with
 // w_s != 0. Does nothing when the events did not fit (pass 1 then walks the paths).
 template <bool TWO>
-__global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
+__device__ __forceinline__ void event_adjoint_run(const TransportArgs& A) {
     const unsigned long long cnt = *A.ev_count;  // reserved slots: whole chunks
     if (cnt > A.ev_cap) return;
     const unsigned long long C = A.ev_cap;
@@ -963,6 +986,20 @@ __global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
     }
     stored = warp_sumu(stored);
     if ((threadIdx.x & 31u) == 0u && stored) atomicAdd(A.stats + MST_ST_EVENTS_STORED, (double)stored);
+}
+
+template <bool TWO>
+__global__ void __launch_bounds__(kTB) k_event_adjoint(const TransportArgs A) {
+    event_adjoint_run<TWO>(A);
+}
+
+// the batched form: the scenes of a table one after the other (block-uniform)
+template <bool TWO>
+__global__ void __launch_bounds__(kTB) k_event_adjoint_batch(const TransportArgs* __restrict__ scenes, int n_scenes) {
+    for (int s = 0; s < n_scenes; ++s) {
+        event_adjoint_run<TWO>(scenes[s]);
+        __syncthreads();
+    }
 }
 
 // Exclusive prefix sum of the photons' event counts (three passes over tiles of kScanTile):
@@ -1190,16 +1227,16 @@ template <int MODE, bool TWO>
 cudaError_t launch_trip(const TransportArgs& a, int trip, int blocks, cudaStream_t st) {
     if constexpr (MODE == kFwdVoxel) {
         switch (trip) {
-            case 6: return launch_mode<0, MODE, TWO, 6>(a, blocks, st);
+            case 8: return launch_mode<0, MODE, TWO, 8>(a, blocks, st);
             case 10: return launch_mode<0, MODE, TWO, 10>(a, blocks, st);
-            case 12: return launch_mode<0, MODE, TWO, 12>(a, blocks, st);
+            case 16: return launch_mode<0, MODE, TWO, 16>(a, blocks, st);
             default: return launch_mode<0, MODE, TWO>(a, blocks, st);
         }
     } else {
         switch (trip) {
             case 4: return launch_mode<0, MODE, TWO, 4>(a, blocks, st);
-            case 6: return launch_mode<0, MODE, TWO, 6>(a, blocks, st);
             case 8: return launch_mode<0, MODE, TWO, 8>(a, blocks, st);
+            case 10: return launch_mode<0, MODE, TWO, 10>(a, blocks, st);
             default: return launch_mode<0, MODE, TWO>(a, blocks, st);
         }
     }
@@ -1243,7 +1280,68 @@ cudaError_t launch_species(const TransportArgs& a, int dtype, int mode, int trip
                                     : launch_dt<2, TWO>(a, mode, trip, blocks, st));
 }
 
+// The batched form: FP32 grid, one species, the modes of the full gradient with stored events.
+// Function attributes (shared memory, carveout) are set by batch_occupancy() before any launch,
+// outside a stream capture.
+template <int MODE, int TRIP = 0>
+cudaError_t launch_batch_mode(const TransportArgs* table, int n, int blocks, cudaStream_t st) {
+    k_transport_batch<0, MODE, false, TRIP><<<blocks, kTB, smem_bytes<(MODE >= 2)>(), st>>>(table, n);
+    return cudaGetLastError();
+}
+
+template <int MODE, int TRIP = 0>
+int batch_occupancy() {
+    return occupancy(k_transport_batch<0, MODE, false, TRIP>, smem_bytes<(MODE >= 2)>());
+}
+
 }  // namespace
+
+cudaError_t launch_transport_batch(const TransportArgs* table, int n, int mode, int trip, int blocks,
+                                   cudaStream_t st) {
+    switch (mode) {
+        case kFwdVoxel:
+            switch (trip) {
+                case 8: return launch_batch_mode<kFwdVoxel, 8>(table, n, blocks, st);
+                case 10: return launch_batch_mode<kFwdVoxel, 10>(table, n, blocks, st);
+                case 16: return launch_batch_mode<kFwdVoxel, 16>(table, n, blocks, st);
+                default: return launch_batch_mode<kFwdVoxel>(table, n, blocks, st);
+            }
+        case kPass2W:
+            switch (trip) {
+                case 4: return launch_batch_mode<kPass2W, 4>(table, n, blocks, st);
+                case 8: return launch_batch_mode<kPass2W, 8>(table, n, blocks, st);
+                case 10: return launch_batch_mode<kPass2W, 10>(table, n, blocks, st);
+                default: return launch_batch_mode<kPass2W>(table, n, blocks, st);
+            }
+        case kPass2: return launch_batch_mode<kPass2>(table, n, blocks, st);
+        case kPass1: return launch_batch_mode<kPass1>(table, n, blocks, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int transport_batch_blocks_per_sm(int mode) {
+    static int occ[7] = {0, 0, 0, 0, 0, 0, 0};
+    static bool ready = false;
+    if (!ready) {  // every instantiation's attributes, once; the default trips give the occupancy
+        occ[kFwdVoxel] = batch_occupancy<kFwdVoxel>();
+        batch_occupancy<kFwdVoxel, 8>();
+        batch_occupancy<kFwdVoxel, 10>();
+        batch_occupancy<kFwdVoxel, 16>();
+        occ[kPass2W] = batch_occupancy<kPass2W>();
+        batch_occupancy<kPass2W, 4>();
+        batch_occupancy<kPass2W, 8>();
+        batch_occupancy<kPass2W, 10>();
+        occ[kPass2] = batch_occupancy<kPass2>();
+        occ[kPass1] = batch_occupancy<kPass1>();
+        ready = true;
+    }
+    return mode >= 0 && mode < 7 && occ[mode] > 0 ? occ[mode] : 1;
+}
+
+cudaError_t launch_event_adjoint_batch(const TransportArgs* table, int n, int blocks, cudaStream_t st) {
+    k_event_adjoint_batch<false><<<blocks, kTB, 0, st>>>(table, n);
+    return cudaGetLastError();
+}
 
 int transport_blocks_per_sm(int dtype, int mode, bool two) {
     static int cache[2][3][7] = {{{0}}};

@@ -91,3 +91,82 @@ def test_batch_rejects_shared_handles(m):
     g = m.Grid.from_scene(f32_scene(sc))
     with pytest.raises(m.MSTError):
         m.Batch([g, g])
+
+
+def _diverged(m, grid, sc, p, beta):
+    import torch
+    import oracle
+    h = torch.zeros(p.n_photons, dtype=torch.int32, device="cuda")
+    grid.set_debug(h, None)
+    grid.render(beta, m.make_params(p), images=False)
+    grid.set_debug(None, None)
+    return (h.cpu().numpy().view(np.uint32) != oracle.render(sc, p, want_L=False, hashes=True)["hash"]).astype(np.uint8)
+
+
+def test_persistent_batch_matches_the_oracle(m):
+    """Three scenes of different grids, cameras and optics in one persistent launch per transport
+    pass (the batched form of the full gradient), each against the FP64 oracle: images to 1e-4,
+    loss to 1e-4, gradient to 1e-3 relative L2 (Sec. 3.3 Eq. Icpixel, Eq. Cost, Sec. 5.1
+    Eq. divCost1), photons whose FP32 path left the oracle's voxel sequence excluded on both
+    sides."""
+    import torch
+    import oracle
+    cases = _scenes()
+    grids = [m.Grid.from_scene(sc) for sc, _ in cases]
+    betas_np = [synth.smoothed(sc.beta, sc.shape, 0.3).astype(np.float32).astype(np.float64) for sc, _ in cases]
+    betas = [dev(b, np.float32) for b in betas_np]
+    meas = [oracle.forward_images(sc, p.replace(seed=p.seed + 100))[0] for sc, p in cases]
+    skips = [_diverged(m, g, sc.with_beta(b), p, bd) for g, (sc, p), b, bd in zip(grids, cases, betas_np, betas)]
+    for g, s in zip(grids, skips):
+        g.set_debug(None, dev(s, np.uint8))
+    params = [m.make_params(p, grad_mode="full", reg_eta=0.05) for _, p in cases]
+    batch = m.Batch(grids)
+    batch.set_form("persistent")
+    out = batch.render_grad(betas, params, [dev(x, np.float64) for x in meas], images=True)
+    torch.cuda.synchronize()
+    assert batch.form() == "persistent"
+    for i, ((sc, p), b, s) in enumerate(zip(cases, betas_np, skips)):
+        st = grids[i].stats()
+        assert st["events_stored"] == st["events"] > 0
+        ref = oracle.full_grad(sc.with_beta(b), p, meas[i], eta=0.05, skip=s)
+        img = out["images"][i].cpu().numpy()
+        ei = float(np.max(np.abs(img - ref["images"]) / np.maximum(np.abs(ref["images"]),
+                                                                   1e-3 * np.abs(ref["images"]).max())))
+        el = abs(out["loss"][i].item() - ref["loss"]) / ref["loss"]
+        eg = rel_l2(out["grad"][i].cpu().numpy(), ref["grad"])
+        record(f"batch_persistent_oracle[{i}]", diverged_frac=s.mean(), images_max_rel=ei, loss_rel=el, grad_rel_l2=eg)
+        assert ei < 1e-4 and el < 1e-4 and eg < 1e-3, (i, ei, el, eg)
+    for g in grids:
+        g.set_debug(None, None)
+    batch.close()
+
+
+def test_persistent_and_branch_forms_agree(m):
+    """The same full-gradient batch as one persistent launch per pass and as one graph branch
+    per scene, call after call (capture, then replay), with the wavefront the batch autotuner
+    picks: equal up to the order of the FP32 atomic additions."""
+    import torch
+    cases = _scenes()
+    grids = [m.Grid.from_scene(sc) for sc, _ in cases]
+    betas = [dev(synth.smoothed(sc.beta, sc.shape, 0.3), np.float32) for sc, _ in cases]
+    meas = [g.render(dev(sc.beta, np.float32), m.make_params(p, seed=p.seed + 100))["images"]
+            for g, (sc, p) in zip(grids, cases)]
+    params = [m.make_params(p, grad_mode="full") for _, p in cases]
+    batch = m.Batch(grids)
+    batch.set_form("persistent")
+    choice = batch.autotune(betas, params, meas, sample_div=4)
+    assert choice["forward_trip"] in (8, 10, 12, 16) and choice["replay_trip"] in (4, 6, 8, 10)
+    pers = [batch.render_grad(betas, params, meas) for _ in range(2)]
+    torch.cuda.synchronize()
+    assert batch.form() == "persistent"
+    batch.set_form("branches")
+    br = batch.render_grad(betas, params, meas)
+    torch.cuda.synchronize()
+    assert batch.form() == "branches"
+    for i in range(len(cases)):
+        for rep, o in enumerate(pers):
+            eg = rel_l2(o["grad"][i].cpu().numpy(), br["grad"][i].cpu().numpy())
+            el = abs(o["loss"][i].item() - br["loss"][i].item()) / br["loss"][i].item()
+            record(f"batch_persistent_vs_branches[{i},rep{rep}]", grad_rel_l2=eg, loss_rel=el)
+            assert eg < 1e-5 and el < 1e-6, (i, rep, eg, el)
+    batch.close()

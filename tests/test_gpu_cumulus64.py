@@ -1,8 +1,8 @@
 """Oracle parity at the benchmark scene itself: the 64^3 x 20 m cumulus field with 9 in-situ
 128x128 cameras (two inside the cloud base), rendered and differentiated by the CUDA path in the
-benchmark's launch configuration (stored-event adjoint, wavefront of 8 voxels per trip and 3
-blocks per SM forward, 5 and 3 in replay pass 2) at 1e5 photons, which the FP64 oracle traces in
-about a second.
+benchmark's launch configuration (stored-event adjoint, the wavefront its autotuner picks on this
+scene: 16 voxels per trip and 3 blocks per SM forward, 8 and 3 in replay pass 2) at 1e5 photons,
+which the FP64 oracle traces in about a second.
 
 Which photons are compared. The same Philox streams drive both sides, but FP32 and FP64 carry
 a photon along paths that drift apart: a collision point l = tau / beta amplifies the rounding of
@@ -33,7 +33,7 @@ from tests.gpu_util import dev, f32_scene, max_rel, need_gpu, record, rel_l2
 pytestmark = pytest.mark.gpu
 
 N_PHOTONS = 100_000
-WAVEFRONT = dict(forward_trip=8, forward_blocks=3, replay_trip=5, replay_blocks=3)
+WAVEFRONT = dict(forward_trip=16, forward_blocks=3, replay_trip=8, replay_blocks=3)
 DRIFT = 1e-4  # metres between the FP32 and FP64 last event points of a photon
 
 

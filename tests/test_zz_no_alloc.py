@@ -1,5 +1,5 @@
 """mst_transmittance_noalloc, the entry point for callers that cannot allocate device memory
-(code inside a stream capture, hosts with their own memory arena). It must give the same
+(hosts with their own memory arena, plugins that may not allocate after start-up). It must give the same
 transmittance as the handle-based mst_transmittance, call after call, using only its fixed
 device scratch array. Collected last on purpose: a failure here leaves every other test run."""
 import ctypes
