@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default wavefront shape")
+    ap.add_argument("--wavefront", default=None,
+                    help="forward trip, forward blocks per SM, pass-2 trip, pass-2 blocks per SM (e.g. 16,3,8,3): set "
+                         "instead of autotuning")
     ap.add_argument("--no-replay-form", action="store_true",
                     help="skip the timing of the replay form (W by replay pass 1, no stored events)")
     ap.add_argument("--cpu-photons", type=float, default=1e6, help="photons of the CPU-baseline sample")
@@ -260,8 +263,13 @@ def run_ours(args):
     params = m.make_params(p, grad_mode=args.grad, grid_dtype=args.grid_dtype)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
     # wavefront shape picked by the autotuner on this scene (2^24-photon calls), before the warm-up
-    wavefront = None if args.no_autotune else grid.autotune(beta, m.make_params(p, grid_dtype=args.grid_dtype),
-                                                            n_sample=1 << 24)
+    if args.wavefront:
+        wf = [int(v) for v in args.wavefront.split(",")]
+        grid.set_wavefront(*wf)
+        wavefront = dict(forward_trip=wf[0], forward_blocks_per_sm=wf[1], replay_trip=wf[2], replay_blocks_per_sm=wf[3])
+    else:
+        wavefront = None if args.no_autotune else grid.autotune(beta, m.make_params(p, grid_dtype=args.grid_dtype),
+                                                                n_sample=1 << 24)
 
     for _ in range(args.warmup):
         grid.render_grad(beta, params, meas, images=False)
