@@ -589,8 +589,19 @@ def run_classic_study(args):
         torch.cuda.synchronize()
         st = grid.stats()
         out[est] = {"ms": a.elapsed_time(b), "phase_ms": {k: v[0] for k, v in grid.phase_times().items() if v[1]},
-                    "segments": st["segments"], "replay_segments": st["replay_segments"], "events": st["events"]}
+                    "segments": st["segments"], "replay_segments": st["replay_segments"], "events": st["events"],
+                    "shadow_rays": st["shadow_rays"], "shadow_segments": st["shadow_segments"]}
         grid.set_profiling(False)
+        # the forward render alone (images, no gradient)
+        prm = m.make_params(p, estimator=est)
+        grid.render(beta, prm)
+        a.record()
+        grid.render(beta, prm)
+        b.record()
+        torch.cuda.synchronize()
+        st = grid.stats()
+        out[est]["forward_only"] = {"ms": a.elapsed_time(b), "segments": st["segments"], "events": st["events"],
+                                    "shadow_rays": st["shadow_rays"], "shadow_segments": st["shadow_segments"]}
     print(json.dumps(out))
     return 0
 

@@ -67,7 +67,10 @@ enum {
     MST_ST_REPLAY_SCATTERS = 22, MST_ST_LOST = 23, /* walks abandoned (non-finite direction); 0 in valid use */
     MST_ST_EVENTS_STORED = 24, /* full gradient: events the forward stored for the adjoint (0: replayed instead) */
     MST_ST_BMC_PATHS = 25, MST_ST_BMC_EVENTS = 26, MST_ST_BMC_SEGMENTS = 27, /* mst_render_bmc: flight + sun-ray voxels */
-    MST_ST_AIR_EVENTS = 28 /* two-species medium (mst_set_air): forward events whose particle was air */
+    MST_ST_AIR_EVENTS = 28, /* two-species medium (mst_set_air): forward events whose particle was air */
+    MST_ST_SHADOW_RAYS = 29, MST_ST_SHADOW_SEGMENTS = 30 /* classic estimator (Eq. fle): shadow rays walked by the
+                                                            call's transport passes, and their voxel segments (the
+                                                            scatter walk of replay pass 2 counted again) */
 };
 
 /* phases timed by the profiler (mst_get_phase_times) */

@@ -34,7 +34,7 @@ STAT_NAMES = ["esc_xm", "esc_xp", "esc_ym", "esc_yp", "esc_zm", "esc_zp", "absor
               "forced", "events", "segments", "capped", "escaped_n", "launched", "traced", "replay_segments",
               "replay_events", "los_segments", "pixel_segments", "backproj_segments", "losadj_segments",
               "replay_scatters", "lost", "events_stored", "bmc_paths", "bmc_events", "bmc_segments",
-              "air_events"]
+              "air_events", "shadow_rays", "shadow_segments"]
 EXPORTS = ["mst_version", "mst_default_params", "mst_create_grid", "mst_destroy", "mst_render", "mst_render_grad",
            "mst_transmittance", "mst_form_images", "mst_surrogate_grad", "mst_ray_counts", "mst_regularizer",
            "mst_set_debug", "mst_set_debug_points", "mst_get_stats", "mst_sync", "mst_last_error", "mst_set_profiling",

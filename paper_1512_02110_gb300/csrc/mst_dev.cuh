@@ -114,7 +114,7 @@ __device__ __forceinline__ void hg_sample(const HG& h, float u, float& ct, float
         omc = 2.f * (1.f - u);
         opc = 2.f * u;
     } else {
-        const float D = h.omg + h.tg * u;
+        const float D = fmaf(h.tg, u, h.omg);  // spelled out, like the multiply-adds of rotate_dir
         const float s = h.omg2 / D;
         omc = h.omg * (1.f - u) * (s + h.omg) / D;
         opc = h.opg * u * (s + h.opg) / D;
@@ -138,21 +138,26 @@ __device__ __forceinline__ void rayleigh_sample(float u, float& ct, float& st) {
 
 // New unit direction at polar angle (cos ct, sin st) and azimuth 2 pi u1 about d. Transverse
 // frame: e2 = normalize(axis x d), e1 = e2 x d, axis = z unless |d_z| >= 0.9, then x.
+// Every multiply-add is spelled out (fmaf, or __fmul_rn which is never fused): the kernels that
+// replay a path must compute each direction bit for bit like the forward did, whatever the
+// compiler fuses in the code around them.
 __device__ __forceinline__ float3 rotate_dir(float3 d, float ct, float st, float u1) {
     float sp, cp;
     sincospif(2.f * u1, &sp, &cp);
     float3 e2;
     if (fabsf(d.z) < 0.9f) {
-        const float n = rsqrtf(d.x * d.x + d.y * d.y);
+        const float n = rsqrtf(fmaf(d.x, d.x, __fmul_rn(d.y, d.y)));
         e2 = make_float3(-d.y * n, d.x * n, 0.f);
     } else {
-        const float n = rsqrtf(d.y * d.y + d.z * d.z);
+        const float n = rsqrtf(fmaf(d.y, d.y, __fmul_rn(d.z, d.z)));
         e2 = make_float3(0.f, -d.z * n, d.y * n);
     }
-    const float3 e1 = make_float3(e2.y * d.z - e2.z * d.y, e2.z * d.x - e2.x * d.z, e2.x * d.y - e2.y * d.x);
-    float3 o = make_float3(st * (cp * e1.x + sp * e2.x) + ct * d.x, st * (cp * e1.y + sp * e2.y) + ct * d.y,
-                           st * (cp * e1.z + sp * e2.z) + ct * d.z);
-    const float rn = rsqrtf(o.x * o.x + o.y * o.y + o.z * o.z);
+    const float3 e1 = make_float3(fmaf(e2.y, d.z, -__fmul_rn(e2.z, d.y)), fmaf(e2.z, d.x, -__fmul_rn(e2.x, d.z)),
+                                  fmaf(e2.x, d.y, -__fmul_rn(e2.y, d.x)));
+    const float3 o = make_float3(fmaf(st, fmaf(cp, e1.x, __fmul_rn(sp, e2.x)), __fmul_rn(ct, d.x)),
+                                 fmaf(st, fmaf(cp, e1.y, __fmul_rn(sp, e2.y)), __fmul_rn(ct, d.y)),
+                                 fmaf(st, fmaf(cp, e1.z, __fmul_rn(sp, e2.z)), __fmul_rn(ct, d.z)));
+    const float rn = rsqrtf(fmaf(o.x, o.x, fmaf(o.y, o.y, __fmul_rn(o.z, o.z))));
     return make_float3(o.x * rn, o.y * rn, o.z * rn);
 }
 

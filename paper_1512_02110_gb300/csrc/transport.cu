@@ -186,7 +186,10 @@ __device__ __forceinline__ void flight_init(Flight& f, const TransportArgs& A, c
 // tau <= beta * (distance to the next face). Returns true then, or when the voxel is the halo
 // (beta = +inf; the caller tells the two apart by b), with b and the face distance m of the voxel;
 // false after crossing into the next voxel. SCORE (replay pass 2): every voxel the flight crosses
-// receives -S * length in the gradient tile (padded like the grid).
+// receives -S * length in the gradient tile (padded like the grid). The product beta * m is
+// rounded on its own (__fmul_rn: never fused into the subtraction that follows), and so is the
+// product in flight_offset: the forward and the replay passes are different kernels, and a
+// multiply-add fused in one and not in another would send a photon along another path.
 template <int DT, bool SCORE>
 __device__ __forceinline__ bool flight_step(const TransportArgs& A, Flight& f, float& tau, float& b, float& m, float S,
                                             unsigned& nsc) {
@@ -196,7 +199,7 @@ __device__ __forceinline__ bool flight_step(const TransportArgs& A, Flight& f, f
     const bool py = !px && f.ty <= m;
     const int next = f.lin + (px ? f.dx : (py ? f.dy : f.dz));
     f.bn = BetaFetch<DT>::get(A.beta_pad, next);
-    const float bs = b * m;
+    const float bs = __fmul_rn(b, m);
     if (!(tau > bs)) return true;
     tau -= bs;
     if (SCORE && S != 0.f && m > 0.f) {
@@ -213,7 +216,7 @@ __device__ __forceinline__ bool flight_step(const TransportArgs& A, Flight& f, f
 // offset along one axis, inside the current voxel, of the point a distance l past the current
 // point (d: the direction component; p0: the flight's start offset, kept when d = 0)
 __device__ __forceinline__ float flight_offset(float t, float d, float h, float p0, float l) {
-    const float v = d > 0.f ? h - (t - l) * d : (d < 0.f ? (t - l) * -d : p0);
+    const float v = d > 0.f ? h - __fmul_rn(t - l, d) : (d < 0.f ? (t - l) * -d : p0);
     return fminf(fmaxf(v, 0.f), h);
 }
 
@@ -334,53 +337,153 @@ __device__ __forceinline__ float le_adjoint(const TransportArgs& A, const Photon
     return air ? le_adjoint_p<true>(A, ph, w, k) : le_adjoint_p<false>(A, ph, w, k);
 }
 
-// Eq. fle: pixel p(X_s) of camera c += albedo I_s P t_{s->c} / (|V|^2 Omega_p)
-// Eq. fle: for each camera whose image holds the event, the pixel p gets
-// f = albedo I P(mu) exp(-tau(X_s -> X_c)) / (|X_c - X_s|^2 Omega_p). OP 0 adds f to the
-// classic image; OP 1 returns w_s = sum_c cres[p] f (the event's share of <dE/di, i>, for the
-// classic-estimator gradient); OP 2 also scatters the shadow-ray terms d f / d beta_m =
-// -f * (length of the ray in voxel m), weighted by cres[p], into the gradient tile.
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Optical depth t_{s->c} of Eq. fle: the segment from a point (voxel (ix, iy, iz) + offset p)
+// to camera cm's centre, walked on the padded grid like a free flight. The walk ends at the
+// camera or at the grid's boundary (the first halo voxel, extinction +inf: nothing outside the
+// grid attenuates). SCATTER: every voxel of the segment also receives sw * (its length) in the
+// gradient tile (padded like the grid), the shadow-ray term d f / d beta_m = -f * length.
+template <int DT, bool SCATTER>
+__device__ __forceinline__ float shadow_tau(const TransportArgs& A, int ix, int iy, int iz, float3 p, const Cam& cm,
+                                            float sw, unsigned& nseg) {
+    const Geo& g = A.g;
+    const float3 v = local_delta(g, ix, iy, iz, p, cm.ix, cm.iy, cm.iz, make_float3(cm.lx, cm.ly, cm.lz));
+    float rem = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    const float inv = 1.f / rem;
+    float tx, ty, tz, qx, qy, qz;
+    int dx, dy, dz;
+    flight_axis(fminf(fmaxf(p.x, 0.f), g.hx), v.x * inv, g.hx, 1, tx, qx, dx);
+    flight_axis(fminf(fmaxf(p.y, 0.f), g.hy), v.y * inv, g.hy, g.p0, ty, qy, dy);
+    flight_axis(fminf(fmaxf(p.z, 0.f), g.hz), v.z * inv, g.hz, g.p01, tz, qz, dz);
+    int lin = pad_index(g, ix, iy, iz);
+    float bn = BetaFetch<DT>::get(A.beta_pad, lin);
+    float tau = 0.f;
+#pragma unroll 1
+    for (;;) {
+        const float b = bn;
+        if (isinf(b)) break;
+        ++nseg;
+        const float m = fminf(tx, fminf(ty, tz));
+        const bool px = tx <= m;
+        const bool py = !px && ty <= m;
+        const int next = lin + (px ? dx : (py ? dy : dz));
+        const bool last = !(rem > m);
+        if (!last) bn = BetaFetch<DT>::get(A.beta_pad, next);
+        const float seg = last ? rem : m;
+        tau += b * seg;
+        if (SCATTER) atomicAdd(A.gacc + lin, sw * seg);
+        if (last) break;
+        rem -= m;
+        tx = px ? qx : tx - m;
+        ty = py ? qy : ty - m;
+        tz = (px || py) ? tz - m : qz;
+        lin = next;
+    }
+    return tau;
+}
+
+// Where an event lands in camera cm (Eq. fle): false when the camera does not see it (behind
+// the camera, outside the image, on the centre, or, with a residual, a pixel of zero residual);
+// else the pixel gp and f0 = albedo I_s P(mu) / (|X_c - X_s|^2 Omega_p), times the pixel's
+// residual when RES.
+template <bool RES>
+__device__ __forceinline__ bool classic_pixel(const TransportArgs& A, const Photon& ph, const Cam& cm, float w, bool air,
+                                              int& gp, float& f0) {
+    const float3 v = local_delta(A.g, cm.ix, cm.iy, cm.iz, make_float3(cm.lx, cm.ly, cm.lz), ph.ix, ph.iy, ph.iz, ph.p);
+    const float zc = v.x * cm.fx + v.y * cm.fy + v.z * cm.fz;
+    if (!(zc > 0.f)) return false;
+    const float x = (v.x * cm.rx + v.y * cm.ry + v.z * cm.rz) / zc;
+    const float y = (v.x * cm.ux + v.y * cm.uy + v.z * cm.uz) / zc;
+    const float px = floorf((x / cm.tx + 1.f) * 0.5f * (float)cm.w);
+    const float py = floorf((y / cm.ty + 1.f) * 0.5f * (float)cm.h);
+    if (px < 0.f || py < 0.f || px >= (float)cm.w || py >= (float)cm.h) return false;
+    gp = cm.pix_off + (int)py * cm.w + (int)px;
+    const float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
+    if (!(r2 > 0.f)) return false;
+    float cr = 1.f;
+    if (RES) {
+        cr = (float)A.cres[gp];
+        if (cr == 0.f) return false;
+    }
+    const float mu = -(ph.d.x * v.x + ph.d.y * v.y + ph.d.z * v.z) * rsqrtf(r2);
+    f0 = cr * (w * (air ? rayleigh_phase(mu) : hg_phase(A.hg, mu)) / (r2 * A.omega[gp]));
+    return true;
+}
+
+// Per-warp scratch of the classic estimate, in shared memory: for a group of kClassicGroup
+// cameras, each (event lane, camera) pair's value f (res) and pixel (pix), and the list of shadow
+// rays to walk (job: event lane | camera in the group << 5); per lane, the voxel segments its
+// shadow rays walked, and the warp's count of shadow rays (MST_ST_SHADOW_*).
+constexpr int kClassicGroup = 8;
+constexpr int kClassicWords = kClassicGroup * 32 * 2 + kClassicGroup * 32 / 4 + 32 + 4;  // per warp
+struct ClassicScratch {
+    float* res;      // [kClassicGroup][32]
+    int* pix;        // [kClassicGroup][32]
+    uint8_t* job;    // [kClassicGroup * 32]
+    unsigned* seg;   // [32]
+    unsigned* rays;  // [1]
+};
+
+// Eq. fle for the warp's round of events (lane i < n holds event i; act says whether this lane
+// holds one), shadow rays issued warp-coherently: the lanes first find, camera by camera, which
+// cameras see their event and compact those (event, camera) pairs into a list; then every lane
+// walks one shadow ray of the list at a time, 32 rays per pass over the list, so the warp's lanes
+// stay busy however few cameras see each event. OP 0 adds each f = f0 exp(-t) to its pixel of
+// the classic image; OP 1 returns w_s = sum_c cres[p] f (the event's share of <dE/di, i>, for the
+// classic-estimator gradient), summed over the cameras in their order; OP 2 also scatters the
+// shadow-ray terms -cres[p] f * (length in voxel m) into the gradient tile.
 template <int DT, int OP>
-__device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon& ph, float w, float* gacc, bool air) {
+__device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon& e, float w, bool air, bool act,
+                                            const ClassicScratch& cs) {
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t vox = (uint32_t)e.ix | ((uint32_t)e.iy << 11) | ((uint32_t)e.iz << 22);
     float acc = 0.f;
-    for (int c = 0; c < A.cams.n; ++c) {
-        const Cam& cm = A.cams.c[c];
-        // point relative to the camera
-        const float3 v = local_delta(A.g, cm.ix, cm.iy, cm.iz, make_float3(cm.lx, cm.ly, cm.lz), ph.ix, ph.iy, ph.iz,
-                                     ph.p);
-        const float zc = v.x * cm.fx + v.y * cm.fy + v.z * cm.fz;
-        if (!(zc > 0.f)) continue;
-        const float x = (v.x * cm.rx + v.y * cm.ry + v.z * cm.rz) / zc;
-        const float y = (v.x * cm.ux + v.y * cm.uy + v.z * cm.uz) / zc;
-        const float px = floorf((x / cm.tx + 1.f) * 0.5f * (float)cm.w);
-        const float py = floorf((y / cm.ty + 1.f) * 0.5f * (float)cm.h);
-        if (px < 0.f || py < 0.f || px >= (float)cm.w || py >= (float)cm.h) continue;
-        const int gp = cm.pix_off + (int)py * cm.w + (int)px;
-        const float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
-        if (!(r2 > 0.f)) continue;
-        float cr = 0.f;
-        if (OP > 0) {
-            cr = (float)A.cres[gp];
-            if (cr == 0.f) continue;
+    for (int c0 = 0; c0 < A.cams.n; c0 += kClassicGroup) {
+        const int gn = min(kClassicGroup, A.cams.n - c0);
+        int qn = 0;
+        for (int cl = 0; cl < gn; ++cl) {
+            int gp = 0;
+            float f0 = 0.f;
+            const bool vis = act && classic_pixel<(OP > 0)>(A, e, A.cams.c[c0 + cl], w, air, gp, f0);
+            cs.res[cl * 32 + lane] = vis ? f0 : 0.f;
+            if (OP == 0) cs.pix[cl * 32 + lane] = gp;
+            const unsigned vm = __ballot_sync(kFull, vis);
+            if (vis) cs.job[qn + __popc(vm & lanemask_lt())] = (uint8_t)(lane | ((unsigned)cl << 5));
+            qn += __popc(vm);
         }
-        const float mu = -(ph.d.x * v.x + ph.d.y * v.y + ph.d.z * v.z) * rsqrtf(r2);
-        float tau = 0.f;
-        unsigned long long ns = 0;
-        walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p,
-                       [&](const Walk& wk, float len) { tau += BetaFetch<DT>::get(A.beta, wk.lin) * len; }, ns);
-        const float val = w * (air ? rayleigh_phase(mu) : hg_phase(A.hg, mu)) * expf(-tau) / (r2 * A.omega[gp]);
-        if (OP == 0) {
-            atomicAdd(A.cimg + gp, (double)val);
-        } else {
-            acc += cr * val;
-            if (OP == 2) {
-                const float sw = -cr * val;
-                walk_to_camera(A.g, cm, ph.ix, ph.iy, ph.iz, ph.p,
-                               [&](const Walk& wk, float len) {
-                                   atomicAdd(gacc + pad_index(A.g, wk.ix, wk.iy, wk.iz), sw * len);
-                               }, ns);
+        if (lane == 0u) *cs.rays += (unsigned)qn;
+        __syncwarp();
+        for (int j0 = 0; j0 < qn; j0 += 32) {
+            const int j = j0 + (int)lane;
+            const unsigned jb = j < qn ? cs.job[j] : 0u;
+            const int el = (int)(jb & 31u), cl = (int)(jb >> 5);
+            const uint32_t v = __shfl_sync(kFull, vox, el);
+            const float3 p = make_float3(__shfl_sync(kFull, e.p.x, el), __shfl_sync(kFull, e.p.y, el),
+                                         __shfl_sync(kFull, e.p.z, el));
+            if (j < qn) {
+                const Cam& cm = A.cams.c[c0 + cl];
+                const int ix = (int)(v & 0x7FFu), iy = (int)((v >> 11) & 0x7FFu), iz = (int)(v >> 22);
+                const int r = cl * 32 + el;
+                unsigned ns = 0u;
+                const float f = cs.res[r] * expf(-shadow_tau<DT, false>(A, ix, iy, iz, p, cm, 0.f, ns));
+                if (OP == 0) {
+                    atomicAdd(A.cimg + cs.pix[r], (double)f);
+                } else {
+                    cs.res[r] = f;
+                    if (OP == 2) shadow_tau<DT, true>(A, ix, iy, iz, p, cm, -f, ns);
+                }
+                cs.seg[lane] += ns;
             }
         }
+        __syncwarp();
+        if (OP > 0)
+            for (int cl = 0; cl < gn; ++cl) acc += cs.res[cl * 32 + lane];
+        __syncwarp();
     }
     return acc;
 }
@@ -475,8 +578,8 @@ constexpr int kSlots = 64;
 constexpr int kStepsForward = 12;
 constexpr int kStepsPass1 = 8;
 constexpr int kStepsPass2 = 6;
-constexpr int kMinBlocksForward = 3;  // voxel estimator; the classic one keeps a 1-block budget
-constexpr int kMinBlocksClassic = 1;
+constexpr int kMinBlocksForward = 3;
+constexpr int kMinBlocksClassic = 3;
 constexpr int kMinBlocksPass1 = 3;
 constexpr int kMinBlocksPass2 = 3;
 
@@ -563,12 +666,6 @@ __device__ __forceinline__ uint4 unstash_block(const Stack<NW>& q, int slot) {
     const volatile uint32_t* b = q.w + slot;
     const int c = q.cap;
     return make_uint4(b[0], b[c], b[2 * c], b[3 * c]);
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
 }
 
 // One slice of the rolling fold (see kFoldSweep): the warp swaps the slice's FP32 bins to zero
@@ -687,7 +784,7 @@ template <int DT, int MODE, bool TWO, int TRIP>
 __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* smem) {
     constexpr bool PASS1 = MODE == kPass1 || MODE == kPass1C;
     constexpr bool PASS2 = MODE == kPass2 || MODE == kPass2W || MODE == kPass2C;
-    constexpr bool CLASSIC_ADJ = MODE == kPass1C || MODE == kPass2C;
+    constexpr bool CLASSIC = MODE == kFwdClassic || MODE == kPass1C || MODE == kPass2C;
     constexpr bool REPLAY = PASS1 || PASS2;
     constexpr int kStepsPerTrip = TRIP > 0 ? TRIP : (PASS2 ? kStepsPass2 : (PASS1 ? kStepsPass1 : kStepsForward));
     constexpr int NW = Rec<REPLAY>::NW;
@@ -707,6 +804,18 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
         t.u = reinterpret_cast<unsigned*>(tb + 11 * kTB) + threadIdx.x;
     }
     t.zero();
+    ClassicScratch cls{};  // the classic estimate's per-warp scratch, after the stacks and tallies
+    if constexpr (CLASSIC) {
+        uint32_t* cb = smem + (kTB / 32) * NW * kSlots + (REPLAY ? 0 : kTB * 15) + warp * kClassicWords;
+        cls.res = reinterpret_cast<float*>(cb);
+        cls.pix = reinterpret_cast<int*>(cb + kClassicGroup * 32);
+        cls.job = reinterpret_cast<uint8_t*>(cb + 2 * kClassicGroup * 32);
+        cls.seg = cb + 2 * kClassicGroup * 32 + kClassicGroup * 8;
+        cls.rays = cls.seg + 32;
+        cls.seg[lane] = 0u;
+        if (lane == 0u) *cls.rays = 0u;
+        __syncwarp();
+    }
 
     Photon ph;
     Flight w;
@@ -838,37 +947,36 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
                     ch_fill += (unsigned)n;
                 }
             }
-            if ((int)lane < n) {
-                get(stk, ev_n - 1 - (int)lane, A, e, enev, eacc);
-                e.s += 1u;
-                ++events;
-                const int k = lin_index(A.g, e.ix, e.iy, e.iz);
+            if constexpr (CLASSIC) {
+                // the classic estimate runs on the whole warp (its shadow rays are spread over all
+                // lanes), between the event's per-lane first half and its second
+                const bool act = (int)lane < n;
                 const int slot = ev_n - 1 - (int)lane;
-                uint4 xb = make_uint4(0u, 0u, 0u, 0u);  // two species: the event's Philox block
                 bool air = false;
-                if constexpr (TWO) {
-                    const uint4 x = draw_bits(A.key, e.id, e.s);
-                    air = particle_is_air(A, x, k);
-                    stash_block(stk, slot, x);
+                float wgt = 0.f;
+                if (act) {
+                    get(stk, slot, A, e, enev, eacc);
+                    e.s += 1u;
+                    ++events;
+                    const int k = lin_index(A.g, e.ix, e.iy, e.iz);
+                    if constexpr (TWO) {
+                        const uint4 x = draw_bits(A.key, e.id, e.s);
+                        air = particle_is_air(A, x, k);
+                        stash_block(stk, slot, x);
+                    }
+                    if (air) air_events.add();
+                    wgt = (air ? A.albedo_air : A.albedo) * e.I;
+                    if (!REPLAY) e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
                 }
-                if (air) air_events.add();
-                const float wgt = (air ? A.albedo_air : A.albedo) * e.I;
-                if (!REPLAY) {
-                    e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
-                    if (MODE == kFwdVoxel && A.ev_cap && ev_slot < A.ev_cap) store_event(A, ev_slot, e, wgt, air);
-                    if (MODE == 0) le_voxel(A, e, wgt, k, air);
-                    else le_classic<DT, 0>(A, e, wgt, nullptr, air);
+                const float we = le_classic<DT, REPLAY ? (PASS2 ? 2 : 1) : 0>(A, e, wgt, air, act, cls);
+                if (act) {
+                    uint4 xb = make_uint4(0u, 0u, 0u, 0u);
                     if constexpr (TWO) xb = unstash_block(stk, slot);
-                    term = after_event<TWO>(A, e, t, air, xb);
-                    if (term) finish_photon(A, e, term);
-                } else {
-                    float we;
-                    if constexpr (MODE == kPass2W) we = A.wseq[e.hash + e.s - 1u];
-                    else if constexpr (CLASSIC_ADJ) we = le_classic<DT, PASS2 ? 2 : 1>(A, e, wgt, A.gacc, air);
-                    else we = le_adjoint(A, e, wgt, k, air);
-                    if (PASS1) {
+                    if (!REPLAY) {
+                        term = after_event<TWO>(A, e, t, air, xb);
+                        if (term) finish_photon(A, e, term);
+                    } else if (PASS1) {
                         eacc += (double)we;
-                        if constexpr (TWO) xb = unstash_block(stk, slot);
                         term = after_event<TWO>(A, e, t, air, xb);
                         if (term) {
                             A.wbuf[e.idx - A.out_base] = eacc;
@@ -878,12 +986,60 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
                         const float S = (float)eacc;  // the score weight of the flight that ended here
                         if (TWO && S != 0.f) {  // two species: the collision voxel's term (see flight_step)
                             atomicAdd(A.gacc + pad_index(A.g, e.ix, e.iy, e.iz),
-                                      S * ((air ? 0.f : 1.f / __ldg(A.beta_aer + k)) - e.tau));
+                                      S * ((air ? 0.f : 1.f / __ldg(A.beta_aer + lin_index(A.g, e.ix, e.iy, e.iz))) -
+                                           e.tau));
                             ++scatters;
                         }
                         eacc -= (double)we;
-                        if constexpr (TWO) xb = unstash_block(stk, slot);
                         term = e.s == enev ? 1 : after_event<TWO>(A, e, t, air, xb);  // stop at pass 1's last event
+                    }
+                }
+            } else {  // the voxelised estimate (or the stored w_s), per lane
+                if ((int)lane < n) {
+                    get(stk, ev_n - 1 - (int)lane, A, e, enev, eacc);
+                    e.s += 1u;
+                    ++events;
+                    const int k = lin_index(A.g, e.ix, e.iy, e.iz);
+                    const int slot = ev_n - 1 - (int)lane;
+                    uint4 xb = make_uint4(0u, 0u, 0u, 0u);  // two species: the event's Philox block
+                    bool air = false;
+                    if constexpr (TWO) {
+                        const uint4 x = draw_bits(A.key, e.id, e.s);
+                        air = particle_is_air(A, x, k);
+                        stash_block(stk, slot, x);
+                    }
+                    if (air) air_events.add();
+                    const float wgt = (air ? A.albedo_air : A.albedo) * e.I;
+                    if (!REPLAY) {
+                        e.hash = (e.hash ^ (uint32_t)k) * kFnvPrime;
+                        if (MODE == kFwdVoxel && A.ev_cap && ev_slot < A.ev_cap) store_event(A, ev_slot, e, wgt, air);
+                        le_voxel(A, e, wgt, k, air);
+                        if constexpr (TWO) xb = unstash_block(stk, slot);
+                        term = after_event<TWO>(A, e, t, air, xb);
+                        if (term) finish_photon(A, e, term);
+                    } else {
+                        float we;
+                        if constexpr (MODE == kPass2W) we = A.wseq[e.hash + e.s - 1u];
+                        else we = le_adjoint(A, e, wgt, k, air);
+                        if (PASS1) {
+                            eacc += (double)we;
+                            if constexpr (TWO) xb = unstash_block(stk, slot);
+                            term = after_event<TWO>(A, e, t, air, xb);
+                            if (term) {
+                                A.wbuf[e.idx - A.out_base] = eacc;
+                                A.nevbuf[e.idx - A.out_base] = e.s;
+                            }
+                        } else {
+                            const float S = (float)eacc;  // the score weight of the flight that ended here
+                            if (TWO && S != 0.f) {  // two species: the collision voxel's term (see flight_step)
+                                atomicAdd(A.gacc + pad_index(A.g, e.ix, e.iy, e.iz),
+                                          S * ((air ? 0.f : 1.f / __ldg(A.beta_aer + k)) - e.tau));
+                                ++scatters;
+                            }
+                            eacc -= (double)we;
+                            if constexpr (TWO) xb = unstash_block(stk, slot);
+                            term = e.s == enev ? 1 : after_event<TWO>(A, e, t, air, xb);  // stop at pass 1's last event
+                        }
                     }
                 }
             }
@@ -893,6 +1049,13 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
             if (term == 0) put(stk, kSlots - 1 - (rd_n + __popc(gmask & lanemask_lt())), e, enev, eacc);
             rd_n += __popc(gmask);
             __syncwarp();
+        }
+    }
+    if constexpr (CLASSIC) {
+        const unsigned long long ss = warp_sumu(cls.seg[lane]);
+        if (lane == 0u) {
+            atomicAdd(A.stats + MST_ST_SHADOW_RAYS, (double)*cls.rays);
+            atomicAdd(A.stats + MST_ST_SHADOW_SEGMENTS, (double)ss);
         }
     }
     if constexpr (REPLAY) {
@@ -1191,10 +1354,15 @@ __global__ void k_fold_grad(float* __restrict__ gacc, double* __restrict__ g64, 
     }
 }
 
-template <bool REPLAY>
+// dynamic shared memory of a transport block: the warps' photon stacks, the forward's tallies
+// and the classic estimate's scratch
+template <int MODE>
 constexpr size_t smem_bytes() {
+    constexpr bool REPLAY = MODE >= 2;
+    constexpr bool CLASSIC = MODE == kFwdClassic || MODE == kPass1C || MODE == kPass2C;
     return (size_t)(kTB / 32) * Rec<REPLAY>::NW * kSlots * sizeof(uint32_t) +
-           (REPLAY ? 0 : (size_t)kTB * 15 * sizeof(uint32_t));
+           (REPLAY ? 0 : (size_t)kTB * 15 * sizeof(uint32_t)) +
+           (CLASSIC ? (size_t)(kTB / 32) * kClassicWords * sizeof(uint32_t) : 0);
 }
 
 template <typename K>
@@ -1214,10 +1382,10 @@ int occupancy(K kern, size_t smem) {
 template <int DT, int MODE, bool TWO, int TRIP = 0>
 cudaError_t launch_mode(const TransportArgs& a, int blocks, cudaStream_t st) {
     if constexpr (TRIP != 0) {  // a variant of the autotuner: the default's carveout (set by occupancy())
-        static const int once = occupancy(k_transport<DT, MODE, TWO, TRIP>, smem_bytes<(MODE >= 2)>());
+        static const int once = occupancy(k_transport<DT, MODE, TWO, TRIP>, smem_bytes<MODE>());
         (void)once;
     }
-    k_transport<DT, MODE, TWO, TRIP><<<blocks, kTB, smem_bytes<(MODE >= 2)>(), st>>>(a);
+    k_transport<DT, MODE, TWO, TRIP><<<blocks, kTB, smem_bytes<MODE>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1245,13 +1413,13 @@ cudaError_t launch_trip(const TransportArgs& a, int trip, int blocks, cudaStream
 template <int DT, bool TWO>
 int occupancy_mode(int mode) {
     switch (mode) {
-        case kFwdVoxel: return occupancy(k_transport<DT, kFwdVoxel, TWO>, smem_bytes<false>());
-        case kFwdClassic: return occupancy(k_transport<DT, kFwdClassic, TWO>, smem_bytes<false>());
-        case kPass2: return occupancy(k_transport<DT, kPass2, TWO>, smem_bytes<true>());
-        case kPass2W: return occupancy(k_transport<DT, kPass2W, TWO>, smem_bytes<true>());
-        case kPass1C: return occupancy(k_transport<DT, kPass1C, TWO>, smem_bytes<true>());
-        case kPass2C: return occupancy(k_transport<DT, kPass2C, TWO>, smem_bytes<true>());
-        default: return occupancy(k_transport<DT, kPass1, TWO>, smem_bytes<true>());
+        case kFwdVoxel: return occupancy(k_transport<DT, kFwdVoxel, TWO>, smem_bytes<kFwdVoxel>());
+        case kFwdClassic: return occupancy(k_transport<DT, kFwdClassic, TWO>, smem_bytes<kFwdClassic>());
+        case kPass2: return occupancy(k_transport<DT, kPass2, TWO>, smem_bytes<kPass2>());
+        case kPass2W: return occupancy(k_transport<DT, kPass2W, TWO>, smem_bytes<kPass2W>());
+        case kPass1C: return occupancy(k_transport<DT, kPass1C, TWO>, smem_bytes<kPass1C>());
+        case kPass2C: return occupancy(k_transport<DT, kPass2C, TWO>, smem_bytes<kPass2C>());
+        default: return occupancy(k_transport<DT, kPass1, TWO>, smem_bytes<kPass1>());
     }
 }
 
@@ -1285,13 +1453,13 @@ cudaError_t launch_species(const TransportArgs& a, int dtype, int mode, int trip
 // outside a stream capture.
 template <int MODE, int TRIP = 0>
 cudaError_t launch_batch_mode(const TransportArgs* table, int n, int blocks, cudaStream_t st) {
-    k_transport_batch<0, MODE, false, TRIP><<<blocks, kTB, smem_bytes<(MODE >= 2)>(), st>>>(table, n);
+    k_transport_batch<0, MODE, false, TRIP><<<blocks, kTB, smem_bytes<MODE>(), st>>>(table, n);
     return cudaGetLastError();
 }
 
 template <int MODE, int TRIP = 0>
 int batch_occupancy() {
-    return occupancy(k_transport_batch<0, MODE, false, TRIP>, smem_bytes<(MODE >= 2)>());
+    return occupancy(k_transport_batch<0, MODE, false, TRIP>, smem_bytes<MODE>());
 }
 
 }  // namespace

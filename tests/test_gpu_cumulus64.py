@@ -28,7 +28,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import dev, f32_scene, max_rel, need_gpu, record, rel_l2
+from tests.gpu_util import dev, f32_scene, last_point_drift, max_rel, need_gpu, record, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -42,26 +42,6 @@ def m():
     return need_gpu()
 
 
-def _paths(m, grid, sc, p, beta):
-    """Per photon: voxel sequence differs (bool) and the distance (m) between the GPU's and the
-    oracle's last event points."""
-    import torch
-    n = p.n_photons
-    h = torch.zeros(n, dtype=torch.int32, device="cuda")
-    pts = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
-    grid.set_debug(h, None)
-    grid.set_debug_points(pts)
-    grid.render(beta, m.make_params(p), images=False)
-    grid.set_debug(None, None)
-    grid.set_debug_points(None)
-    pg = pts.cpu().numpy()
-    vox = pg[:, 3].copy().view(np.uint32).astype(np.int64)
-    ijk = np.stack([vox & 2047, (vox >> 11) & 2047, vox >> 22], axis=1)
-    xg = ijk * np.array(sc.h) + pg[:, :3].astype(np.float64)
-    ro = oracle.render(sc, p, want_L=False, hashes=True, points=True)
-    return h.cpu().numpy().view(np.uint32) != ro["hash"], np.linalg.norm(xg - ro["point"], axis=1)
-
-
 @pytest.fixture(scope="module")
 def case(m):
     sc, p = synth.cfg_cumulus64(N_PHOTONS)
@@ -72,7 +52,7 @@ def case(m):
     # measured images: the oracle's render of the same field from another seed (the benchmark
     # evaluates the step at the true field against images of seed 4)
     meas = oracle.forward_images(sc, p.replace(seed=4))[0]
-    diverged, drift = _paths(m, grid, sc, p, beta)
+    diverged, drift = last_point_drift(m, grid, sc, p, beta)
     return dict(sc=sc, p=p, grid=grid, beta=beta, meas=meas, diverged=diverged, drift=drift,
                 skip_voxels=diverged.astype(np.uint8), skip_paths=(diverged | (drift > DRIFT)).astype(np.uint8))
 

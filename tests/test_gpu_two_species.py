@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import dev, f32_scene, gpu_hashes, max_rel, need_gpu, record, rel_l2
+from tests.gpu_util import dev, f32_scene, gpu_hashes, max_rel, need_gpu, pixel_edge_moves, record, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -105,23 +105,30 @@ def test_two_species_full_gradient(m, estimator, memory):
     grid.set_debug(None, None)
     ref = oracle.full_grad(sc, p, meas, mask, eta=0.05, skip=skip, classic=estimator == "classic")
     img, ri = out["images"].cpu().numpy(), ref["images"]
-    # Classic estimator: an event within FP32 rounding of a pixel edge may be counted in the
-    # neighbouring pixel; with air at the floor cameras one such event changes a faint pixel by
-    # 1e-6 of the brightest (a 1e-5 m camera shift moves the FP64 oracle's image the same way).
-    # Pixel assignment is not unique there, so per pixel only those above 1 % of the brightest
-    # are compared, and the whole image in relative L2.
+    # Classic estimator: an event within FP32 rounding of a pixel edge is counted in one pixel on
+    # the GPU and in its neighbour in the oracle, with its whole contribution (bisected: photon
+    # 10060 of this case, 5.9e-5 in pixel 606 on the GPU, 5.7e-5 in pixel 605 in the oracle, the
+    # two pixels' solid angles apart). With air at the floor cameras such an event may also change
+    # a faint pixel by 1e-6 of the brightest. So per pixel those above 1 % of the brightest are
+    # held to 2e-4 unless a move to a neighbour explains the difference (at most 4 such pixels),
+    # and the whole image to 1e-4 in relative L2.
     floor = (1e-2 if estimator == "classic" else 1e-3) * np.abs(ri).max()
     ei = max_rel(img, ri, floor)
     e2 = rel_l2(img, ri)
     el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
     eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    moved, unexplained = pixel_edge_moves(img, ri, sc, 2e-4, 1e-2) if estimator == "classic" else ([], [])
     record(f"two_species_full_gradient[{estimator},{memory}]", diverged_frac=skip.mean(), images_max_rel=ei,
-           images_rel_l2=e2, loss_rel=el, grad_rel_l2=eg)
+           images_rel_l2=e2, loss_rel=el, grad_rel_l2=eg, pixels_moved=len(moved))
     if memory == "stored":
         assert st["events_stored"] == st["events"] > 0
     else:
         assert st["events_stored"] == 0
-    assert ei < 2e-4 and e2 < 1e-4 and el < 1e-4 and eg < 1e-3, (ei, e2, el, eg)
+    if estimator == "classic":
+        assert not unexplained and len(moved) <= 4, (unexplained, list(moved))
+    else:
+        assert ei < 2e-4, ei
+    assert e2 < 1e-4 and el < 1e-4 and eg < 1e-3, (ei, e2, el, eg)
 
 
 def test_zero_air_field_is_one_species(m):
