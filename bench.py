@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--photons", type=float, default=1e8)
     ap.add_argument("--grad", default="full", choices=["full", "surrogate"])
     ap.add_argument("--grid-dtype", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--estimator", default="voxel", choices=["voxel", "classic"],
+                    help="local estimate of the --single call (the benchmark uses the voxelised one)")
     ap.add_argument("--ref-photons", type=float, default=2e4, help="photons per oracle step (bounded sample)")
     ap.add_argument("--recon-iters", type=int, default=50,
                     help="iterations of --study recon; --study haze runs 2x for L-BFGS")
@@ -474,12 +476,14 @@ def run_single(args):
     grid = m.Grid.from_scene(sc)
     beta = torch.from_numpy(sc.beta.astype(np.float32)).cuda()
     meas = torch.zeros(sc.n_pix, dtype=torch.float64, device="cuda")
-    out = grid.render_grad(beta, m.make_params(p, grad_mode=args.grad, grid_dtype=args.grid_dtype), meas,
-                           images=False)
+    out = grid.render_grad(beta, m.make_params(p, grad_mode=args.grad, grid_dtype=args.grid_dtype,
+                                               estimator=args.estimator), meas, images=False)
     torch.cuda.synchronize()
     st = grid.stats()
-    print(json.dumps({"single": True, "photons": int(args.photons), "loss": out["loss"].item(),
-                      "segments": st["segments"], "events": st["events"], "events_stored": st["events_stored"]}))
+    print(json.dumps({"single": True, "photons": int(args.photons), "estimator": args.estimator,
+                      "loss": out["loss"].item(), "segments": st["segments"], "events": st["events"],
+                      "events_stored": st["events_stored"], "shadow_rays": st["shadow_rays"],
+                      "shadow_segments": st["shadow_segments"]}))
     return 0
 
 

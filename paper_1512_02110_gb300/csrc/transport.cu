@@ -1036,9 +1036,9 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
                                           S * ((air ? 0.f : 1.f / __ldg(A.beta_aer + k)) - e.tau));
                                 ++scatters;
                             }
-                            eacc -= (double)we;
                             if constexpr (TWO) xb = unstash_block(stk, slot);
                             term = e.s == enev ? 1 : after_event<TWO>(A, e, t, air, xb);  // stop at pass 1's last event
+                            eacc -= (double)we;  // after the scattering step, which hides the w_s load
                         }
                     }
                 }
