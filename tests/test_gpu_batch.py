@@ -165,3 +165,54 @@ def test_persistent_and_branch_forms_agree(m):
             record(f"batch_persistent_vs_branches[{i},rep{rep}]", grad_rel_l2=eg, loss_rel=el)
             assert eg < 1e-5 and el < 1e-6, (i, rep, eg, el)
     batch.close()
+
+
+@pytest.mark.parametrize("form", ["persistent", "branches"])
+def test_uneven_batch_matches_the_oracle(m, form):
+    """Scenes of the batched workload's own generator, as uneven as it makes them: a 96^3 grid
+    with 12 cameras of 128^2, a 32^3 grid with 12 cameras of 64^2 and a 24^3 grid with 4 cameras
+    of 64^2 (blob and fractal fields, albedo, g and sun from the generator; 20 m voxels), 3e4
+    photons each, in one batch of each form, each scene against the FP64 oracle on the photons
+    that keep their path (voxel sequence and last event point within 1e-4 m): each camera's image
+    to 1e-4 in relative L2 and per pixel (above 1e-3 of the brightest) to 5e-4, the loss to 1e-4,
+    the gradient to 1e-3 relative L2. The per-pixel bound is the FP32 limit of the pixel-ray
+    walks in a grid this large: bisected, the worst pixel of the 96^3 scene (3.0e-4) takes all of
+    its value from one voxel ~2 km from its camera through short chords, and the rounding of the
+    sub-pixel ray directions (~6e-8 rad, ~1e-4 m there) moves those chords; its L agrees to 8e-6
+    and the GPU's T moves it by 3e-5. The measured images are zero (a synthetic input: the loss is
+    then the images' own energy), so that no oracle render of the large scene is needed beyond
+    the compared ones."""
+    import torch
+    import oracle
+    allsc = synth.batch_scenes(16)
+    cases = [(f32_scene(sc), p.replace(n_photons=30_000)) for sc, p in (allsc[5], allsc[1], allsc[0])]
+    grids = [m.Grid.from_scene(sc) for sc, _ in cases]
+    betas_np = [synth.smoothed(sc.beta, sc.shape, 0.2).astype(np.float32).astype(np.float64) for sc, _ in cases]
+    betas = [dev(b, np.float32) for b in betas_np]
+    meas = [np.zeros(sc.n_pix) for sc, _ in cases]
+    skips = []
+    for g, (sc, p), b, bd in zip(grids, cases, betas_np, betas):
+        div, drift = last_point_drift(m, g, sc.with_beta(b), p, bd)
+        skips.append((div | (drift > 1e-4)).astype(np.uint8))
+        g.set_debug(None, dev(skips[-1], np.uint8))
+    params = [m.make_params(p, grad_mode="full") for _, p in cases]
+    batch = m.Batch(grids)
+    batch.set_form(form)
+    out = batch.render_grad(betas, params, [dev(x, np.float64) for x in meas], images=True)
+    torch.cuda.synchronize()
+    assert batch.form() == form
+    for i, ((sc, p), b, s) in enumerate(zip(cases, betas_np, skips)):
+        ref = oracle.full_grad(sc.with_beta(b), p, meas[i], skip=s)
+        img = out["images"][i].cpu().numpy()
+        ei = float(np.max(np.abs(img - ref["images"]) / np.maximum(np.abs(ref["images"]),
+                                                                   1e-3 * np.abs(ref["images"]).max())))
+        npx = int(sc.cam_w[0]) * int(sc.cam_h[0])
+        ec = max(rel_l2(img[c * npx:(c + 1) * npx], ref["images"][c * npx:(c + 1) * npx]) for c in range(sc.n_cams))
+        el = abs(out["loss"][i].item() - ref["loss"]) / ref["loss"]
+        eg = rel_l2(out["grad"][i].cpu().numpy(), ref["grad"])
+        record(f"batch_uneven_oracle[{form},{sc.shape[0]}^3,{sc.n_cams}cams]", excluded_frac=s.mean(),
+               images_max_rel=ei, images_camera_rel_l2=ec, loss_rel=el, grad_rel_l2=eg)
+        assert ei < 5e-4 and ec < 1e-4 and el < 1e-4 and eg < 1e-3, (i, ei, ec, el, eg)
+    for g in grids:
+        g.set_debug(None, None)
+    batch.close()

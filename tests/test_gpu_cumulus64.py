@@ -14,10 +14,11 @@ thousand more than 5e-2 m. "Paths that do not diverge" are therefore those whose
 agrees (path checksum) and whose last event point lies within 1e-4 m of the oracle's (~14 % of
 the photons are left out); the others are excluded from both sides (skip mask).
 
-Compared on those photons: L per bin to 1e-4 relative (Sec. 3.2 Eq. Lcupdate) and images per
-pixel to 2e-4 (Sec. 3.3 Eq. Icpixel: the FP32 LOS walks alone put ~1e-4 into the images of this
-scene, where optical depths to the cameras reach ~30, with an L computed by the oracle), and
-the surrogate gradient (Sec. 5.1 Eq. divCost1) to 1e-3 relative L2 with its loss to 1e-4.
+Compared on those photons: L per bin to 1e-4 relative (Sec. 3.2 Eq. Lcupdate), each camera's
+image to 1e-4 in relative L2 and images per pixel to 2e-4 (Sec. 3.3 Eq. Icpixel: given the
+oracle's L and T, the FP32 pixel-ray walks alone put 9.7e-5 into a faint pixel of this scene,
+whose value comes through short chords of voxels far from its camera; the GPU's T adds 7e-6),
+and the surrogate gradient (Sec. 5.1 Eq. divCost1) to 1e-3 relative L2 with its loss to 1e-4.
 On every photon whose voxel sequence agrees: the loss (Eq. Cost) to 1e-4, the full gradient to
 1e-3 relative L2, L to 1e-4 relative L2 over all bins, and the event and escape counts exactly.
 Without any exclusion, over 8 seeds: every image within 3 Monte-Carlo standard errors overall,
@@ -68,11 +69,15 @@ def test_L_and_images_on_photons_that_keep_their_path(m, case):
     _, T = oracle.transmittance(sc)
     Ir = oracle.images(sc, Lr, T)
     eL = max_rel(out["L"].cpu().numpy(), Lr, 1e-3 * np.abs(Lr).max())
-    eI = max_rel(out["images"].cpu().numpy(), Ir, 1e-3 * np.abs(Ir).max())
+    img = out["images"].cpu().numpy()
+    eI = max_rel(img, Ir, 1e-3 * np.abs(Ir).max())
+    npx = int(sc.cam_w[0]) * int(sc.cam_h[0])
+    eC = max(rel_l2(img[c * npx:(c + 1) * npx], Ir[c * npx:(c + 1) * npx]) for c in range(sc.n_cams))
     d = case["drift"][~case["diverged"]]
     record("cumulus64_L_images", excluded_frac=skip.mean(), diverged_frac=case["diverged"].mean(), L_max_rel=eL,
-           images_max_rel=eI, drift_median=np.median(d), drift_p90=np.quantile(d, 0.9), drift_max=d.max())
-    assert eL < 1e-4 and eI < 2e-4, (eL, eI)
+           images_max_rel=eI, images_camera_rel_l2=eC, drift_median=np.median(d), drift_p90=np.quantile(d, 0.9),
+           drift_max=d.max())
+    assert eL < 1e-4 and eI < 2e-4 and eC < 1e-4, (eL, eI, eC)
 
 
 def test_loss_and_full_gradient(m, case):
