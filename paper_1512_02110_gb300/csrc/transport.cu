@@ -343,48 +343,98 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Optical depth t_{s->c} of Eq. fle: the segment from a point (voxel (ix, iy, iz) + offset p)
-// to camera cm's centre, walked on the padded grid like a free flight. The walk ends at the
-// camera or at the grid's boundary (the first halo voxel, extinction +inf: nothing outside the
-// grid attenuates). SCATTER: every voxel of the segment also receives sw * (its length) in the
-// gradient tile (padded like the grid), the shadow-ray term d f / d beta_m = -f * length.
-template <int DT, bool SCATTER>
-__device__ __forceinline__ float shadow_tau(const TransportArgs& A, int ix, int iy, int iz, float3 p, const Cam& cm,
-                                            float sw, unsigned& nseg) {
-    const Geo& g = A.g;
+// A shadow ray of Eq. fle: the segment from a point (voxel (ix, iy, iz) + offset p) to camera
+// cm's centre, walked on the padded grid like a free flight: per axis the distance to the next
+// face (t) and between faces (q), the padded index stride of a crossing, and the length left.
+struct Shadow {
+    float tx, ty, tz, qx, qy, qz, rem;
+    int dx, dy, dz, lin;
+};
+
+__device__ __forceinline__ Shadow shadow_init(const Geo& g, int ix, int iy, int iz, float3 p, const Cam& cm) {
+    Shadow r;
     const float3 v = local_delta(g, ix, iy, iz, p, cm.ix, cm.iy, cm.iz, make_float3(cm.lx, cm.ly, cm.lz));
-    float rem = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
-    const float inv = 1.f / rem;
-    float tx, ty, tz, qx, qy, qz;
-    int dx, dy, dz;
-    flight_axis(fminf(fmaxf(p.x, 0.f), g.hx), v.x * inv, g.hx, 1, tx, qx, dx);
-    flight_axis(fminf(fmaxf(p.y, 0.f), g.hy), v.y * inv, g.hy, g.p0, ty, qy, dy);
-    flight_axis(fminf(fmaxf(p.z, 0.f), g.hz), v.z * inv, g.hz, g.p01, tz, qz, dz);
-    int lin = pad_index(g, ix, iy, iz);
+    r.rem = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    const float inv = 1.f / r.rem;
+    flight_axis(fminf(fmaxf(p.x, 0.f), g.hx), v.x * inv, g.hx, 1, r.tx, r.qx, r.dx);
+    flight_axis(fminf(fmaxf(p.y, 0.f), g.hy), v.y * inv, g.hy, g.p0, r.ty, r.qy, r.dy);
+    flight_axis(fminf(fmaxf(p.z, 0.f), g.hz), v.z * inv, g.hz, g.p01, r.tz, r.qz, r.dz);
+    r.lin = pad_index(g, ix, iy, iz);
+    return r;
+}
+
+// Its optical depth t_{s->c}. The walk ends at the camera or at the grid's boundary (the first
+// halo voxel, extinction +inf: nothing outside the grid attenuates); nvox returns the voxels it
+// crossed. The extinction is loaded two voxels ahead: the walk starts, and every step stands, in
+// the grid, so the voxel after next lies at most in the second halo layer.
+template <int DT>
+__device__ __forceinline__ float shadow_tau(const TransportArgs& A, int ix, int iy, int iz, float3 p, const Cam& cm,
+                                            unsigned& nvox) {
+    Shadow r = shadow_init(A.g, ix, iy, iz, p, cm);
+    float tx = r.tx, ty = r.ty, tz = r.tz, rem = r.rem;
+    const float qx = r.qx, qy = r.qy, qz = r.qz;
+    const int dx = r.dx, dy = r.dy, dz = r.dz;
+    int lin = r.lin;
     float bn = BetaFetch<DT>::get(A.beta_pad, lin);
+    float bn2;
+    {
+        const float m = fminf(tx, fminf(ty, tz));
+        const bool px = tx <= m;
+        const bool py = !px && ty <= m;
+        bn2 = BetaFetch<DT>::get(A.beta_pad, lin + (px ? dx : (py ? dy : dz)));
+    }
     float tau = 0.f;
 #pragma unroll 1
     for (;;) {
         const float b = bn;
         if (isinf(b)) break;
-        ++nseg;
+        ++nvox;
         const float m = fminf(tx, fminf(ty, tz));
         const bool px = tx <= m;
         const bool py = !px && ty <= m;
         const int next = lin + (px ? dx : (py ? dy : dz));
+        const float ux = px ? qx : tx - m;
+        const float uy = py ? qy : ty - m;
+        const float uz = (px || py) ? tz - m : qz;
+        const float m2 = fminf(ux, fminf(uy, uz));
+        const bool px2 = ux <= m2;
+        const bool py2 = !px2 && uy <= m2;
         const bool last = !(rem > m);
-        if (!last) bn = BetaFetch<DT>::get(A.beta_pad, next);
-        const float seg = last ? rem : m;
-        tau += b * seg;
-        if (SCATTER) atomicAdd(A.gacc + lin, sw * seg);
+        float bn3 = 0.f;
+        if (!last) bn3 = BetaFetch<DT>::get(A.beta_pad, next + (px2 ? dx : (py2 ? dy : dz)));
+        tau += b * (last ? rem : m);
         if (last) break;
         rem -= m;
-        tx = px ? qx : tx - m;
-        ty = py ? qy : ty - m;
-        tz = (px || py) ? tz - m : qz;
+        tx = ux;
+        ty = uy;
+        tz = uz;
         lin = next;
+        bn = bn2;
+        bn2 = bn3;
     }
     return tau;
+}
+
+// The shadow-ray terms d f / d beta_m = -f * (length in voxel m): the same walk again, its nvox
+// voxels known from shadow_tau, so it loads no extinction; every voxel receives sw * length in
+// the gradient tile (padded like the grid).
+__device__ __forceinline__ void shadow_scatter(const TransportArgs& A, int ix, int iy, int iz, float3 p, const Cam& cm,
+                                               float sw, unsigned nvox) {
+    Shadow r = shadow_init(A.g, ix, iy, iz, p, cm);
+#pragma unroll 1
+    for (unsigned k = 0u; k < nvox; ++k) {
+        const float m = fminf(r.tx, fminf(r.ty, r.tz));
+        const bool px = r.tx <= m;
+        const bool py = !px && r.ty <= m;
+        const bool last = !(r.rem > m);
+        atomicAdd(A.gacc + r.lin, sw * (last ? r.rem : m));
+        if (last) break;
+        r.rem -= m;
+        r.tx = px ? r.qx : r.tx - m;
+        r.ty = py ? r.qy : r.ty - m;
+        r.tz = (px || py) ? r.tz - m : r.qz;
+        r.lin += px ? r.dx : (py ? r.dy : r.dz);
+    }
 }
 
 // Where an event lands in camera cm (Eq. fle): false when the camera does not see it (behind
@@ -469,15 +519,15 @@ __device__ __forceinline__ float le_classic(const TransportArgs& A, const Photon
                 const Cam& cm = A.cams.c[c0 + cl];
                 const int ix = (int)(v & 0x7FFu), iy = (int)((v >> 11) & 0x7FFu), iz = (int)(v >> 22);
                 const int r = cl * 32 + el;
-                unsigned ns = 0u;
-                const float f = cs.res[r] * expf(-shadow_tau<DT, false>(A, ix, iy, iz, p, cm, 0.f, ns));
+                unsigned nv = 0u;
+                const float f = cs.res[r] * expf(-shadow_tau<DT>(A, ix, iy, iz, p, cm, nv));
                 if (OP == 0) {
                     atomicAdd(A.cimg + cs.pix[r], (double)f);
                 } else {
                     cs.res[r] = f;
-                    if (OP == 2) shadow_tau<DT, true>(A, ix, iy, iz, p, cm, -f, ns);
+                    if (OP == 2) shadow_scatter(A, ix, iy, iz, p, cm, -f, nv);
                 }
-                cs.seg[lane] += ns;
+                cs.seg[lane] += OP == 2 ? 2u * nv : nv;
             }
         }
         __syncwarp();
