@@ -328,10 +328,12 @@ def run_ours(args):
     # Achieved = algorithmic operations per launch / average launch time, with per-unit counts:
     # 15 per transport segment, 27 per event and camera (local estimate: direction, cosine,
     # Henyey-Greenstein phase, two MUFU), 35 per event (scattering sample, roulette), 2 per replay
-    # score scatter; the stored-event adjoint 27 per event and camera, 36 B record + 4 B per camera
-    # + 8 B of W per event. The byte form against the measured HBM copy rate (4 B per segment, 8 B
-    # per camera per event) is kept beside it, with the stored events' bytes the forward also
-    # writes (40 B per event, 4 B per photon) reported apart.
+    # score scatter; replay pass 2 on the stored events 10 per segment (its flights know their last
+    # voxel: no extinction and no free-path test before it), 4 B of extinction per flight and the
+    # event's 16 B step; the stored-event adjoint 27 per event and camera, 44 B record + 4 B per
+    # camera + 8 B of W + the 16 B step per event. The byte form against the measured HBM copy
+    # rate (4 B per segment, 8 B per camera per event) is kept beside it, with the stored events'
+    # bytes the forward also writes (44 B per event, 4 B per photon) reported apart.
     C = sc.n_cams
     seg1, ev1 = st["segments"], st["events"]
     stored = st.get("events_stored", 0.0)
@@ -343,12 +345,14 @@ def run_ours(args):
     kernels = {
         "k_transport": (phase_acc["transport"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 8 * C * ev1),
         "k_replay_pass1": (phase_acc["replay"], 15 * seg1 + ops_ev * ev1, 4 * seg1 + 4 * C * ev1),
-        # with stored events pass 2 reads each w_s (4 B) instead of summing over the cameras
-        "k_replay_pass2": (phase_acc["replay2"], 15 * seg2 + (35 if stored > 0 else ops_ev) * ev2
-                           + 2 * st["replay_scatters"],
-                           4 * seg2 + (4 if stored > 0 else 4 * C) * ev2 + 8 * st["replay_scatters"]),
+        # with stored events pass 2 reads each event's step (w_s, its voxel, the free path left
+        # there) instead of summing over the cameras, and only the last voxel's extinction
+        "k_replay_pass2": ((phase_acc["replay2"], 10 * seg2 + 35 * ev2 + 2 * st["replay_scatters"],
+                            (4 + 16) * ev2 + 8 * st["replay_scatters"]) if stored > 0 else
+                           (phase_acc["replay2"], 15 * seg2 + ops_ev * ev2 + 2 * st["replay_scatters"],
+                            4 * seg2 + 4 * C * ev2 + 8 * st["replay_scatters"])),
         "k_event_adjoint": (phase_acc.get("event_adjoint", [0.0, 0]), 27 * C * stored,
-                            (36 + 4 * C + 8) * stored),
+                            (44 + 4 * C + 8 + 16) * stored),
     }
     kernels = {k: v for k, v in kernels.items() if v[0][1] > 0 and v[1] > 0}
     kern = max(kernels, key=lambda k: kernels[k][0][0])
@@ -372,7 +376,7 @@ def run_ours(args):
                         "peak_source": peak_kind,
                         "bytes": "algorithmic: 4 B of extinction per voxel segment, 8 B per camera per event "
                                  "(FP32 read-modify-write of the L tile)",
-                        "stored_event_bytes_per_launch": (40 * stored + 4 * st["traced"]) / calls_per_step
+                        "stored_event_bytes_per_launch": (44 * stored + 4 * st["traced"]) / calls_per_step
                         if kern == "k_transport" and stored > 0 else 0.0},
                 "phase_ms_per_step": {k: v[0] / args.steps for k, v in phase_acc.items()}}
     launches = int(sum(v[1] for v in phase_acc.values()))

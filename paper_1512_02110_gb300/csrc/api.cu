@@ -382,7 +382,8 @@ bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
     g->wseq = nullptr;
     g->ch_next = nullptr;
     g->ev_cap = 0;
-    if (cudaMalloc(&g->evrec, want * kEventWords * 4) != cudaSuccess || cudaMalloc(&g->wseq, want * 4) != cudaSuccess ||
+    if (cudaMalloc(&g->evrec, want * kEventWords * 4) != cudaSuccess ||
+        cudaMalloc(&g->wseq, want * sizeof(EventStep)) != cudaSuccess ||
         cudaMalloc(&g->ch_next, sizeof(uint32_t) * (want / kEventChunk + 1)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(g->evrec);

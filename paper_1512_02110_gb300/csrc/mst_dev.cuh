@@ -189,11 +189,12 @@ __device__ __forceinline__ void unpad(const Geo& g, int q, int& ix, int& iy, int
     iz = a - kHalo;
 }
 
-// linear voxel index of an interior padded index
-__device__ __forceinline__ int unpad_lin(const Geo& g, int q) {
+// linear voxel index k of a padded index; false for a halo voxel
+__device__ __forceinline__ bool interior_lin(const Geo& g, int q, int& k) {
     int ix, iy, iz;
     unpad(g, q, ix, iy, iz);
-    return lin_index(g, ix, iy, iz);
+    k = lin_index(g, ix, iy, iz);
+    return (unsigned)ix < (unsigned)g.nx && (unsigned)iy < (unsigned)g.ny && (unsigned)iz < (unsigned)g.nz;
 }
 
 template <int DT>

@@ -23,13 +23,24 @@ constexpr uint64_t kReplayChunk = 1ull << 24;    // photons per replay pass-1 / 
 // for calls of at most kRecordMaxPhotons photons; W then comes from the stored events and the
 // replay is one pass-2 launch over the call's photons.
 constexpr uint64_t kRecordMaxPhotons = 1ull << 27;
-constexpr int kEventWords = 10;  // packed voxel, offset (3), incoming direction (3), albedo * weight, photon, event number
-constexpr int kEventBytes = kEventWords * 4 + 4;  // the record and its w_s
+// packed voxel, offset (3), incoming direction (3), albedo * weight, photon, event number, and the
+// free path left when the flight entered the event's voxel
+constexpr int kEventWords = 11;
+// What replay pass 2 needs of each stored event, in the photon's slot (event order): w_s, the
+// event's packed voxel and the free path left on entering it. Pass 2 then walks each flight to
+// that voxel without loading the extinction of the voxels before it.
+struct EventStep {
+    float w;
+    uint32_t vox;
+    float tau_in;
+    uint32_t pad;
+};
+constexpr int kEventBytes = kEventWords * 4 + (int)sizeof(EventStep);  // the record and its slot
 constexpr unsigned kEventChunk = 256;  // record slots a warp of the forward reserves at a time
 constexpr int kTransportWarps = 8;     // warps per transport block (256 threads)
 constexpr uint32_t kEndChunk = 0xFFFFFFFFu;  // end of a warp's chunk list
 constexpr int kMaxWarpsPerSm = 64;     // warp_head entries per SM (the forward runs 24)
-constexpr uint64_t kDefaultRecordBytes = 24ull << 30;
+constexpr uint64_t kDefaultRecordBytes = 32ull << 30;
 constexpr uint64_t kFoldSweep = 1ull << 21;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
 constexpr int kMaxTickets = (int)(2 * (kMaxPhotons / kReplayChunk));
@@ -71,7 +82,7 @@ struct TransportArgs {
     uint32_t* evrec;           // stored events [kEventWords][ev_cap] (forward), or NULL
     unsigned long long ev_cap;     // capacity of evrec in events (0: no events stored)
     unsigned long long* ev_count;  // events offered for storage; > ev_cap: they did not fit
-    float* wseq;               // [ev_cap] w_s of the stored events, photon after photon (event order)
+    EventStep* wseq;           // [ev_cap] the stored events' steps, photon after photon (event order)
     uint32_t* ch_next;         // [ev_cap / kEventChunk] next chunk of the same forward warp (kEndChunk: none)
     uint32_t* warp_head;       // [warps of the forward launch] each warp's first chunk (kEndChunk: none)
     uint32_t n_warps;          // warps of the forward launch that stored the events
@@ -119,7 +130,7 @@ struct mst_grid {
     uint32_t* evoff = nullptr;          // [replay_cap] first w_s slot of each photon (stored events)
     uint64_t replay_cap = 0;            // photons the four buffers above hold
     uint32_t* evrec = nullptr;          // [kEventWords][ev_cap] stored events (full gradient)
-    float* wseq = nullptr;              // [ev_cap] their w_s, grouped by photon
+    mst::EventStep* wseq = nullptr;     // [ev_cap] their steps (w_s, voxel, free path), grouped by photon
     unsigned long long ev_cap = 0;
     unsigned long long* ev_count = nullptr;  // device counter of the last recording forward
     unsigned long long* ev_seen = nullptr;   // pinned host copy of it, read at the next call

@@ -149,6 +149,7 @@ struct Flight {
     int lin;
     float bn;  // extinction of voxel lin, loaded ahead
     int left;  // voxel steps left before a flight is abandoned (only a non-finite direction gets there)
+    int tgt;   // replay pass 2 on the stored events: padded index of the voxel the flight ends in
 };
 
 // 1 / |d| by the hardware reciprocal (__fdividef, within 2 ulp)
@@ -182,6 +183,22 @@ __device__ __forceinline__ void flight_init(Flight& f, const TransportArgs& A, c
     f.left = g.max_steps;
 }
 
+// Replay pass 2 on the stored events: the same flight, told by the step the stored-event adjoint
+// wrote for the event that ends it (slot evoff + events so far, ph.hash holding evoff) where it
+// ends and how much free path it has left on entering that voxel (tau). Its voxels before that
+// one need no extinction: the flight crosses them.
+__device__ __forceinline__ void flight_init_stored(Flight& f, const TransportArgs& A, const Photon& ph, float& tau) {
+    const Geo& g = A.g;
+    const uint4 st = __ldg(reinterpret_cast<const uint4*>(A.wseq) + (ph.hash + ph.s));
+    flight_axis(fminf(fmaxf(ph.p.x, 0.f), g.hx), ph.d.x, g.hx, 1, f.tx, f.qx, f.dx);
+    flight_axis(fminf(fmaxf(ph.p.y, 0.f), g.hy), ph.d.y, g.hy, g.p0, f.ty, f.qy, f.dy);
+    flight_axis(fminf(fmaxf(ph.p.z, 0.f), g.hz), ph.d.z, g.hz, g.p01, f.tz, f.qz, f.dz);
+    f.lin = pad_index(g, ph.ix, ph.iy, ph.iz);
+    f.left = g.max_steps;
+    f.tgt = pad_index(g, (int)(st.y & 0x7FFu), (int)((st.y >> 11) & 0x7FFu), (int)(st.y >> 22));
+    tau = __uint_as_float(st.z);
+}
+
 // One voxel of a free flight (Eq. MCextinct): the free path tau runs out in this voxel when
 // tau <= beta * (distance to the next face). Returns true then, or when the voxel is the halo
 // (beta = +inf; the caller tells the two apart by b), with b and the face distance m of the voxel;
@@ -210,6 +227,27 @@ __device__ __forceinline__ bool flight_step(const TransportArgs& A, Flight& f, f
     f.ty = py ? f.qy : f.ty - m;
     f.tz = (px || py) ? f.tz - m : f.qz;
     f.lin = next;
+    return false;
+}
+
+// One voxel of a replay pass-2 flight whose end is known (flight_init_stored): true in the voxel
+// the flight ends in (the caller loads its extinction there), else the voxel receives -S *
+// length in the gradient tile and the flight crosses into the next one, by the arithmetic of
+// flight_step, so that it visits the same voxels.
+__device__ __forceinline__ bool flight_step_stored(const TransportArgs& A, Flight& f, float S, unsigned& nsc) {
+    // (a voxel index past the padded grid would mean the walk missed its end: it stops there)
+    if (f.lin == f.tgt || (unsigned)f.lin >= (unsigned)A.g.npad) return true;
+    const float m = fminf(f.tx, fminf(f.ty, f.tz));
+    const bool px = f.tx <= m;
+    const bool py = !px && f.ty <= m;
+    if (S != 0.f && m > 0.f) {
+        atomicAdd(A.gacc + f.lin, -S * m);
+        ++nsc;
+    }
+    f.tx = px ? f.qx : f.tx - m;
+    f.ty = py ? f.qy : f.ty - m;
+    f.tz = (px || py) ? f.tz - m : f.qz;
+    f.lin += px ? f.dx : (py ? f.dy : f.dz);
     return false;
 }
 
@@ -585,7 +623,9 @@ __device__ __forceinline__ void finish_photon(const TransportArgs& A, const Phot
 }
 
 // One stored event (forward, full gradient): what w_s = sum_c a_c(k) albedo I_s P_c(s) needs.
-// Word 9 holds the event number, with the particle (1: air) in bit 31.
+// Word 9 holds the event number, with the particle (1: air) in bit 31; word 10 the free path left
+// when the flight entered the event's voxel (e.tau, set at the collision), with which replay
+// pass 2 ends the flight there.
 __device__ __forceinline__ void store_event(const TransportArgs& A, unsigned long long i, const Photon& e, float wgt,
                                             bool air) {
     const unsigned long long C = A.ev_cap;
@@ -600,6 +640,7 @@ __device__ __forceinline__ void store_event(const TransportArgs& A, unsigned lon
     r[7 * C] = __float_as_uint(wgt);
     r[8 * C] = e.idx - A.out_base;
     r[9 * C] = e.s | (air ? 0x80000000u : 0u);
+    r[10 * C] = __float_as_uint(e.tau);  // the free path left on entering the event's voxel
 }
 
 // ------------------------------------------------------------------------------------------
@@ -736,8 +777,9 @@ __device__ __forceinline__ void fold_slice(const TransportArgs& A, uint32_t batc
                     if (v != 0.f) atomicAdd(A.L64 + (size_t)c * A.g.nvox + k, (double)v);
                 }
             } else {  // gradient tile [nvox] -> g64 [nvox]
-                const float v = atomicExch(A.gacc + i, 0.f);  // padded tile: the halo stays 0
-                if (v != 0.f) atomicAdd(A.g64 + unpad_lin(A.g, (int)i), (double)v);
+                const float v = atomicExch(A.gacc + i, 0.f);  // padded tile
+                int k;
+                if (v != 0.f && interior_lin(A.g, (int)i, k)) atomicAdd(A.g64 + k, (double)v);
             }
         }
     }
@@ -891,8 +933,12 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
             const int take = min(__popc(empty), rd_n);
             if (!fly && rank < take) {
                 get(stk, kSlots - rd_n + rank, A, ph, nev, acc);
-                flight_init<DT>(w, A, ph);
-                tau = ph.tau;
+                if constexpr (MODE == kPass2W) {
+                    flight_init_stored(w, A, ph, tau);
+                } else {
+                    flight_init<DT>(w, A, ph);
+                    tau = ph.tau;
+                }
                 fly = true;
             }
             rd_n -= take;
@@ -914,9 +960,13 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
                 return false;
             }
             launch_photon(A, ph, pid);
-            if (MODE == kPass2W) ph.hash = A.evoff[pid];
-            flight_init<DT>(w, A, ph);
-            tau = ph.tau;
+            if constexpr (MODE == kPass2W) {
+                ph.hash = A.evoff[pid];
+                flight_init_stored(w, A, ph, tau);
+            } else {
+                flight_init<DT>(w, A, ph);
+                tau = ph.tau;
+            }
             t.add_launch(A.I0);
             return true;
         }, [&](uint32_t t0) { fold_slice<MODE>(A, t0 / (uint32_t)kTicketBatch, lane); });
@@ -930,17 +980,38 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
             int nstep = 0;
             bool stop = false;
             float b = 0.f, m = 0.f;
+            if constexpr (MODE == kPass2W) {  // the flight's last voxel is known: no extinction before it
 #pragma unroll 1
-            while (nstep < kStepsPerTrip) {
-                ++nstep;
-                if (flight_step<DT, PASS2>(A, w, tau, b, m, S, scatters)) {
-                    stop = true;
-                    break;
+                while (nstep < kStepsPerTrip) {
+                    ++nstep;
+                    if (flight_step_stored(A, w, S, scatters)) {
+                        stop = true;
+                        break;
+                    }
                 }
-            }
-            if (stop) {
-                r = flight_end<TWO>(A, ph, w, tau, b, S, scatters);
-                if (r >= 0) --nstep;  // the halo voxel is no segment of the path
+                if (stop) {
+                    r = (unsigned)w.lin < (unsigned)A.g.npad
+                            ? flight_end<TWO>(A, ph, w, tau, BetaFetch<DT>::get(A.beta_pad, w.lin), S, scatters)
+                            : kWalkOverflow;
+                    // a stored flight ends in its event; any other end is a replay that left the
+                    // forward's path, counted as lost (0 in valid use; the fold drops what such a
+                    // walk added to the halo)
+                    if (r != kCollided) atomicAdd(A.stats + MST_ST_LOST, 1.0);
+                }
+            } else {
+#pragma unroll 1
+                while (nstep < kStepsPerTrip) {
+                    ++nstep;
+                    if (flight_step<DT, PASS2>(A, w, tau, b, m, S, scatters)) {
+                        stop = true;
+                        break;
+                    }
+                }
+                if (stop) {
+                    r = flight_end<TWO>(A, ph, w, tau, b, S, scatters);
+                    if (r >= 0) --nstep;  // the halo voxel is no segment of the path
+                    if (MODE == kFwdVoxel && r == kCollided) ph.tau = tau;  // kept for the stored event
+                }
             }
             segments += nstep;
             // a flight longer than any straight walk through the grid is abandoned
@@ -1069,7 +1140,7 @@ __device__ __forceinline__ void transport_run(const TransportArgs& A, uint32_t* 
                         if (term) finish_photon(A, e, term);
                     } else {
                         float we;
-                        if constexpr (MODE == kPass2W) we = A.wseq[e.hash + e.s - 1u];
+                        if constexpr (MODE == kPass2W) we = A.wseq[e.hash + e.s - 1u].w;
                         else we = le_adjoint(A, e, wgt, k, air);
                         if (PASS1) {
                             eacc += (double)we;
@@ -1187,7 +1258,8 @@ __device__ __forceinline__ void event_adjoint_run(const TransportArgs& A) {
                 const float w = le_adjoint(A, e, __uint_as_float(r[7 * C]), lin_index(A.g, e.ix, e.iy, e.iz),
                                            TWO && (sw >> 31) != 0u);
                 const uint32_t s = sw & 0x7FFFFFFFu;
-                A.wseq[A.evoff[j] + s - 1u] = w;  // event s of photon j: slot evoff[j] + s - 1
+                // event s of photon j: slot evoff[j] + s - 1 (one 16-byte store)
+                reinterpret_cast<uint4*>(A.wseq)[A.evoff[j] + s - 1u] = make_uint4(__float_as_uint(w), v, r[10 * C], 0u);
                 if (w != 0.f) {
                     atomicAdd(A.wbuf + j, (double)w);
                     // S_j = sum_{s >= j} w_s vanishes past the photon's last event with w_s != 0,
@@ -1393,12 +1465,14 @@ __global__ void k_fold_L(float* __restrict__ Lacc, double* __restrict__ L64, int
     }
 }
 
-// the gradient tile is padded like the grid the flights walk; its halo is never written
+// the gradient tile is padded like the grid the flights walk; its halo receives nothing in valid
+// use, and what a replay that left the forward's path added there is dropped
 __global__ void k_fold_grad(float* __restrict__ gacc, double* __restrict__ g64, const Geo g) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.npad; q += gridDim.x * blockDim.x) {
         const float v = gacc[q];
         if (v != 0.f) {
-            g64[unpad_lin(g, q)] += (double)v;
+            int k;
+            if (interior_lin(g, q, k)) g64[k] += (double)v;
             gacc[q] = 0.f;
         }
     }

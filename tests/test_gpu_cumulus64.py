@@ -96,6 +96,7 @@ def test_loss_and_full_gradient(m, case):
     # the benchmark's path: W from the events the forward stored, then replay pass 2 alone
     assert st["events_stored"] == st["events"] > 0
     assert st["traced"] == p.n_photons - int(skip.sum())
+    assert st["lost"] == 0  # every flight of replay pass 2 ended in its stored event's voxel
     rs = ref["stats"]
     for k in ["events", "escaped_n", "capped"]:
         assert st[k] == rs[k], (k, st[k], rs[k])
