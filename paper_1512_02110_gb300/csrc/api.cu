@@ -330,7 +330,7 @@ int ensure_replay(mst_grid* g, uint64_t n) {
 }
 
 // Whether the forward of a full-gradient call of n photons stores its events, with the buffer
-// sized for them: room for 6 events per photon at first, then 1.25 x the events the last
+// sized for them: room for 4 events per photon at first, then 1.25 x the events the last
 // storing call offered (read without a wait once its copy has landed), within the budget. Never
 // fails the call: too many photons, no budget, a failed allocation or a call inside a stream
 // capture (no allocation there) all mean W by replay.
@@ -359,11 +359,11 @@ bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
     // the forward reserves slots in per-warp chunks: one chunk per resident warp of headroom
     const uint64_t tails = (uint64_t)g->sm_count * transport_blocks_per_sm(dtype, 0, g->air != nullptr) *
                            kTransportWarps * kEventChunk;
-    // need: the last count this handle's forward reserved (6 per photon before any), plus the
+    // need: the last count this handle's forward reserved (4 per photon before any), plus the
     // tails; a buffer below it is replaced by one 1.25 x the need, so that counts that drift by a
     // few chunks from call to call do not reallocate it every time
-    const uint64_t need = std::min<uint64_t>(std::max<uint64_t>((g->ev_last ? g->ev_last : 6 * n) + tails, 1024), max_ev);
-    const uint64_t want = std::min<uint64_t>(need + need / 4, max_ev);
+    const uint64_t need = std::min<uint64_t>(std::max<uint64_t>((g->ev_last ? g->ev_last : 4 * n) + tails, 1024), max_ev);
+    uint64_t want = std::min<uint64_t>(need + need / 4, max_ev);
     if (!g->warp_head) {  // the forward's warps: at most kMaxWarpsPerSm per SM
         if (cudaMalloc(&g->warp_head, sizeof(uint32_t) * (size_t)g->sm_count * kMaxWarpsPerSm) != cudaSuccess) {
             cudaGetLastError();
@@ -382,6 +382,17 @@ bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
     g->wseq = nullptr;
     g->ch_next = nullptr;
     g->ev_cap = 0;
+    // leave a sixteenth of the device (at least 4 GiB) free for the call's other buffers, other
+    // handles (a batch sizes all of its handles before it runs) and the caller: a buffer that
+    // would not leave it is made smaller, and one below the need is not made (W by replay)
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const uint64_t reserve = std::max<uint64_t>(total_b / 16, 4ull << 30);
+    want = std::min<uint64_t>(want, free_b > reserve ? (free_b - reserve) / rec_bytes : 0);
+    if (want < need) return false;
     if (cudaMalloc(&g->evrec, want * kEventWords * 4) != cudaSuccess ||
         cudaMalloc(&g->wseq, want * sizeof(EventStep)) != cudaSuccess ||
         cudaMalloc(&g->ch_next, sizeof(uint32_t) * (want / kEventChunk + 1)) != cudaSuccess) {

@@ -40,7 +40,7 @@ constexpr unsigned kEventChunk = 256;  // record slots a warp of the forward res
 constexpr int kTransportWarps = 8;     // warps per transport block (256 threads)
 constexpr uint32_t kEndChunk = 0xFFFFFFFFu;  // end of a warp's chunk list
 constexpr int kMaxWarpsPerSm = 64;     // warp_head entries per SM (the forward runs 24)
-constexpr uint64_t kDefaultRecordBytes = 32ull << 30;
+constexpr uint64_t kDefaultRecordBytes = 24ull << 30;
 constexpr uint64_t kFoldSweep = 1ull << 21;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
 constexpr int kMaxTickets = (int)(2 * (kMaxPhotons / kReplayChunk));
