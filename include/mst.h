@@ -315,7 +315,7 @@ int mst_autotune(mst_grid *g, const float *beta_dev, const mst_params *p, uint64
  * (60 B per scattering event: voxel, position, incoming direction, weight, photon index, event
  * number, the free path left on entering the voxel, and the event's step for replay pass 2:
  * w_s, voxel, free path), for
- * calls of at most 2^27 photons. Default 24 GiB; 0 stores nothing (W by replay). The buffer
+ * calls of at most 2^27 photons. Default 32 GiB; 0 stores nothing (W by replay). The buffer
  * is allocated at the first full-gradient call that needs it and grown, within the budget,
  * when a call stored more events than it held, and never so large that less than a sixteenth of
  * the device's memory (at least 4 GiB) stays free; a call whose events do not fit, or whose

@@ -331,7 +331,8 @@ int ensure_replay(mst_grid* g, uint64_t n) {
 
 // Whether the forward of a full-gradient call of n photons stores its events, with the buffer
 // sized for them: room for 4 events per photon at first, then 1.25 x the events the last
-// storing call offered (read without a wait once its copy has landed), within the budget. Never
+// storing call offered (the handle's first count waited for, later ones read without a wait once
+// their copy has landed), within the budget. Never
 // fails the call: too many photons, no budget, a failed allocation or a call inside a stream
 // capture (no allocation there) all mean W by replay.
 bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
@@ -347,9 +348,14 @@ bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
     }
     unsigned long long seen = 0;
     if (g->ev_seen_pending) {
-        if (cudaEventQuery(g->ev_seen_ready) == cudaSuccess) {
+        // the first count of the handle is waited for (once: the first call's buffer came from a
+        // guess); later ones are taken when they have arrived
+        const cudaError_t q =
+            g->ev_counted ? cudaEventQuery(g->ev_seen_ready) : cudaEventSynchronize(g->ev_seen_ready);
+        if (q == cudaSuccess) {
             seen = *g->ev_seen;
             g->ev_seen_pending = false;
+            g->ev_counted = true;
             g->ev_last = seen;
         } else {
             cudaGetLastError();  // not ready yet: size from the last count that arrived
@@ -1167,6 +1173,7 @@ int mst_autotune(mst_grid* g, const float* beta, const mst_params* p, uint64_t n
     const bool prof0 = g->prof;
     // the sample's event counts must not size the buffers of the handle's real calls
     const unsigned long long ev_last0 = g->ev_last;
+    const bool ev_counted0 = g->ev_counted;
     const int saved_trip[7] = {g->wf_trip[0], 0, g->wf_trip[2], 0, g->wf_trip[4], 0, 0};
     const int saved_blocks[7] = {g->wf_blocks[0], 0, g->wf_blocks[2], 0, g->wf_blocks[4], 0, 0};
     const int occ_f = transport_blocks_per_sm(q.grid_dtype, 0, g->air != nullptr);
@@ -1209,6 +1216,7 @@ int mst_autotune(mst_grid* g, const float* beta, const mst_params* p, uint64_t n
     g->prof = prof0;
     prof_reset(g);
     g->ev_last = ev_last0;
+    g->ev_counted = ev_counted0;
     g->ev_seen_pending = false;  // a count pending from before was overwritten by the sample's
     cudaFree(meas);
     cudaFree(grad);
@@ -1573,7 +1581,11 @@ int mst_batch_autotune(mst_batch* b, const float* const* betas, const mst_params
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
     std::vector<unsigned long long> ev_last0(n);
-    for (int i = 0; i < n; ++i) ev_last0[i] = b->grids[i]->ev_last;
+    std::vector<char> ev_counted0(n);
+    for (int i = 0; i < n; ++i) {
+        ev_last0[i] = b->grids[i]->ev_last;
+        ev_counted0[i] = b->grids[i]->ev_counted;
+    }
     const int saved[4] = {b->trip_fwd, b->blocks_fwd, b->trip_p2, b->blocks_p2};
     int rc = ok ? MST_OK : MST_ERR_OOM;
     if (!ok) b->err = "autotune buffers: out of device memory";
@@ -1622,6 +1634,7 @@ int mst_batch_autotune(mst_batch* b, const float* const* betas, const mst_params
         }
     for (int i = 0; i < n; ++i) {  // the sample's event counts must not size the real calls' buffers
         b->grids[i]->ev_last = ev_last0[i];
+        b->grids[i]->ev_counted = ev_counted0[i] != 0;
         b->grids[i]->ev_seen_pending = false;
     }
     if (b->launched) {
@@ -1699,6 +1712,7 @@ int mst_batch_render_grad(mst_batch* b, const float* const* betas, const mst_par
             mst_grid* g = b->grids[i];
             if (g->batch_stored && *g->ev_seen > g->ev_cap) {
                 g->ev_last = *g->ev_seen;
+                g->ev_counted = true;
                 g->batch_stored = ensure_records(g, params[i].n_photons, params[i].grid_dtype);
                 g->err.clear();
             }

@@ -40,7 +40,7 @@ constexpr unsigned kEventChunk = 256;  // record slots a warp of the forward res
 constexpr int kTransportWarps = 8;     // warps per transport block (256 threads)
 constexpr uint32_t kEndChunk = 0xFFFFFFFFu;  // end of a warp's chunk list
 constexpr int kMaxWarpsPerSm = 64;     // warp_head entries per SM (the forward runs 24)
-constexpr uint64_t kDefaultRecordBytes = 24ull << 30;
+constexpr uint64_t kDefaultRecordBytes = 32ull << 30;
 constexpr uint64_t kFoldSweep = 1ull << 21;
 constexpr int kTicketBatch = 64;  // photon ids a warp takes from the global ticket at a time
 constexpr int kMaxTickets = (int)(2 * (kMaxPhotons / kReplayChunk));
@@ -136,6 +136,7 @@ struct mst_grid {
     unsigned long long* ev_seen = nullptr;   // pinned host copy of it, read at the next call
     cudaEvent_t ev_seen_ready = nullptr;     // recorded after that copy
     bool ev_seen_pending = false;
+    bool ev_counted = false;                 // a count of this handle's stored events has arrived
     unsigned long long ev_last = 0;          // events offered by the last storing call whose count arrived
     bool capturing = false;                  // inside a stream capture: no allocation, no event query
     bool batch_stored = false;               // the batch allocated this handle's event buffers before capture
