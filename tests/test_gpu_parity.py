@@ -376,7 +376,8 @@ def test_full_gradient_classic_estimator(m, torch):
 def test_full_gradient_stored_events_match_replay(m, torch, budget):
     """W from the forward's stored events (the default) against W from replay pass 1: same
     loss and gradient up to the order of floating-point additions. "overflow": a budget of
-    2048 events, far fewer than the call makes, so the device falls back to pass 1."""
+    2048 events (60 B each with its step), far fewer than the call makes, so the device falls
+    back to pass 1."""
     sc, p, meas, mask = _grad_case()
     beta = dev(sc.beta, np.float32)
     args = (beta, m.make_params(p, grad_mode="full", reg_eta=0.05), dev(meas, np.float64), dev(mask, np.uint8))
@@ -384,7 +385,7 @@ def test_full_gradient_stored_events_match_replay(m, torch, budget):
     a = g_st.render_grad(*args)
     st_a = g_st.stats()
     g_rp = m.Grid.from_scene(sc)
-    g_rp.set_replay_memory(0 if budget == "replay" else 2048 * 44)
+    g_rp.set_replay_memory(0 if budget == "replay" else 2048 * 60)
     b = g_rp.render_grad(*args)
     st_b = g_rp.stats()
     assert st_a["events_stored"] == st_a["events"] > 2048
@@ -396,6 +397,31 @@ def test_full_gradient_stored_events_match_replay(m, torch, budget):
     assert el < 1e-6 and eg < 1e-5, (el, eg)  # the forward L sums in FP32 atomics in any order
     # pass 2 walks the same photons either way; the replay also walks every path in pass 1
     assert st_b["replay_segments"] > st_a["replay_segments"]
+
+
+def test_record_buffer_follows_the_first_count(m, torch):
+    """An optically thick, nearly conservative cube (beta 40 1/km over 0.8 km, albedo 0.999) makes
+    tens of events per photon, more than the first call's buffer holds (sized for 4 per photon
+    and one chunk per resident warp): that call computes W by replay pass 1 on the device. The
+    handle waits for that call's count at its next call, and stores every event from then on,
+    with the same loss and gradient."""
+    shape, h = (16, 16, 16), (50.0, 50.0, 50.0)
+    beta = np.full(int(np.prod(shape)), 40.0 * synth.KM)
+    cams = synth.make_cameras([(400.0, 400.0, -30.0), (100.0, 700.0, -30.0)], 16, 16, 60.0)
+    sc = f32_scene(synth.make_scene(shape, h, beta, cams))
+    p = synth.Params(albedo=0.999, g=0.85, sun_zenith=0.3, n_photons=200_000, seed=5)
+    grid = m.Grid.from_scene(sc)
+    args = (dev(sc.beta, np.float32), m.make_params(p, grad_mode="full"), dev(np.zeros(sc.n_pix), np.float64))
+    a = grid.render_grad(*args)
+    s1 = grid.stats()
+    b = grid.render_grad(*args)
+    s2 = grid.stats()
+    el = abs(a["loss"].item() - b["loss"].item()) / abs(b["loss"].item())
+    eg = rel_l2(a["grad"].cpu().numpy(), b["grad"].cpu().numpy())
+    record("record_buffer_first_count", events_per_photon=s1["events"] / p.n_photons, loss_rel=el, grad_rel_l2=eg)
+    assert s1["events"] > 15 * p.n_photons, s1["events"]  # ~27 per photon (oracle)
+    assert s1["events_stored"] == 0 and s2["events_stored"] == s2["events"] == s1["events"], (s1, s2)
+    assert el < 1e-6 and eg < 1e-5, (el, eg)
 
 
 def test_surrogate_mode_of_render_grad(m, torch):
