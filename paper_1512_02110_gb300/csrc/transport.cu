@@ -1319,13 +1319,35 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& t
     return wsum[warp] + incl - v;
 }
 
+// A thread's kScanPer consecutive counts: four 16-byte loads when all lie below n (lo is a
+// multiple of 16 counts, the array 16-byte aligned), else one by one.
+__device__ __forceinline__ void load_counts(const uint32_t* __restrict__ x, uint32_t n, uint32_t lo,
+                                            uint32_t (&v)[kScanPer]) {
+    static_assert(kScanPer == 16, "four uint4 per thread");
+    if (lo + kScanPer <= n) {
+        const uint4* p = reinterpret_cast<const uint4*>(x + lo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 u = __ldg(p + q);
+            v[4 * q] = u.x;
+            v[4 * q + 1] = u.y;
+            v[4 * q + 2] = u.z;
+            v[4 * q + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q) v[q] = lo + q < n ? x[lo + q] : 0u;
+    }
+}
+
 __global__ void __launch_bounds__(kTB) k_scan_tiles(const uint32_t* __restrict__ x, uint32_t n,
                                                     uint32_t* __restrict__ tsum) {
     const uint32_t lo = blockIdx.x * (uint32_t)kScanTile + threadIdx.x * kScanPer;
+    uint32_t c[kScanPer];
+    load_counts(x, n, lo, c);
     uint32_t v = 0u;
 #pragma unroll
-    for (int q = 0; q < kScanPer; ++q)
-        if (lo + q < n) v += x[lo + q];
+    for (int q = 0; q < kScanPer; ++q) v += c[q];
     uint32_t total = 0u;
     block_exclusive_scan(v, total);
     if (threadIdx.x == 0) tsum[blockIdx.x] = total;
@@ -1369,19 +1391,34 @@ __global__ void __launch_bounds__(kTB) k_scan_apply(const uint32_t* __restrict__
                                                     const uint32_t* __restrict__ tsum, uint32_t* __restrict__ out) {
     const uint32_t lo = blockIdx.x * (uint32_t)kScanTile + threadIdx.x * kScanPer;
     uint32_t v[kScanPer], sum = 0u;
+    load_counts(x, n, lo, v);
 #pragma unroll
-    for (int q = 0; q < kScanPer; ++q) {
-        v[q] = lo + q < n ? x[lo + q] : 0u;
-        sum += v[q];
-    }
+    for (int q = 0; q < kScanPer; ++q) sum += v[q];
     uint32_t total = 0u;
     uint32_t run = tsum[blockIdx.x] + block_exclusive_scan(sum, total);
+    if (lo + kScanPer <= n) {  // four 16-byte stores
+        uint4* o = reinterpret_cast<uint4*>(out + lo);
 #pragma unroll
-    for (int q = 0; q < kScanPer; ++q)
-        if (lo + q < n) {
-            out[lo + q] = run;
-            run += v[q];
+        for (int q = 0; q < 4; ++q) {
+            uint4 u;
+            u.x = run;
+            run += v[4 * q];
+            u.y = run;
+            run += v[4 * q + 1];
+            u.z = run;
+            run += v[4 * q + 2];
+            u.w = run;
+            run += v[4 * q + 3];
+            o[q] = u;
         }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q)
+            if (lo + q < n) {
+                out[lo + q] = run;
+                run += v[q];
+            }
+    }
 }
 
 // Pass-2 work list. Photons with W != 0 are binned by their pass-1 event count (the last bin
