@@ -64,7 +64,9 @@ enum {
     MST_ST_LAUNCHED = 14, MST_ST_TRACED = 15,
     MST_ST_REPLAY_SEGMENTS = 16, MST_ST_REPLAY_EVENTS = 17, MST_ST_LOS_SEGMENTS = 18,
     MST_ST_PIXEL_SEGMENTS = 19, MST_ST_BACKPROJ_SEGMENTS = 20, MST_ST_LOSADJ_SEGMENTS = 21,
-    MST_ST_REPLAY_SCATTERS = 22, MST_ST_LOST = 23, /* walks abandoned (non-finite direction); 0 in valid use */
+    MST_ST_REPLAY_SCATTERS = 22,
+    MST_ST_LOST = 23, /* walks abandoned (non-finite direction), or replay flights that missed their stored
+                         event's voxel; 0 in valid use */
     MST_ST_EVENTS_STORED = 24, /* full gradient: events the forward stored for the adjoint (0: replayed instead) */
     MST_ST_BMC_PATHS = 25, MST_ST_BMC_EVENTS = 26, MST_ST_BMC_SEGMENTS = 27, /* mst_render_bmc: flight + sun-ray voxels */
     MST_ST_AIR_EVENTS = 28, /* two-species medium (mst_set_air): forward events whose particle was air */

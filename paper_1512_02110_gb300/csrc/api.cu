@@ -361,7 +361,7 @@ bool ensure_records(mst_grid* g, uint64_t n, int dtype) {
             cudaGetLastError();  // not ready yet: size from the last count that arrived
         }
     }
-    const uint64_t max_ev = std::min<uint64_t>(g->rec_budget / rec_bytes, 0xFFFFFFFFull);  // 32-bit w_s slots
+    const uint64_t max_ev = std::min<uint64_t>(g->rec_budget / rec_bytes, 0xFFFFFFFFull);  // 32-bit slot indices
     // the forward reserves slots in per-warp chunks: one chunk per resident warp of headroom
     const uint64_t tails = (uint64_t)g->sm_count * transport_blocks_per_sm(dtype, 0, g->air != nullptr) *
                            kTransportWarps * kEventChunk;

@@ -127,7 +127,7 @@ struct mst_grid {
     double* wbuf = nullptr;       // [replay_cap], allocated by the first full-gradient call
     uint32_t* nevbuf = nullptr;   // [replay_cap]
     mst::ScoreRec* plist = nullptr;     // [replay_cap]
-    uint32_t* evoff = nullptr;          // [replay_cap] first w_s slot of each photon (stored events)
+    uint32_t* evoff = nullptr;          // [replay_cap] first step slot of each photon (stored events)
     uint64_t replay_cap = 0;            // photons the four buffers above hold
     uint32_t* evrec = nullptr;          // [kEventWords][ev_cap] stored events (full gradient)
     mst::EventStep* wseq = nullptr;     // [ev_cap] their steps (w_s, voxel, free path), grouped by photon

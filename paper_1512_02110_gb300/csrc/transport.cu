@@ -25,7 +25,7 @@ struct Photon {
     int ix, iy, iz;
     float I, tau;
     uint32_t s;      // scattering events so far
-    uint32_t hash;   // forward: path checksum; replay pass 2 on stored w_s: the photon's first w_s slot
+    uint32_t hash;   // forward: path checksum; replay pass 2 on the stored events: the photon's first step slot
     uint64_t id;     // global photon id (Philox counter)
     uint32_t idx;    // call-relative index (hash / skip arrays)
 };
@@ -657,7 +657,7 @@ __device__ __forceinline__ void store_event(const TransportArgs& A, unsigned lon
 constexpr int kScoreTile = 4096;   // photons per block in the list kernels
 // Stored events are written in per-warp chunks of kEvChunk slots (one reservation on the global
 // counter per chunk). A warp's photons come from its own ticket batches, so a chunk holds the
-// events of a few dozen photons, and the adjoint that walks a chunk finds their W and w_s slots
+// events of a few dozen photons, and the adjoint that walks a chunk finds their W and step slots
 // together in cache instead of scattered over all photons in flight. The buffer keeps one chunk
 // per resident warp of headroom for the chunks' unused tails.
 constexpr unsigned kEvChunk = kEventChunk;
@@ -1221,9 +1221,10 @@ __global__ void __launch_bounds__(kTB, min_blocks(MODE))
 }
 
 // w_s of every event the forward stored, instead of replay pass 1: the same arithmetic
-// (le_adjoint) on the same event state, written to the photon's slot in wseq for pass 2 and
-// added to W in FP64; nevbuf (zeroed after the slot scan) receives each photon's last event with
-// w_s != 0. Does nothing when the events did not fit (pass 1 then walks the paths).
+// (le_adjoint) on the same event state, written with the event's voxel and free path to the
+// photon's step slot in wseq for pass 2, and added to W in FP64; nevbuf (zeroed after the slot
+// scan) receives each photon's last event with w_s != 0. Does nothing when the events did not
+// fit (pass 1 then walks the paths).
 template <bool TWO>
 __device__ __forceinline__ void event_adjoint_run(const TransportArgs& A) {
     const unsigned long long cnt = *A.ev_count;  // reserved slots: whole chunks
@@ -1232,7 +1233,7 @@ __device__ __forceinline__ void event_adjoint_run(const TransportArgs& A) {
     unsigned long long stored = 0ull;
     // A block follows one forward warp's chunks in the order the warp wrote them (lists taken
     // from a ticket): a photon's events lie in one or two neighbouring chunks of its warp, so its
-    // W, offset and w_s slots are used while they are still cached.
+    // W, offset and step slots are used while they are still cached.
     __shared__ uint32_t list;
     for (;;) {
         if (threadIdx.x == 0) list = atomicAdd(A.ticket, 1u);
@@ -1288,7 +1289,7 @@ __global__ void __launch_bounds__(kTB) k_event_adjoint_batch(const TransportArgs
 }
 
 // Exclusive prefix sum of the photons' event counts (three passes over tiles of kScanTile):
-// photon j's w_s go to wseq[evoff[j] + s - 1], so pass 2 reads each photon's in event order.
+// photon j's steps go to wseq[evoff[j] + s - 1], so pass 2 reads each photon's in event order.
 constexpr int kScanPer = 16;                 // consecutive counts per thread
 constexpr int kScanTile = kTB * kScanPer;    // counts per block
 
