@@ -399,6 +399,30 @@ def test_full_gradient_stored_events_match_replay(m, torch, budget):
     assert st_b["replay_segments"] > st_a["replay_segments"]
 
 
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+def test_full_gradient_half_precision_grid(m, torch, kind):
+    """Full gradient with the extinction staged in FP16 / BF16 (FP32 arithmetic): the kernels of
+    that grid type (forward storing its events, the stored-event adjoint, replay pass 2 on the
+    stored steps, the LOS and image walks) against the oracle on the rounded beta."""
+    sc, p, meas, mask = _grad_case()
+    sc = sc.with_beta(quantised(sc.beta, kind))
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    skip, _, _ = _diverged(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render_grad(beta, m.make_params(p, grad_mode="full", grid_dtype=kind, reg_eta=0.05),
+                           dev(meas, np.float64), dev(mask, np.uint8))
+    st = grid.stats()
+    grid.set_debug(None, None)
+    ref = oracle.full_grad(sc, p, meas, mask, eta=0.05, skip=skip)
+    ei = max_rel(out["images"].cpu().numpy(), ref["images"], 1e-3 * np.abs(ref["images"]).max())
+    el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
+    eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    record(f"full_gradient[{kind}]", diverged_frac=skip.mean(), images_max_rel=ei, loss_rel=el, grad_rel_l2=eg)
+    assert st["events_stored"] == st["events"] > 0 and st["lost"] == 0
+    assert ei < 1e-4 and el < 1e-4 and eg < 1e-3, (ei, el, eg)
+
+
 def test_record_buffer_follows_the_first_count(m, torch):
     """An optically thick, nearly conservative cube (beta 40 1/km over 0.8 km, albedo 0.999) makes
     tens of events per photon, more than the first call's buffer holds (sized for 4 per photon
