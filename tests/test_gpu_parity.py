@@ -195,10 +195,14 @@ def test_forward_blobs16(m, torch):
 
 
 def test_forward_small_scene_roulette_and_order(m, torch):
+    """Roulette below 0.6 of the launch weight (reached at the 5th event at albedo 0.9) and the
+    order cap at 6 events both end photons."""
     sc = _small_scene()
     p = synth.Params(albedo=0.9, g=0.6, sun_zenith=math.radians(50), sun_azimuth=1.1, n_photons=60_001, seed=77,
-                     rr_threshold=0.2, rr_survival=0.3, max_order=6)
-    _forward_parity(m, torch, f32_scene(sc), p, name="forward[small,roulette,order6]")
+                     rr_threshold=0.6, rr_survival=0.3, max_order=6)
+    grid, _, _ = _forward_parity(m, torch, f32_scene(sc), p, name="forward[small,roulette,order6]")
+    st = grid.stats()
+    assert st["rr_killed"] > 0 and st["forced"] > 0, (st["rr_killed"], st["forced"])
 
 
 @pytest.mark.parametrize("kind", ["f16", "bf16"])
@@ -420,6 +424,33 @@ def test_full_gradient_half_precision_grid(m, torch, kind):
     eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
     record(f"full_gradient[{kind}]", diverged_frac=skip.mean(), images_max_rel=ei, loss_rel=el, grad_rel_l2=eg)
     assert st["events_stored"] == st["events"] > 0 and st["lost"] == 0
+    assert ei < 1e-4 and el < 1e-4 and eg < 1e-3, (ei, el, eg)
+
+
+def test_full_gradient_roulette_on_stored_events(m, torch):
+    """Full gradient on the stored events where Russian roulette ends and reweights photons (small
+    scene, three cameras in and around the grid, one of them inside the medium; roulette below
+    half the launch weight, reached after ~7 events at albedo 0.9): pass 2 must stop where the
+    forward stopped and carry the reweighted I, against the oracle."""
+    sc = f32_scene(_small_scene())
+    p = synth.Params(albedo=0.9, g=0.6, sun_zenith=math.radians(50), sun_azimuth=1.1, n_photons=60_001, seed=77,
+                     rr_threshold=0.5, rr_survival=0.3)
+    meas = oracle.forward_images(sc, p.replace(seed=4))[0]
+    sc = sc.with_beta(synth.smoothed(sc.beta, sc.shape, 0.3).astype(np.float32).astype(np.float64))
+    grid = m.Grid.from_scene(sc)
+    beta = dev(sc.beta, np.float32)
+    skip, _, _ = _diverged(m, grid, sc, p, beta)
+    grid.set_debug(None, dev(skip, np.uint8))
+    out = grid.render_grad(beta, m.make_params(p, grad_mode="full"), dev(meas, np.float64))
+    st = grid.stats()
+    grid.set_debug(None, None)
+    ref = oracle.full_grad(sc, p, meas, skip=skip)
+    ei = max_rel(out["images"].cpu().numpy(), ref["images"], 1e-3 * np.abs(ref["images"]).max())
+    el = abs(out["loss"].item() - ref["loss"]) / ref["loss"]
+    eg = rel_l2(out["grad"].cpu().numpy(), ref["grad"])
+    record("full_gradient[roulette]", diverged_frac=skip.mean(), images_max_rel=ei, loss_rel=el,
+           grad_rel_l2=eg, rr_killed=st["rr_killed"])
+    assert st["events_stored"] == st["events"] > 0 and st["lost"] == 0 and st["rr_killed"] > 0
     assert ei < 1e-4 and el < 1e-4 and eg < 1e-3, (ei, el, eg)
 
 
